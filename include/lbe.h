@@ -1,0 +1,153 @@
+/*
+ * lbe.h — C ABI of the GB300 (sm_103a) lattice Boltzmann library.
+ *
+ * The library runs the time step of §2 of Günther, Janoschek, Frijters,
+ * Harting, "Lattice Boltzmann simulations of anisotropic particles at liquid
+ * interfaces" (arXiv:1109.3277): a two-component Shan–Chen D3Q19 BGK fluid
+ * (Eq. 1–3) coupled to rigid ellipsoids by moving bounce-back (Eq. 4) with
+ * momentum exchange (Eq. 5), anisotropic Hertz and lubrication pair forces
+ * (Eq. 6–9), outer-shell density fill and particle colour (Eq. 10 and the
+ * colour rule after it), all on one GPU.
+ *
+ * Conventions
+ *  - Lattice units: spacing and time step 1, c_s^2 = 1/3.  Node (x,y,z) sits
+ *    at position (x,y,z); node index n = x + nx*(y + ny*z).
+ *  - Component 0 is "red", component 1 is "blue".
+ *  - A particle's symmetry axis is its body x axis; quaternions are
+ *    (w, x, y, z) and rotate body vectors into the lab frame.
+ *  - Ownership: the caller owns every host pointer; the library copies
+ *    inputs and writes outputs into caller buffers.  Each lbe_ctx owns all
+ *    device memory it allocates and frees it in lbe_destroy.
+ *  - Errors: every call returns an lbe_status; nothing aborts and no C++
+ *    exception crosses the ABI.  An invalid argument leaves the context
+ *    unchanged.  lbe_last_error() gives a one-line message.
+ *  - Streams: work is enqueued on the descriptor's cuda_stream (a
+ *    cudaStream_t; NULL makes the library create its own stream).
+ *    lbe_step returns once the work is enqueued; lbe_read_*, lbe_mass and
+ *    lbe_get_populations synchronise that stream and report any deferred
+ *    device error.
+ */
+#ifndef LBE_H
+#define LBE_H
+#include <stddef.h>
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define LBE_API __attribute__((visibility("default")))
+#else
+#define LBE_API
+#endif
+
+typedef struct lbe_ctx lbe_ctx;
+
+typedef enum {
+    LBE_OK = 0,
+    LBE_EINVAL = -1,   /* invalid argument; nothing changed */
+    LBE_ENOMEM = -2,   /* device or host allocation failed */
+    LBE_ECUDA = -3,    /* a CUDA call failed; see lbe_last_error */
+    LBE_ENUMERIC = -4, /* non-finite or negative density detected */
+    LBE_EOVERLAP = -5, /* reserved */
+    LBE_ETIMEOUT = -6, /* a bounded wait ran out */
+    LBE_EBUSY = -7     /* the request cannot be taken now (serving) */
+} lbe_status;
+
+/* Population storage.  Arithmetic is FP32 in every mode; the 16-bit modes
+ * store δf = f - w_i rho_ref^c and halve the population bytes. */
+typedef enum {
+    LBE_STORE_F32 = 0,
+    LBE_STORE_BF16_OFS = 1,
+    LBE_STORE_F16_OFS = 2
+} lbe_storage;
+
+/* Particle motion. */
+typedef enum {
+    LBE_PARTICLES_FREE = 0,       /* Newton–Euler under fluid + pair forces */
+    LBE_PARTICLES_STATIC = 1,     /* geometry fixed; V, ω still enter Eq. 4 */
+    LBE_PARTICLES_PRESCRIBED = 2  /* V and lab-frame ω held constant, geometry moves */
+} lbe_particle_mode;
+
+typedef struct {
+    int32_t nx, ny, nz;      /* lattice extent, each >= 1 (nz >= 3 with walls) */
+    int32_t walls_z;         /* 0: periodic in z; 1: one-node walls at z=0 and z=nz-1
+                                (the impenetrable walls of the §4 adsorption box) */
+    double  tau[2];          /* BGK relaxation time per component, > 1/2 (Eq. 2) */
+    double  g_br;            /* Shan–Chen coupling of Eq. 3; > 0 demixes (§4: 0.1, 0.08) */
+    double  body_force[3];   /* extra force per unit density on every fluid node */
+    double  rho_ref[2];      /* 16-bit offset base per component; also the density given
+                                to a node uncovered with no fluid neighbour */
+    int32_t storage;         /* lbe_storage */
+    int32_t particle_mode;   /* lbe_particle_mode */
+    double  k_hertz;         /* K_H of the Hertz potential (§2: 100) */
+    double  lub_cut;         /* Δc of the lubrication correction (§2: 2/3); 0 disables it */
+    double  lub_rho;         /* density in μ = ν ρ of the lubrication correction */
+    void   *cuda_stream;     /* cudaStream_t to enqueue on, or NULL */
+} lbe_lattice_desc;
+
+/* Create a lattice on the current CUDA device with populations at the rest
+ * equilibrium f_i^c = w_i rho0^c (Eq. 2 at u = 0).
+ *  rho0: host, double [2][nz][ny][nx], caller-owned, copied; values on wall
+ *        nodes are ignored.
+ * Returns LBE_EINVAL for a bad descriptor, LBE_ENOMEM if device memory runs
+ * out (nothing is kept), LBE_ECUDA for other CUDA failures. */
+LBE_API lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_ctx **out);
+
+/* Add n rigid ellipsoids (§2: radius r_par along the symmetry axis, r_perp
+ * across it; colour delta_rho, the surface-density parameter of the
+ * wettability rule).  Host arrays, caller-owned, copied:
+ *  pos [n][3] (inside the lattice), quat [n][4] (normalised on entry),
+ *  vel [n][3] and omega [n][3] (lab frame; NULL = zero),
+ *  r_par [n], r_perp [n] (> 0), delta_rho [n].
+ * Non-wall nodes inside a particle become solid (a node inside several
+ * particles belongs to the lowest index); their fluid is discarded. */
+LBE_API lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const double *quat,
+                             const double *vel, const double *omega, const double *r_par,
+                             const double *r_perp, const double *delta_rho);
+
+/* Advance nsteps time steps (Eq. 1 per step, with every coupling above),
+ * asynchronously on the context's stream. */
+LBE_API lbe_status lbe_step(lbe_ctx *c, int32_t nsteps);
+
+/* Read the current fields (synchronises).  Host outputs, any may be NULL:
+ *  rho  double [2][N]: ρ^c on fluid nodes, 0 on solid nodes;
+ *  vel  double [3][N]: (Σ_c j^c + ½ Σ_c F^c) / Σ_c ρ^c on fluid nodes, 0 on solid;
+ *  node_type uint8 [N]: 0 fluid, 1 wall, 2 particle. */
+LBE_API lbe_status lbe_read_fields(lbe_ctx *c, double *rho, double *vel, uint8_t *node_type);
+
+/* Read the particle state (synchronises).  Host outputs, each n*k doubles or
+ * NULL: pos, quat (w,x,y,z), vel, omega (lab), force and torque = the total
+ * of the last update (momentum exchange + pair forces + fill/empty). */
+LBE_API lbe_status lbe_read_particles(lbe_ctx *c, double *pos, double *quat, double *vel, double *omega,
+                              double *force, double *torque);
+
+/* Per-component fluid mass Σ_x Σ_i f_i^c over fluid nodes, summed in FP64
+ * in a fixed order (synchronises). */
+LBE_API lbe_status lbe_mass(lbe_ctx *c, double out[2]);
+
+/* Raw populations f[2][19][N] as doubles (synchronises / uploads).  Solid
+ * nodes hold unspecified values. */
+LBE_API lbe_status lbe_get_populations(lbe_ctx *c, double *f);
+LBE_API lbe_status lbe_set_populations(lbe_ctx *c, const double *f);
+
+/* Per-kernel timing with CUDA events on the context's stream.  When enabled,
+ * every launch of the dominant fluid kernel is bracketed by events;
+ * lbe_profile_read returns the summed milliseconds and the launch count
+ * since the last enable, and synchronises. */
+LBE_API lbe_status lbe_profile_enable(lbe_ctx *c, int32_t enable);
+LBE_API lbe_status lbe_profile_read(lbe_ctx *c, double *ms_total, int64_t *launches);
+
+/* Number of kernels one lbe_step(c, 1) enqueues (for launch accounting). */
+LBE_API int32_t lbe_kernels_per_step(const lbe_ctx *c);
+
+/* Device bytes held by the context. */
+LBE_API size_t lbe_device_bytes(const lbe_ctx *c);
+
+LBE_API const char *lbe_last_error(const lbe_ctx *c);
+LBE_API void lbe_destroy(lbe_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,444 @@
+// Fluid kernels of the lattice Boltzmann step (§2 of Günther et al.,
+// arXiv:1109.3277): moments, ψ, outer-shell fill with the colour rule,
+// Shan–Chen force (Eq. 3), shifted-velocity BGK collision (Eq. 2) and
+// streaming (Eq. 1) with halfway bounce-back, plus readers and mass sums.
+#include "lbe_internal.cuh"
+
+namespace lbe {
+
+namespace {
+
+struct Coord {
+    int x, y, z;
+};
+
+__device__ __forceinline__ Coord coord_of(const Lat &L, int n)
+{
+    Coord c;
+    c.x = n % L.nx;
+    int t = n / L.nx;
+    c.y = t % L.ny;
+    c.z = t / L.ny;
+    return c;
+}
+
+// Wrapped coordinates x-1, x, x+1 (and for y, z).  With walls the z
+// neighbours of the boundary planes do not exist and are flagged -1.
+struct Nbr {
+    int xs[3], ys[3], zs[3];
+};
+
+__device__ __forceinline__ Nbr nbr_of(const Lat &L, Coord c)
+{
+    Nbr b;
+    b.xs[0] = c.x == 0 ? L.nx - 1 : c.x - 1;
+    b.xs[1] = c.x;
+    b.xs[2] = c.x == L.nx - 1 ? 0 : c.x + 1;
+    b.ys[0] = c.y == 0 ? L.ny - 1 : c.y - 1;
+    b.ys[1] = c.y;
+    b.ys[2] = c.y == L.ny - 1 ? 0 : c.y + 1;
+    if (L.walls) {
+        b.zs[0] = c.z - 1;
+        b.zs[2] = c.z + 1 < L.nz ? c.z + 1 : -1;
+    } else {
+        b.zs[0] = c.z == 0 ? L.nz - 1 : c.z - 1;
+        b.zs[2] = c.z == L.nz - 1 ? 0 : c.z + 1;
+    }
+    b.zs[1] = c.z;
+    return b;
+}
+
+__device__ __forceinline__ int nidx(const Lat &L, const Nbr &b, int i)
+{
+    int z = b.zs[cz(i) + 1];
+    if (z < 0) return -1;
+    return b.xs[cx(i) + 1] + L.nx * (b.ys[cy(i) + 1] + L.ny * z);
+}
+
+template <class S>
+__device__ __forceinline__ const typename S::T *slot(const typename S::T *f, const Lat &L, int c,
+                                                     int i)
+{
+    return f + (size_t)(c * Q + i) * (size_t)L.N;
+}
+template <class S>
+__device__ __forceinline__ typename S::T *slot(typename S::T *f, const Lat &L, int c, int i)
+{
+    return f + (size_t)(c * Q + i) * (size_t)L.N;
+}
+
+// ---------------------------------------------------------------- init
+
+template <class S>
+__global__ void k_init_f(Lat L, const double *__restrict__ rho0, typename S::T *__restrict__ f,
+                         const uint8_t *__restrict__ type)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.N) return;
+    bool fl = type[n] == FLUID;
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        float r = fl ? (float)rho0[(size_t)c * L.N + n] : 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; i++) S::st(slot<S>(f, L, c, i) + n, wgt(i) * r, L.base[c][i]);
+    }
+}
+
+// ------------------------------------------------------------- moments
+// ρ^c = Σ_i f_i^c on fluid nodes and ψ^c = 1 - exp(-ρ^c) (Eq. 3's weight).
+
+template <class S>
+__global__ void __launch_bounds__(256) k_moments(Lat L, const typename S::T *__restrict__ f,
+                                                 const uint8_t *__restrict__ type,
+                                                 float *__restrict__ rho, float *__restrict__ psi)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.N || type[n] != FLUID) return;
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        float r = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; i++) r += S::ld(slot<S>(f, L, c, i) + n, L.base[c][i]);
+        rho[(size_t)c * L.N + n] = r;
+        psi[(size_t)c * L.N + n] = 1.f - expf(-r);
+    }
+}
+
+// ---------------------------------------------------------- shell fill
+// Solid nodes with at least one fluid neighbour take the mean ρ^c of those
+// neighbours (Eq. 10); the colour Δρ of the owning particle is added to red
+// if positive, else |Δρ| to blue.  Walls take Δρ = 0.
+
+__global__ void __launch_bounds__(256) k_shell(Lat L, const float *__restrict__ rho,
+                                               float *__restrict__ psi,
+                                               const uint8_t *__restrict__ type,
+                                               const uint32_t *__restrict__ owner,
+                                               const double *__restrict__ drho)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.N) return;
+    uint8_t t = type[n];
+    if (t == FLUID) return;
+    Coord c = coord_of(L, n);
+    Nbr b = nbr_of(L, c);
+    float s0 = 0.f, s1 = 0.f;
+    int cnt = 0;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        int m = nidx(L, b, i);
+        if (m < 0 || type[m] != FLUID) continue;
+        s0 += rho[m];
+        s1 += rho[(size_t)L.N + m];
+        cnt++;
+    }
+    if (cnt == 0) return;  // interior: never read by a fluid node
+    float r0 = s0 / (float)cnt, r1 = s1 / (float)cnt;
+    float dr = t == PART ? (float)drho[owner[n]] : 0.f;
+    if (dr > 0.f)
+        r0 += dr;
+    else
+        r1 += fabsf(dr);
+    psi[n] = 1.f - expf(-r0);
+    psi[(size_t)L.N + n] = 1.f - expf(-r1);
+}
+
+// ------------------------------------------------------ collide + stream
+// Shan–Chen force F^c = -g ψ^c(x) Σ_{i=1..18} ψ^{c'}(x+c_i) c_i + ρ^c g_body,
+// shifted velocity u' = Σ_c j^c/τ_c / Σ_c ρ^c/τ_c, equilibrium of component
+// c at u' + τ_c F^c/ρ^c, BGK relaxation, then push streaming: a population
+// whose target is solid is reflected into the opposite slot of its own node.
+
+template <class S>
+__global__ void __launch_bounds__(256) k_collide_stream(Lat L, const typename S::T *__restrict__ fin,
+                                                        typename S::T *__restrict__ fout,
+                                                        const float *__restrict__ psi,
+                                                        const uint8_t *__restrict__ type)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.N || type[n] != FLUID) return;
+    Coord co = coord_of(L, n);
+    Nbr b = nbr_of(L, co);
+    float f[2][Q];
+#pragma unroll
+    for (int c = 0; c < 2; c++)
+#pragma unroll
+        for (int i = 0; i < Q; i++) f[c][i] = S::ld(slot<S>(fin, L, c, i) + n, L.base[c][i]);
+    float rho[2], j[2][3];
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            r += f[c][i];
+            if (cx(i)) jx += cx(i) * f[c][i];
+            if (cy(i)) jy += cy(i) * f[c][i];
+            if (cz(i)) jz += cz(i) * f[c][i];
+        }
+        rho[c] = r;
+        j[c][0] = jx;
+        j[c][1] = jy;
+        j[c][2] = jz;
+    }
+    float s[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    int nb[Q];
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        int m = nidx(L, b, i);
+        nb[i] = m;
+        float p0 = m >= 0 ? psi[m] : 0.f, p1 = m >= 0 ? psi[(size_t)L.N + m] : 0.f;
+        // red feels blue's ψ and vice versa
+        if (cx(i)) { s[0][0] += cx(i) * p1; s[1][0] += cx(i) * p0; }
+        if (cy(i)) { s[0][1] += cy(i) * p1; s[1][1] += cy(i) * p0; }
+        if (cz(i)) { s[0][2] += cz(i) * p1; s[1][2] += cz(i) * p0; }
+    }
+    nb[0] = n;
+    float den = rho[0] * L.itau[0] + rho[1] * L.itau[1];
+    float up[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        up[k] = den > 0.f ? (j[0][k] * L.itau[0] + j[1][k] * L.itau[1]) / den : 0.f;
+    bool solid_nb[Q];
+#pragma unroll
+    for (int i = 1; i < Q; i++) solid_nb[i] = nb[i] < 0 || type[nb[i]] != FLUID;
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        float pc = psi[(size_t)c * L.N + n];
+        float r = rho[c];
+        float ue[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            float F = -L.g * pc * s[c][k] + r * L.body[k];
+            ue[k] = r > 0.f ? up[k] + L.tau[c] * F / r : up[k];
+        }
+        float uu = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
+        float it = L.itau[c];
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            float cu = cx(i) * ue[0] + cy(i) * ue[1] + cz(i) * ue[2];
+            float feq = wgt(i) * r * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
+            float fs = f[c][i] - (f[c][i] - feq) * it;
+            if (i == 0) {
+                S::st(slot<S>(fout, L, c, 0) + n, fs, L.base[c][0]);
+            } else if (!solid_nb[i]) {
+                S::st(slot<S>(fout, L, c, i) + nb[i], fs, L.base[c][i]);
+            } else {
+                S::st(slot<S>(fout, L, c, opp(i)) + n, fs, L.base[c][opp(i)]);
+            }
+        }
+    }
+}
+
+// -------------------------------------------------------------- fields
+
+template <class S>
+__global__ void k_fields(Lat L, const typename S::T *__restrict__ f, const float *__restrict__ psi,
+                         const uint8_t *__restrict__ type, double *__restrict__ rho_out,
+                         double *__restrict__ vel_out)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.N) return;
+    if (type[n] != FLUID) {
+        if (rho_out) {
+            rho_out[n] = 0.0;
+            rho_out[(size_t)L.N + n] = 0.0;
+        }
+        if (vel_out)
+            for (int k = 0; k < 3; k++) vel_out[(size_t)k * L.N + n] = 0.0;
+        return;
+    }
+    Coord co = coord_of(L, n);
+    Nbr b = nbr_of(L, co);
+    float rho[2], m[3] = {0.f, 0.f, 0.f};
+    for (int c = 0; c < 2; c++) {
+        float r = 0.f;
+        for (int i = 0; i < Q; i++) {
+            float v = S::ld(slot<S>(f, L, c, i) + n, L.base[c][i]);
+            r += v;
+            m[0] += cx(i) * v;
+            m[1] += cy(i) * v;
+            m[2] += cz(i) * v;
+        }
+        rho[c] = r;
+    }
+    for (int c = 0; c < 2; c++) {
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+        for (int i = 1; i < Q; i++) {
+            int mm = nidx(L, b, i);
+            float p = mm >= 0 ? psi[(size_t)(1 - c) * L.N + mm] : 0.f;
+            sx += cx(i) * p;
+            sy += cy(i) * p;
+            sz += cz(i) * p;
+        }
+        float pc = psi[(size_t)c * L.N + n];
+        m[0] += 0.5f * (-L.g * pc * sx + rho[c] * L.body[0]);
+        m[1] += 0.5f * (-L.g * pc * sy + rho[c] * L.body[1]);
+        m[2] += 0.5f * (-L.g * pc * sz + rho[c] * L.body[2]);
+    }
+    float tot = rho[0] + rho[1];
+    if (rho_out) {
+        rho_out[n] = rho[0];
+        rho_out[(size_t)L.N + n] = rho[1];
+    }
+    if (vel_out)
+        for (int k = 0; k < 3; k++) vel_out[(size_t)k * L.N + n] = tot > 0.f ? m[k] / tot : 0.0;
+}
+
+// ---------------------------------------------------------------- mass
+// Per-block FP64 partial sums in a fixed grid-stride order, then one block
+// adds the partials in index order: the result does not depend on timing.
+
+constexpr int MASS_BLOCKS = 1024;
+constexpr int MASS_THREADS = 256;
+
+template <class S>
+__global__ void __launch_bounds__(MASS_THREADS) k_mass(Lat L, const typename S::T *__restrict__ f,
+                                                       const uint8_t *__restrict__ type,
+                                                       double *__restrict__ partials)
+{
+    double a0 = 0.0, a1 = 0.0;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < L.N; n += gridDim.x * blockDim.x) {
+        if (type[n] != FLUID) continue;
+        float r0 = 0.f, r1 = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            r0 += S::ld(slot<S>(f, L, 0, i) + n, L.base[0][i]);
+            r1 += S::ld(slot<S>(f, L, 1, i) + n, L.base[1][i]);
+        }
+        a0 += (double)r0;
+        a1 += (double)r1;
+    }
+    __shared__ double sh[2][MASS_THREADS];
+    sh[0][threadIdx.x] = a0;
+    sh[1][threadIdx.x] = a1;
+    __syncthreads();
+    for (int w = MASS_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = sh[0][0];
+        partials[gridDim.x + blockIdx.x] = sh[1][0];
+    }
+}
+
+__global__ void k_mass_final(const double *__restrict__ partials, int nb, double *__restrict__ out)
+{
+    __shared__ double sh[2][MASS_THREADS];
+    double a0 = 0.0, a1 = 0.0;
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+        a0 += partials[k];
+        a1 += partials[nb + k];
+    }
+    sh[0][threadIdx.x] = a0;
+    sh[1][threadIdx.x] = a1;
+    __syncthreads();
+    for (int w = MASS_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sh[0][0];
+        out[1] = sh[1][0];
+    }
+}
+
+// --------------------------------------------------------- raw f access
+
+template <class S>
+__global__ void k_get_f(Lat L, const typename S::T *__restrict__ f, double *__restrict__ out)
+{
+    size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t tot = (size_t)2 * Q * L.N;
+    if (k >= tot) return;
+    int ci = (int)(k / L.N);
+    out[k] = (double)S::cvt(f[k], L.base[ci / Q][ci % Q]);
+}
+
+template <class S>
+__global__ void k_set_f(Lat L, const double *__restrict__ in, typename S::T *__restrict__ f)
+{
+    size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t tot = (size_t)2 * Q * L.N;
+    if (k >= tot) return;
+    int ci = (int)(k / L.N);
+    f[k] = S::enc((float)in[k], L.base[ci / Q][ci % Q]);
+}
+
+inline unsigned blocks_for(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+int mass_blocks() { return MASS_BLOCKS; }
+
+#define LBE_DISPATCH(storage, CALL)                  \
+    do {                                             \
+        switch (storage) {                           \
+        case LBE_STORE_F16_OFS: { using S = StF16; CALL; } break;  \
+        case LBE_STORE_BF16_OFS: { using S = StBF16; CALL; } break; \
+        default: { using S = StF32; CALL; } break;   \
+        }                                            \
+    } while (0)
+
+void launch_init_f(int storage, const Lat &L, const double *rho0, void *f, const uint8_t *type,
+                   cudaStream_t s)
+{
+    LBE_DISPATCH(storage, (k_init_f<S><<<blocks_for(L.N, 256), 256, 0, s>>>(
+                              L, rho0, (typename S::T *)f, type)));
+}
+
+void launch_moments(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho,
+                    float *psi, cudaStream_t s)
+{
+    LBE_DISPATCH(storage, (k_moments<S><<<blocks_for(L.N, 256), 256, 0, s>>>(
+                              L, (const typename S::T *)f, type, rho, psi)));
+}
+
+void launch_shell(const Lat &L, const float *rho, float *psi, const uint8_t *type,
+                  const uint32_t *owner, const double *drho, cudaStream_t s)
+{
+    k_shell<<<blocks_for(L.N, 256), 256, 0, s>>>(L, rho, psi, type, owner, drho);
+}
+
+void launch_collide_stream(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
+                           const uint8_t *type, cudaStream_t s)
+{
+    LBE_DISPATCH(storage, (k_collide_stream<S><<<blocks_for(L.N, 256), 256, 0, s>>>(
+                              L, (const typename S::T *)fin, (typename S::T *)fout, psi, type)));
+}
+
+void launch_fields(int storage, const Lat &L, const void *f, const float *psi, const uint8_t *type,
+                   double *rho_out, double *vel_out, cudaStream_t s)
+{
+    LBE_DISPATCH(storage, (k_fields<S><<<blocks_for(L.N, 256), 256, 0, s>>>(
+                              L, (const typename S::T *)f, psi, type, rho_out, vel_out)));
+}
+
+void launch_mass(int storage, const Lat &L, const void *f, const uint8_t *type, double *partials,
+                 int nblocks, double *out, cudaStream_t s)
+{
+    LBE_DISPATCH(storage, (k_mass<S><<<nblocks, MASS_THREADS, 0, s>>>(
+                              L, (const typename S::T *)f, type, partials)));
+    k_mass_final<<<1, MASS_THREADS, 0, s>>>(partials, nblocks, out);
+}
+
+void launch_get_f(int storage, const Lat &L, const void *f, double *out, cudaStream_t s)
+{
+    size_t tot = (size_t)2 * Q * L.N;
+    LBE_DISPATCH(storage, (k_get_f<S><<<blocks_for(tot, 256), 256, 0, s>>>(
+                              L, (const typename S::T *)f, out)));
+}
+
+void launch_set_f(int storage, const Lat &L, const double *in, void *f, cudaStream_t s)
+{
+    size_t tot = (size_t)2 * Q * L.N;
+    LBE_DISPATCH(storage, (k_set_f<S><<<blocks_for(tot, 256), 256, 0, s>>>(
+                              L, in, (typename S::T *)f)));
+}
+
+}  // namespace lbe

@@ -1,0 +1,542 @@
+// Host side of liblbe: context, device memory, the per-step launch
+// sequence (captured in CUDA graphs) and the C ABI of include/lbe.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbe_internal.cuh"
+
+using namespace lbe;
+
+struct lbe_ctx {
+    lbe_lattice_desc d{};
+    Lat L{};
+    Pair pair{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    size_t esize = 4;
+    void *f[2] = {nullptr, nullptr};
+    int cur = 0;
+    float *rho = nullptr, *psi = nullptr;
+    uint8_t *type = nullptr;
+    uint32_t *owner[2] = {nullptr, nullptr};
+    int ocur = 0;
+    double *mass_partials = nullptr, *mass_out = nullptr;
+    // particles
+    int np = 0, cap = 0;
+    double *pbuf = nullptr;
+    float *x32 = nullptr;
+    Parts P{};
+    // graphs keyed by (cur, ocur)
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    // profiling
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    size_t bytes = 0;
+    std::string err;
+};
+
+namespace {
+
+lbe_status fail(lbe_ctx *c, lbe_status st, const std::string &m)
+{
+    if (c) c->err = m;
+    return st;
+}
+
+lbe_status cuda_fail(lbe_ctx *c, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? LBE_ENOMEM : LBE_ECUDA, m);
+}
+
+#define CK(c, call)                                            \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+size_t storage_size(int s) { return s == LBE_STORE_F32 ? 4 : 2; }
+
+void drop_graphs(lbe_ctx *c)
+{
+    for (auto &g : c->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+// Field offsets inside the particle buffer (doubles per particle).
+enum { OX = 0, OQ = 3, OV = 7, OW = 10, OXO = 13, OQO = 16, ORP = 20, ORO = 21, ODR = 22, OM = 23,
+       OIP = 24, OIQ = 25, OFL = 26, OTL = 29, OFP = 32, OTP = 35, OFE = 38, OTE = 41, OF = 44,
+       OT = 47, PSTRIDE = 50 };
+
+void bind_parts(lbe_ctx *c)
+{
+    // structure of arrays: field k occupies [k*cap, (k+1)*cap) doubles
+    double *b = c->pbuf;
+    size_t cp = (size_t)c->cap;
+    auto at = [&](int off) { return b + (size_t)off * cp; };
+    Parts &P = c->P;
+    P.n = c->np;
+    P.X = at(OX);
+    P.q = at(OQ);
+    P.V = at(OV);
+    P.W = at(OW);
+    P.Xold = at(OXO);
+    P.qold = at(OQO);
+    P.rp = at(ORP);
+    P.ro = at(ORO);
+    P.drho = at(ODR);
+    P.M = at(OM);
+    P.Ipar = at(OIP);
+    P.Iperp = at(OIQ);
+    P.Flink = at(OFL);
+    P.Tlink = at(OTL);
+    P.Fpair = at(OFP);
+    P.Tpair = at(OTP);
+    P.Fpend = at(OFE);
+    P.Tpend = at(OTE);
+    P.F = at(OF);
+    P.T = at(OT);
+    P.X32 = c->x32;
+}
+
+void free_all(lbe_ctx *c)
+{
+    drop_graphs(c);
+    for (auto &e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
+    cudaFree(c->f[0]);
+    cudaFree(c->f[1]);
+    cudaFree(c->rho);
+    cudaFree(c->psi);
+    cudaFree(c->type);
+    cudaFree(c->owner[0]);
+    cudaFree(c->owner[1]);
+    cudaFree(c->mass_partials);
+    cudaFree(c->mass_out);
+    cudaFree(c->pbuf);
+    cudaFree(c->x32);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+template <class T>
+cudaError_t dalloc(lbe_ctx *c, T **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e == cudaSuccess) c->bytes += bytes;
+    return e;
+}
+
+__global__ void k_set_types(Lat L, uint8_t *type)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.N) return;
+    int z = n / (L.nx * L.ny);
+    type[n] = (L.walls && (z == 0 || z == L.nz - 1)) ? WALL : FLUID;
+}
+
+// Enqueue one time step (no host synchronisation).
+void enqueue_step(lbe_ctx *c)
+{
+    cudaStream_t s = c->stream;
+    const Lat &L = c->L;
+    int st = c->d.storage;
+    void *fin = c->f[c->cur], *fout = c->f[1 - c->cur];
+    launch_moments(st, L, fin, c->type, c->rho, c->psi, s);
+    launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, s);
+    if (c->profiling) {
+        if (c->ev_used + 2 > c->ev.size()) {
+            for (int k = 0; k < 256; k++) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                c->ev.push_back(e);
+            }
+        }
+        cudaEventRecord(c->ev[c->ev_used], s);
+    }
+    launch_collide_stream(st, L, fin, fout, c->psi, c->type, s);
+    if (c->profiling) {
+        cudaEventRecord(c->ev[c->ev_used + 1], s);
+        c->ev_used += 2;
+    }
+    if (c->np > 0) {
+        c->P.n = c->np;
+        launch_links(st, L, c->P, fout, c->rho, c->type, c->owner[c->ocur], s);
+        launch_pairs(L, c->P, c->pair, s);
+        launch_integrate(L, c->P, c->d.particle_mode, s);
+        if (c->d.particle_mode != LBE_PARTICLES_STATIC) {
+            uint32_t *oo = c->owner[c->ocur], *on = c->owner[1 - c->ocur];
+            launch_claim(L, c->P, 0, on, s);
+            launch_transition(st, L, c->P, fout, c->type, oo, on, 0, s);
+            launch_reset(L, c->P, 1, oo, s);
+            c->ocur = 1 - c->ocur;
+        }
+    }
+    c->cur = 1 - c->cur;
+}
+
+lbe_status check_async(lbe_ctx *c, const char *where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, where);
+    return LBE_OK;
+}
+
+lbe_status sync(lbe_ctx *c, const char *where)
+{
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, where);
+    return check_async(c, where);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_ctx **out)
+{
+    if (!d || !rho0 || !out) return LBE_EINVAL;
+    *out = nullptr;
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) return LBE_EINVAL;
+    if (d->walls_z && d->nz < 3) return LBE_EINVAL;
+    if (!(d->tau[0] > 0.5) || !(d->tau[1] > 0.5)) return LBE_EINVAL;
+    if (d->storage < LBE_STORE_F32 || d->storage > LBE_STORE_F16_OFS) return LBE_EINVAL;
+    if (d->particle_mode < 0 || d->particle_mode > 2) return LBE_EINVAL;
+    long long N = (long long)d->nx * d->ny * d->nz;
+    if (N > 0x7fffffffLL) return LBE_EINVAL;
+    lbe_ctx *c = new (std::nothrow) lbe_ctx();
+    if (!c) return LBE_ENOMEM;
+    c->d = *d;
+    Lat &L = c->L;
+    L.nx = d->nx;
+    L.ny = d->ny;
+    L.nz = d->nz;
+    L.walls = d->walls_z ? 1 : 0;
+    L.N = (int)N;
+    for (int k = 0; k < 2; k++) {
+        L.tau[k] = (float)d->tau[k];
+        L.itau[k] = (float)(1.0 / d->tau[k]);
+        L.rho_ref[k] = d->rho_ref[k];
+        for (int i = 0; i < Q; i++)
+            L.base[k][i] = d->storage == LBE_STORE_F32 ? 0.f : (float)(wgtd(i) * d->rho_ref[k]);
+    }
+    L.g = (float)d->g_br;
+    for (int k = 0; k < 3; k++) L.body[k] = (float)d->body_force[k];
+    c->pair.k_hertz = d->k_hertz;
+    c->pair.lub_cut = d->lub_cut;
+    c->pair.mu = d->lub_rho * ((0.5 * (d->tau[0] + d->tau[1]) - 0.5) / 3.0);
+    c->pair.mode = d->particle_mode;
+    c->esize = storage_size(d->storage);
+    lbe_status st = LBE_OK;
+    auto bail = [&](cudaError_t e, const char *w) {
+        st = cuda_fail(c, e, w);
+        free_all(c);
+        delete c;
+        return st;
+    };
+    cudaError_t e;
+    if (d->cuda_stream) {
+        c->stream = (cudaStream_t)d->cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return bail(e, "cudaStreamCreate");
+        c->own_stream = true;
+    }
+    size_t fbytes = (size_t)2 * Q * N * c->esize;
+    if ((e = dalloc(c, &c->f[0], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f0)");
+    if ((e = dalloc(c, &c->f[1], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f1)");
+    if ((e = dalloc(c, &c->rho, (size_t)2 * N * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc(rho)");
+    if ((e = dalloc(c, &c->psi, (size_t)2 * N * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc(psi)");
+    if ((e = dalloc(c, &c->type, (size_t)N)) != cudaSuccess) return bail(e, "cudaMalloc(type)");
+    if ((e = dalloc(c, &c->owner[0], (size_t)N * 4)) != cudaSuccess) return bail(e, "cudaMalloc(owner0)");
+    if ((e = dalloc(c, &c->owner[1], (size_t)N * 4)) != cudaSuccess) return bail(e, "cudaMalloc(owner1)");
+    if ((e = dalloc(c, &c->mass_partials, (size_t)2 * mass_blocks() * sizeof(double))) != cudaSuccess)
+        return bail(e, "cudaMalloc(mass)");
+    if ((e = dalloc(c, &c->mass_out, 2 * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc(mass_out)");
+    cudaStream_t s = c->stream;
+    cudaMemsetAsync(c->owner[0], 0xFF, (size_t)N * 4, s);
+    cudaMemsetAsync(c->owner[1], 0xFF, (size_t)N * 4, s);
+    cudaMemsetAsync(c->rho, 0, (size_t)2 * N * sizeof(float), s);
+    cudaMemsetAsync(c->psi, 0, (size_t)2 * N * sizeof(float), s);
+    cudaMemsetAsync(c->f[1], 0, fbytes, s);
+    k_set_types<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(L, c->type);
+    double *drho0 = nullptr;
+    if ((e = cudaMallocAsync((void **)&drho0, (size_t)2 * N * sizeof(double), s)) != cudaSuccess)
+        return bail(e, "cudaMallocAsync(rho0)");
+    cudaMemcpyAsync(drho0, rho0, (size_t)2 * N * sizeof(double), cudaMemcpyHostToDevice, s);
+    launch_init_f(d->storage, L, drho0, c->f[0], c->type, s);
+    cudaFreeAsync(drho0, s);
+    e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return bail(e, "init");
+    bind_parts(c);
+    *out = c;
+    return LBE_OK;
+}
+
+lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const double *quat,
+                             const double *vel, const double *omega, const double *r_par,
+                             const double *r_perp, const double *delta_rho)
+{
+    if (!c) return LBE_EINVAL;
+    if (n < 0 || (n > 0 && (!pos || !quat || !r_par || !r_perp || !delta_rho)))
+        return fail(c, LBE_EINVAL, "add_particles: bad arguments");
+    if (n == 0) return LBE_OK;
+    int ext[3] = {c->d.nx, c->d.ny, c->d.nz};
+    for (int k = 0; k < n; k++) {
+        if (!(r_par[k] > 0) || !(r_perp[k] > 0)) return fail(c, LBE_EINVAL, "add_particles: radii must be positive");
+        double qq = quat[4 * k] * quat[4 * k] + quat[4 * k + 1] * quat[4 * k + 1] +
+                    quat[4 * k + 2] * quat[4 * k + 2] + quat[4 * k + 3] * quat[4 * k + 3];
+        if (!(qq > 0)) return fail(c, LBE_EINVAL, "add_particles: zero quaternion");
+        for (int j = 0; j < 3; j++)
+            if (!(pos[3 * k + j] >= 0) || !(pos[3 * k + j] < ext[j]))
+                return fail(c, LBE_EINVAL, "add_particles: position outside the lattice");
+    }
+    lbe_status st = sync(c, "add_particles");
+    if (st != LBE_OK) return st;
+    static const int FIELDS[][2] = {{OX, 3},  {OQ, 4},  {OV, 3},  {OW, 3},  {OXO, 3}, {OQO, 4}, {ORP, 1},
+                                    {ORO, 1}, {ODR, 1}, {OM, 1},  {OIP, 1}, {OIQ, 1}, {OFL, 3}, {OTL, 3},
+                                    {OFP, 3}, {OTP, 3}, {OFE, 3}, {OTE, 3}, {OF, 3},  {OT, 3}};
+    // Each field of width k occupies k*cap doubles starting at off*cap; the
+    // live state of existing particles is read back and re-laid for the new
+    // capacity.
+    int old = c->np, cap = c->cap, np = old + n;
+    int ncap = np > cap ? (np < 64 ? 64 : np + np / 4) : cap;
+    std::vector<double> oldb;
+    if (old > 0) {
+        oldb.resize((size_t)PSTRIDE * cap);
+        CK(c, cudaMemcpy(oldb.data(), c->pbuf, oldb.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    std::vector<double> blk((size_t)PSTRIDE * ncap, 0.0);
+    for (auto &fk : FIELDS)
+        for (size_t e2 = 0; e2 < (size_t)fk[1] * old; e2++)
+            blk[(size_t)fk[0] * ncap + e2] = oldb[(size_t)fk[0] * cap + e2];
+    size_t cp = (size_t)ncap;
+    for (int k = 0; k < n; k++) {
+        int p = old + k;
+        double qn = std::sqrt(((quat[4 * k] * quat[4 * k] + quat[4 * k + 1] * quat[4 * k + 1]) +
+                               quat[4 * k + 2] * quat[4 * k + 2]) + quat[4 * k + 3] * quat[4 * k + 3]);
+        for (int j = 0; j < 3; j++) {
+            blk[OX * cp + 3 * p + j] = pos[3 * k + j];
+            blk[OV * cp + 3 * p + j] = vel ? vel[3 * k + j] : 0.0;
+            blk[OW * cp + 3 * p + j] = omega ? omega[3 * k + j] : 0.0;
+        }
+        for (int j = 0; j < 4; j++) blk[OQ * cp + 4 * p + j] = quat[4 * k + j] / qn;
+        double rp = r_par[k], ro = r_perp[k];
+        // reading: particle density 1; solid-ellipsoid inertia
+        double M = 4.0 / 3.0 * M_PI * rp * ro * ro;
+        blk[ORP * cp + p] = rp;
+        blk[ORO * cp + p] = ro;
+        blk[ODR * cp + p] = delta_rho[k];
+        blk[OM * cp + p] = M;
+        blk[OIP * cp + p] = 0.4 * M * ro * ro;
+        blk[OIQ * cp + p] = 0.2 * M * (rp * rp + ro * ro);
+    }
+    // placement does not move anything: old geometry = current geometry
+    for (int p = 0; p < np; p++) {
+        for (int j = 0; j < 3; j++) blk[OXO * cp + 3 * p + j] = blk[OX * cp + 3 * p + j];
+        for (int j = 0; j < 4; j++) blk[OQO * cp + 4 * p + j] = blk[OQ * cp + 4 * p + j];
+    }
+    std::vector<float> x32((size_t)3 * ncap, 0.f);
+    for (int p = 0; p < np; p++)
+        for (int j = 0; j < 3; j++) x32[3 * p + j] = (float)blk[OX * cp + 3 * p + j];
+    if (ncap != cap) {
+        double *nb = nullptr;
+        float *nx32 = nullptr;
+        CK(c, cudaMalloc((void **)&nb, blk.size() * sizeof(double)));
+        cudaError_t e = cudaMalloc((void **)&nx32, x32.size() * sizeof(float));
+        if (e != cudaSuccess) {
+            cudaFree(nb);
+            return cuda_fail(c, e, "add_particles: cudaMalloc");
+        }
+        if (c->pbuf) {
+            cudaFree(c->pbuf);
+            cudaFree(c->x32);
+            c->bytes -= (size_t)cap * (PSTRIDE * sizeof(double) + 3 * sizeof(float));
+        }
+        c->pbuf = nb;
+        c->x32 = nx32;
+        c->cap = ncap;
+        c->bytes += (size_t)ncap * (PSTRIDE * sizeof(double) + 3 * sizeof(float));
+    }
+    CK(c, cudaMemcpy(c->pbuf, blk.data(), blk.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->x32, x32.data(), x32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    c->np = np;
+    bind_parts(c);
+    drop_graphs(c);
+    cudaStream_t s = c->stream;
+    uint32_t *oo = c->owner[c->ocur], *on = c->owner[1 - c->ocur];
+    launch_claim(c->L, c->P, 0, on, s);
+    launch_transition(c->d.storage, c->L, c->P, c->f[c->cur], c->type, oo, on, 1, s);
+    launch_reset(c->L, c->P, 1, oo, s);
+    c->ocur = 1 - c->ocur;
+    return sync(c, "add_particles");
+}
+
+lbe_status lbe_step(lbe_ctx *c, int32_t nsteps)
+{
+    if (!c || nsteps < 0) return LBE_EINVAL;
+    if (nsteps == 0) return LBE_OK;
+    if (c->profiling) {
+        for (int k = 0; k < nsteps; k++) enqueue_step(c);
+        return check_async(c, "step");
+    }
+    int pairs = nsteps / 2;
+    if (pairs > 0) {
+        int key = c->cur * 2 + c->ocur;
+        if (!c->graph[key]) {
+            int cur0 = c->cur, ocur0 = c->ocur;
+            cudaGraph_t g;
+            CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+            enqueue_step(c);
+            enqueue_step(c);
+            cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+            c->cur = cur0;
+            c->ocur = ocur0;
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&c->graph[key], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+        }
+        for (int k = 0; k < pairs; k++) CK(c, cudaGraphLaunch(c->graph[key], c->stream));
+    }
+    if (nsteps & 1) enqueue_step(c);
+    return check_async(c, "step");
+}
+
+lbe_status lbe_read_fields(lbe_ctx *c, double *rho, double *vel, uint8_t *node_type)
+{
+    if (!c) return LBE_EINVAL;
+    cudaStream_t s = c->stream;
+    const Lat &L = c->L;
+    size_t N = (size_t)L.N;
+    launch_moments(c->d.storage, L, c->f[c->cur], c->type, c->rho, c->psi, s);
+    launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, s);
+    double *dr = nullptr, *dv = nullptr;
+    if (rho) CK(c, cudaMallocAsync((void **)&dr, 2 * N * sizeof(double), s));
+    if (vel) {
+        cudaError_t e = cudaMallocAsync((void **)&dv, 3 * N * sizeof(double), s);
+        if (e != cudaSuccess) {
+            if (dr) cudaFreeAsync(dr, s);
+            return cuda_fail(c, e, "cudaMallocAsync(vel)");
+        }
+    }
+    launch_fields(c->d.storage, L, c->f[c->cur], c->psi, c->type, dr, dv, s);
+    if (rho) cudaMemcpyAsync(rho, dr, 2 * N * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (vel) cudaMemcpyAsync(vel, dv, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (node_type) cudaMemcpyAsync(node_type, c->type, N, cudaMemcpyDeviceToHost, s);
+    if (dr) cudaFreeAsync(dr, s);
+    if (dv) cudaFreeAsync(dv, s);
+    return sync(c, "read_fields");
+}
+
+lbe_status lbe_read_particles(lbe_ctx *c, double *pos, double *quat, double *vel, double *omega,
+                              double *force, double *torque)
+{
+    if (!c) return LBE_EINVAL;
+    lbe_status st = sync(c, "read_particles");
+    if (st != LBE_OK || c->np == 0) return st;
+    size_t cp = (size_t)c->cap;
+    struct { double *dst; int off, k; } outs[] = {{pos, OX, 3}, {quat, OQ, 4}, {vel, OV, 3},
+                                                  {omega, OW, 3}, {force, OF, 3}, {torque, OT, 3}};
+    for (auto &o : outs)
+        if (o.dst)
+            CK(c, cudaMemcpy(o.dst, c->pbuf + (size_t)o.off * cp, (size_t)o.k * c->np * sizeof(double),
+                             cudaMemcpyDeviceToHost));
+    return LBE_OK;
+}
+
+lbe_status lbe_mass(lbe_ctx *c, double out[2])
+{
+    if (!c || !out) return LBE_EINVAL;
+    launch_mass(c->d.storage, c->L, c->f[c->cur], c->type, c->mass_partials, mass_blocks(), c->mass_out,
+                c->stream);
+    CK(c, cudaMemcpyAsync(out, c->mass_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    lbe_status st = sync(c, "mass");
+    if (st != LBE_OK) return st;
+    if (!std::isfinite(out[0]) || !std::isfinite(out[1]) || out[0] < 0 || out[1] < 0)
+        return fail(c, LBE_ENUMERIC, "mass: non-finite or negative density");
+    return LBE_OK;
+}
+
+lbe_status lbe_get_populations(lbe_ctx *c, double *f)
+{
+    if (!c || !f) return LBE_EINVAL;
+    size_t tot = (size_t)2 * Q * c->L.N;
+    double *d = nullptr;
+    CK(c, cudaMallocAsync((void **)&d, tot * sizeof(double), c->stream));
+    launch_get_f(c->d.storage, c->L, c->f[c->cur], d, c->stream);
+    cudaMemcpyAsync(f, d, tot * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(d, c->stream);
+    return sync(c, "get_populations");
+}
+
+lbe_status lbe_set_populations(lbe_ctx *c, const double *f)
+{
+    if (!c || !f) return LBE_EINVAL;
+    size_t tot = (size_t)2 * Q * c->L.N;
+    double *d = nullptr;
+    CK(c, cudaMallocAsync((void **)&d, tot * sizeof(double), c->stream));
+    cudaMemcpyAsync(d, f, tot * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    launch_set_f(c->d.storage, c->L, d, c->f[c->cur], c->stream);
+    cudaFreeAsync(d, c->stream);
+    return sync(c, "set_populations");
+}
+
+lbe_status lbe_profile_enable(lbe_ctx *c, int32_t enable)
+{
+    if (!c) return LBE_EINVAL;
+    lbe_status st = sync(c, "profile_enable");
+    if (st != LBE_OK) return st;
+    c->profiling = enable != 0;
+    c->ev_used = 0;
+    return LBE_OK;
+}
+
+lbe_status lbe_profile_read(lbe_ctx *c, double *ms_total, int64_t *launches)
+{
+    if (!c || !ms_total || !launches) return LBE_EINVAL;
+    lbe_status st = sync(c, "profile_read");
+    if (st != LBE_OK) return st;
+    double tot = 0.0;
+    for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+        float ms = 0.f;
+        CK(c, cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]));
+        tot += ms;
+    }
+    *ms_total = tot;
+    *launches = (int64_t)(c->ev_used / 2);
+    return LBE_OK;
+}
+
+int32_t lbe_kernels_per_step(const lbe_ctx *c)
+{
+    if (!c) return 0;
+    int k = 3;  // moments, shell, collide+stream
+    if (c->np > 0) {
+        k += 3;  // links, pairs, integrate
+        if (c->d.particle_mode != LBE_PARTICLES_STATIC) k += 3;  // claim, transition, reset
+    }
+    return k;
+}
+
+size_t lbe_device_bytes(const lbe_ctx *c) { return c ? c->bytes : 0; }
+
+const char *lbe_last_error(const lbe_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+void lbe_destroy(lbe_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// Internal declarations shared by the CUDA translation units of liblbe.
+// Method: §2 of Günther et al., arXiv:1109.3277 (two-component Shan–Chen
+// D3Q19 BGK lattice Boltzmann with rigid ellipsoids).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/lbe.h"
+
+namespace lbe {
+
+constexpr int Q = 19;
+constexpr uint8_t FLUID = 0, WALL = 1, PART = 2;
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+
+// D3Q19 velocity set (§2): rest, the 6 axis directions, the 12 face
+// diagonals; the opposite of direction i is i+1 for odd i and i-1 for even i.
+__host__ __device__ constexpr int cx(int i)
+{
+    constexpr int t[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[i];
+}
+__host__ __device__ constexpr int cy(int i)
+{
+    constexpr int t[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[i];
+}
+__host__ __device__ constexpr int cz(int i)
+{
+    constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[i];
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+__host__ __device__ constexpr float wgt(int i) { return i == 0 ? 1.f / 3.f : (i < 7 ? 1.f / 18.f : 1.f / 36.f); }
+__host__ __device__ constexpr double wgtd(int i) { return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+// Population storage.  FP32 stores f itself; the 16-bit modes store
+// δf = f - w_i ρ_ref^c (the offset from the rest equilibrium at ρ_ref).
+struct StF32 {
+    using T = float;
+    static __device__ __forceinline__ float ld(const T *p, float) { return __ldg(p); }
+    static __device__ __forceinline__ float ldc(const T *p, float) { return *p; }
+    static __device__ __forceinline__ void st(T *p, float v, float) { *p = v; }
+    static __device__ __forceinline__ float cvt(T v, float) { return v; }
+    static __device__ __forceinline__ T enc(float v, float) { return v; }
+};
+struct StF16 {
+    using T = __half;
+    static __device__ __forceinline__ float ld(const T *p, float b) { return b + __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ldc(const T *p, float b) { return b + __half2float(*p); }
+    static __device__ __forceinline__ void st(T *p, float v, float b) { *p = __float2half_rn(v - b); }
+    static __device__ __forceinline__ float cvt(T v, float b) { return b + __half2float(v); }
+    static __device__ __forceinline__ T enc(float v, float b) { return __float2half_rn(v - b); }
+};
+struct StBF16 {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float ld(const T *p, float b) { return b + __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ float ldc(const T *p, float b) { return b + __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(T *p, float v, float b) { *p = __float2bfloat16_rn(v - b); }
+    static __device__ __forceinline__ float cvt(T v, float b) { return b + __bfloat162float(v); }
+    static __device__ __forceinline__ T enc(float v, float b) { return __float2bfloat16_rn(v - b); }
+};
+
+// Lattice parameters passed by value to every kernel.
+struct Lat {
+    int nx, ny, nz, walls;
+    int N;                 // nodes (< 2^31)
+    float tau[2], itau[2];
+    float g;
+    float body[3];
+    float base[2][Q];      // w_i ρ_ref^c for the 16-bit modes, 0 for FP32
+    double rho_ref[2];
+};
+
+// Particle state on the device (structure of arrays, FP64).
+struct Parts {
+    int n;
+    double *X, *q, *V, *W;          // position [3n], quaternion [4n], velocity, ω (lab)
+    double *Xold, *qold;            // geometry before the last update
+    double *rp, *ro, *drho;         // radii, colour Δρ
+    double *M, *Ipar, *Iperp;       // mass and body-frame inertia
+    double *Flink, *Tlink;          // momentum exchange of the current step
+    double *Fpair, *Tpair;          // pair forces of the current step
+    double *Fpend, *Tpend;          // fill/empty momentum for the next update
+    double *F, *T;                  // total of the last update
+    float *X32;                     // FP32 copy of X for the pair prefilter
+};
+
+struct Pair {
+    double k_hertz, lub_cut, mu;
+    int mode;
+};
+
+// ---- launchers (fluid.cu) -------------------------------------------------
+void launch_init_f(int storage, const Lat &L, const double *rho0, void *f, const uint8_t *type,
+                   cudaStream_t s);
+void launch_moments(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho,
+                    float *psi, cudaStream_t s);
+void launch_shell(const Lat &L, const float *rho, float *psi, const uint8_t *type,
+                  const uint32_t *owner, const double *drho, cudaStream_t s);
+void launch_collide_stream(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
+                           const uint8_t *type, cudaStream_t s);
+void launch_fields(int storage, const Lat &L, const void *f, const float *psi, const uint8_t *type,
+                   double *rho_out, double *vel_out, cudaStream_t s);
+void launch_mass(int storage, const Lat &L, const void *f, const uint8_t *type, double *partials,
+                 int nblocks, double *out, cudaStream_t s);
+void launch_get_f(int storage, const Lat &L, const void *f, double *out, cudaStream_t s);
+void launch_set_f(int storage, const Lat &L, const double *in, void *f, cudaStream_t s);
+int mass_blocks();
+
+// ---- launchers (particles.cu) ---------------------------------------------
+void launch_links(int storage, const Lat &L, const Parts &P, void *fnew, const float *rho,
+                  const uint8_t *type, const uint32_t *owner, cudaStream_t s);
+void launch_pairs(const Lat &L, const Parts &P, const Pair &pp, cudaStream_t s);
+void launch_integrate(const Lat &L, const Parts &P, int mode, cudaStream_t s);
+void launch_claim(const Lat &L, const Parts &P, int first, uint32_t *owner_new, cudaStream_t s);
+void launch_transition(int storage, const Lat &L, const Parts &P, void *f, uint8_t *type,
+                       const uint32_t *owner_old, const uint32_t *owner_new, int placement,
+                       cudaStream_t s);
+void launch_reset(const Lat &L, const Parts &P, int use_old, uint32_t *owner, cudaStream_t s);
+
+}  // namespace lbe

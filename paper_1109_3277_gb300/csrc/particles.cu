@@ -1,0 +1,716 @@
+// Particle kernels (§2 of Günther et al., arXiv:1109.3277): moving
+// bounce-back correction and momentum exchange (Eq. 4-5), anisotropic
+// Hertz / Berne–Pechukas and lubrication pair forces (Eq. 6-9), the
+// Newton–Euler update, and the node coverage with fill and empty.
+//
+// Per-particle work runs one CTA per particle over the particle's bounding
+// box; per-particle sums are FP64 and reduced in a fixed order, so results
+// are bit-reproducible run to run.
+#include "lbe_internal.cuh"
+
+namespace lbe {
+
+namespace {
+
+constexpr int PT = 128;  // threads per per-particle CTA
+
+// ---------------------------------------------------------- geometry (FP64)
+// The inside test is written with explicit round-to-nearest intrinsics so
+// that no multiply-add is contracted: the quadric is evaluated in a fixed
+// operation order.
+
+__device__ __forceinline__ double m_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double a_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double s_(double a, double b) { return __dsub_rn(a, b); }
+
+__device__ void rotmat(const double *q, double R[3][3])
+{
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0][0] = s_(1.0, m_(2.0, a_(m_(y, y), m_(z, z))));
+    R[0][1] = m_(2.0, s_(m_(x, y), m_(w, z)));
+    R[0][2] = m_(2.0, a_(m_(x, z), m_(w, y)));
+    R[1][0] = m_(2.0, a_(m_(x, y), m_(w, z)));
+    R[1][1] = s_(1.0, m_(2.0, a_(m_(x, x), m_(z, z))));
+    R[1][2] = m_(2.0, s_(m_(y, z), m_(w, x)));
+    R[2][0] = m_(2.0, s_(m_(x, z), m_(w, y)));
+    R[2][1] = m_(2.0, a_(m_(y, z), m_(w, x)));
+    R[2][2] = s_(1.0, m_(2.0, a_(m_(x, x), m_(y, y))));
+}
+
+__device__ __forceinline__ bool periodic_dim(const Lat &L, int k) { return k < 2 || !L.walls; }
+__device__ __forceinline__ int ext_of(const Lat &L, int k) { return k == 0 ? L.nx : (k == 1 ? L.ny : L.nz); }
+
+// Displacement of node coordinate xi from particle coordinate X: nearest
+// periodic image, shifting the integer first and subtracting once.
+__device__ __forceinline__ double node_disp(const Lat &L, int k, int xi, double X)
+{
+    if (periodic_dim(L, k)) {
+        int n = ext_of(L, k);
+        double s = rint(__ddiv_rn(s_((double)xi, X), (double)n));
+        return s_((double)((long long)xi - (long long)s * n), X);
+    }
+    return s_((double)xi, X);
+}
+
+__device__ __forceinline__ double pair_disp(const Lat &L, int k, double a, double b)
+{
+    double r = s_(b, a);
+    if (periodic_dim(L, k)) {
+        double n = (double)ext_of(L, k);
+        r = s_(r, m_(n, rint(__ddiv_rn(r, n))));
+    }
+    return r;
+}
+
+struct Geo {
+    double R[3][3];
+    float R32[3][3];
+    double ip2, io2;
+    float ip2f, io2f;
+};
+
+__device__ void geo_of(const double *q, double rp, double ro, Geo &g)
+{
+    rotmat(q, g.R);
+    for (int a = 0; a < 3; a++)
+        for (int b = 0; b < 3; b++) g.R32[a][b] = (float)g.R[a][b];
+    g.ip2 = __ddiv_rn(1.0, m_(rp, rp));
+    g.io2 = __ddiv_rn(1.0, m_(ro, ro));
+    g.ip2f = (float)g.ip2;
+    g.io2f = (float)g.io2;
+}
+
+// Inside test: an FP32 evaluation decides unless it lies within 1e-3 of the
+// surface, where the exact FP64 evaluation (oracle operation order) decides.
+__device__ __forceinline__ bool inside(const Geo &g, const double dx[3])
+{
+    float d32[3];
+    float x0 = (float)dx[0], x1 = (float)dx[1], x2 = (float)dx[2];
+#pragma unroll
+    for (int k = 0; k < 3; k++) d32[k] = g.R32[0][k] * x0 + g.R32[1][k] * x1 + g.R32[2][k] * x2;
+    float q32 = d32[0] * d32[0] * g.ip2f + (d32[1] * d32[1] + d32[2] * d32[2]) * g.io2f;
+    if (q32 < 0.999f) return true;
+    if (q32 > 1.001f) return false;
+    double d[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+        d[k] = a_(a_(m_(g.R[0][k], dx[0]), m_(g.R[1][k], dx[1])), m_(g.R[2][k], dx[2]));
+    double qv = a_(a_(m_(m_(d[0], d[0]), g.ip2), m_(m_(d[1], d[1]), g.io2)), m_(m_(d[2], d[2]), g.io2));
+    return qv <= 1.0;
+}
+
+struct Box {
+    int lo[3], ext[3];
+    int count;
+};
+
+// Axis-aligned box containing the ellipsoid at X (not necessarily wrapped),
+// widened by one node; clamped to the lattice along walls and to one period.
+__device__ void box_of(const Lat &L, const double *X, const double R[3][3], double rp, double ro,
+                       int lo[3], int hi[3])
+{
+    for (int k = 0; k < 3; k++) {
+        double h = sqrt(rp * rp * R[k][0] * R[k][0] + ro * ro * (R[k][1] * R[k][1] + R[k][2] * R[k][2]));
+        lo[k] = (int)floor(X[k] - h) - 1;
+        hi[k] = (int)ceil(X[k] + h) + 1;
+    }
+}
+
+__device__ void finish_box(const Lat &L, int lo[3], int hi[3], Box &b)
+{
+    for (int k = 0; k < 3; k++) {
+        int n = ext_of(L, k);
+        if (!periodic_dim(L, k)) {
+            if (lo[k] < 0) lo[k] = 0;
+            if (hi[k] > n - 1) hi[k] = n - 1;
+        } else if (hi[k] - lo[k] + 1 > n) {
+            lo[k] = 0;
+            hi[k] = n - 1;
+        }
+        b.lo[k] = lo[k];
+        b.ext[k] = hi[k] >= lo[k] ? hi[k] - lo[k] + 1 : 0;
+    }
+    b.count = b.ext[0] * b.ext[1] * b.ext[2];
+}
+
+__device__ __forceinline__ int wrapi(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+__device__ __forceinline__ void box_node(const Lat &L, const Box &b, int k, int &x, int &y, int &z)
+{
+    int bx = k % b.ext[0];
+    int t = k / b.ext[0];
+    int by = t % b.ext[1];
+    int bz = t / b.ext[1];
+    x = wrapi(b.lo[0] + bx, L.nx);
+    y = wrapi(b.lo[1] + by, L.ny);
+    z = wrapi(b.lo[2] + bz, L.nz);
+}
+
+__device__ __forceinline__ bool is_wall_z(const Lat &L, int z) { return L.walls && (z == 0 || z == L.nz - 1); }
+
+// Fixed-order block reduction of K doubles (PT threads).
+template <int K>
+__device__ void block_sum(double (&v)[K], double (*sh)[PT / 32])
+{
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        double a = v[k];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if ((threadIdx.x & 31) == 0) sh[k][threadIdx.x >> 5] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            double a = 0.0;
+            for (int w = 0; w < PT / 32; w++) a += sh[k][w];
+            v[k] = a;
+        }
+    }
+}
+
+template <class S>
+__device__ __forceinline__ typename S::T *slot(typename S::T *f, const Lat &L, int c, int i)
+{
+    return f + (size_t)(c * Q + i) * (size_t)L.N;
+}
+
+__device__ __forceinline__ int nbr_node(const Lat &L, int x, int y, int z, int i)
+{
+    int xx = x + cx(i), yy = y + cy(i), zz = z + cz(i);
+    xx = xx < 0 ? xx + L.nx : (xx >= L.nx ? xx - L.nx : xx);
+    yy = yy < 0 ? yy + L.ny : (yy >= L.ny ? yy - L.ny : yy);
+    if (L.walls) {
+        if (zz < 0 || zz >= L.nz) return -1;
+    } else {
+        zz = zz < 0 ? zz + L.nz : (zz >= L.nz ? zz - L.nz : zz);
+    }
+    return xx + L.nx * (yy + L.ny * zz);
+}
+
+// ------------------------------------------------------------ links
+// For every link between a solid node x of particle p and a fluid node
+// y = x + c_i: the population leaving y towards x was reflected into slot i
+// of y by the streaming kernel (f*_ī(y)); add C = 6 w_i ρ^c(y) u_surf·c_i
+// with u_surf = V + ω × r_b at the link midpoint (Eq. 4), and give the
+// particle F = (2 f*_ī + C) c_ī and r_b × F (Eq. 5).
+
+template <class S>
+__global__ void __launch_bounds__(PT) k_links(Lat L, Parts P, typename S::T *__restrict__ fnew,
+                                              const float *__restrict__ rho,
+                                              const uint8_t *__restrict__ type,
+                                              const uint32_t *__restrict__ owner)
+{
+    const int p = blockIdx.x;
+    __shared__ Box box;
+    __shared__ double sX[3];
+    __shared__ float sV[3], sW[3];
+    __shared__ double red[6][PT / 32];
+    if (threadIdx.x == 0) {
+        double R[3][3];
+        rotmat(P.q + 4 * p, R);
+        int lo[3], hi[3];
+        box_of(L, P.X + 3 * p, R, P.rp[p], P.ro[p], lo, hi);
+        finish_box(L, lo, hi, box);
+        for (int k = 0; k < 3; k++) {
+            sX[k] = P.X[3 * p + k];
+            sV[k] = (float)P.V[3 * p + k];
+            sW[k] = (float)P.W[3 * p + k];
+        }
+    }
+    __syncthreads();
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = threadIdx.x; k < box.count; k += PT) {
+        int x, y, z;
+        box_node(L, box, k, x, y, z);
+        int n = x + L.nx * (y + L.ny * z);
+        if (owner[n] != (uint32_t)p) continue;
+        float dn[3] = {(float)node_disp(L, 0, x, sX[0]), (float)node_disp(L, 1, y, sX[1]),
+                       (float)node_disp(L, 2, z, sX[2])};
+        float aF[3] = {0.f, 0.f, 0.f}, aT[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 1; i < Q; i++) {
+            int m = nbr_node(L, x, y, z, i);
+            if (m < 0 || type[m] != FLUID) continue;
+            float rb[3] = {dn[0] + 0.5f * cx(i), dn[1] + 0.5f * cy(i), dn[2] + 0.5f * cz(i)};
+            float us[3] = {sV[0] + sW[1] * rb[2] - sW[2] * rb[1], sV[1] + sW[2] * rb[0] - sW[0] * rb[2],
+                           sV[2] + sW[0] * rb[1] - sW[1] * rb[0]};
+            float uc = us[0] * cx(i) + us[1] * cy(i) + us[2] * cz(i);
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                typename S::T *sl = slot<S>(fnew, L, c, i) + m;
+                float fr = S::ldc(sl, L.base[c][i]);
+                float C = 6.f * wgt(i) * rho[(size_t)c * L.N + m] * uc;
+                S::st(sl, fr + C, L.base[c][i]);
+                float a = -(2.f * fr + C);  // F = (2 f* + C) c_ī, c_ī = -c_i
+                float F[3] = {a * cx(i), a * cy(i), a * cz(i)};
+                aF[0] += F[0];
+                aF[1] += F[1];
+                aF[2] += F[2];
+                aT[0] += rb[1] * F[2] - rb[2] * F[1];
+                aT[1] += rb[2] * F[0] - rb[0] * F[2];
+                aT[2] += rb[0] * F[1] - rb[1] * F[0];
+            }
+        }
+        for (int k2 = 0; k2 < 3; k2++) {
+            acc[k2] += (double)aF[k2];
+            acc[3 + k2] += (double)aT[k2];
+        }
+    }
+    block_sum<6>(acc, red);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; k++) {
+            P.Flink[3 * p + k] = acc[k];
+            P.Tlink[3 * p + k] = acc[3 + k];
+        }
+    }
+}
+
+// --------------------------------------------------------- pair forces
+
+__device__ __forceinline__ double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+__device__ __forceinline__ void cross3(const double *a, const double *b, double *o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Anisotropic Hertz interaction (Eq. 6-8): φ = ε(ô_i,ô_j) (1 - r/σ)^{5/2}
+// for r < σ with ε = ε̄ / sqrt(1 - χ^2 (ô_i·ô_j)^2), ε̄ = K_H σ̄^{5/2},
+// σ̄ = 2 r_perp, and the Berne–Pechukas σ(ô_i, ô_j, r̂).  Returns σ; fills
+// the force on j and the torques on i and j (minus the analytic gradients).
+__device__ double hertz_bp(double K, double rp, double ro, const double r[3], const double oi[3],
+                           const double oj[3], double fj[3], double ti[3], double tj[3])
+{
+    for (int k = 0; k < 3; k++) fj[k] = ti[k] = tj[k] = 0.0;
+    double chi = (rp * rp - ro * ro) / (rp * rp + ro * ro);
+    double sbar = 2.0 * ro;
+    double rl = sqrt(dot3(r, r));
+    if (!(rl > 0)) return sbar;
+    double rh[3] = {r[0] / rl, r[1] / rl, r[2] / rl};
+    double a = dot3(rh, oi), b = dot3(rh, oj), c = dot3(oi, oj);
+    double ep = 1.0 + chi * c, em = 1.0 - chi * c;
+    double S = (a + b) * (a + b) / ep + (a - b) * (a - b) / em;
+    double D = 1.0 - 0.5 * chi * S;
+    double sigma = sbar / sqrt(D);
+    double s = rl / sigma;
+    if (s >= 1.0) return sigma;
+    double ebar = K * sbar * sbar * sqrt(sbar);
+    double Ed = 1.0 - chi * chi * c * c;
+    double eps = ebar / sqrt(Ed);
+    double om = 1.0 - s;
+    double phit = om * om * sqrt(om);
+    double dphit = -2.5 * om * sqrt(om);
+    double dsig_dS = 0.25 * chi * sbar / (D * sqrt(D));
+    double dS_da = 2.0 * (a + b) / ep + 2.0 * (a - b) / em;
+    double dS_db = 2.0 * (a + b) / ep - 2.0 * (a - b) / em;
+    double dS_dc = -chi * (a + b) * (a + b) / (ep * ep) + chi * (a - b) * (a - b) / (em * em);
+    double deps_dc = ebar * chi * chi * c / (Ed * sqrt(Ed));
+    double gs = eps * dphit * (-rl / (sigma * sigma)) * dsig_dS;
+    double dphi_drl = eps * dphit / sigma;
+    double gi[3], gj[3];
+    for (int k = 0; k < 3; k++) {
+        double grad = dphi_drl * rh[k] + gs * (dS_da * (oi[k] - a * rh[k]) / rl + dS_db * (oj[k] - b * rh[k]) / rl);
+        fj[k] = -grad;
+        gi[k] = phit * deps_dc * oj[k] + gs * (dS_da * rh[k] + dS_dc * oj[k]);
+        gj[k] = phit * deps_dc * oi[k] + gs * (dS_db * rh[k] + dS_dc * oi[k]);
+    }
+    double u[3];
+    cross3(oi, gi, u);
+    for (int k = 0; k < 3; k++) ti[k] = -u[k];
+    cross3(oj, gj, u);
+    for (int k = 0; k < 3; k++) tj[k] = -u[k];
+    return sigma;
+}
+
+// One thread per particle i sums the Hertz and lubrication (Eq. 9 with 2R
+// -> σ, R^2 -> (σ/2)^2, only for gaps 0 < r - σ < Δc, opposing the normal
+// approach) contributions of every other particle in index order; an FP32
+// distance test skips pairs beyond reach.
+__global__ void k_pairs(Lat L, Parts P, Pair pp)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    double Xi[3] = {P.X[3 * i], P.X[3 * i + 1], P.X[3 * i + 2]};
+    float xi32[3] = {P.X32[3 * i], P.X32[3 * i + 1], P.X32[3 * i + 2]};
+    double Ri[3][3];
+    rotmat(P.q + 4 * i, Ri);
+    double oi[3] = {Ri[0][0], Ri[1][0], Ri[2][0]};
+    double rpi = P.rp[i], roi = P.ro[i];
+    float reach_i = (float)fmax(rpi, roi);
+    float nlat[3] = {(float)L.nx, (float)L.ny, (float)L.nz};
+    double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+    for (int j = 0; j < P.n; j++) {
+        if (j == i) continue;
+        float d2 = 0.f;
+        for (int k = 0; k < 3; k++) {
+            float d = P.X32[3 * j + k] - xi32[k];
+            if (k < 2 || !L.walls) d -= nlat[k] * rintf(d / nlat[k]);
+            d2 += d * d;
+        }
+        float reach = reach_i + (float)fmax(P.rp[j], P.ro[j]) + (float)pp.lub_cut + 0.01f;
+        if (d2 > reach * reach) continue;
+        int a = i < j ? i : j, b = i < j ? j : i;  // pair taken as (a, b), a < b
+        double r[3];
+        for (int k = 0; k < 3; k++) r[k] = pair_disp(L, k, P.X[3 * a + k], P.X[3 * b + k]);
+        double Rj[3][3];
+        rotmat(P.q + 4 * j, Rj);
+        double oj[3] = {Rj[0][0], Rj[1][0], Rj[2][0]};
+        const double *oa = i < j ? oi : oj, *ob = i < j ? oj : oi;
+        double rp = 0.5 * (P.rp[a] + P.rp[b]), ro = 0.5 * (P.ro[a] + P.ro[b]);
+        double fb[3], ta[3], tb[3];
+        double sigma = hertz_bp(pp.k_hertz, rp, ro, r, oa, ob, fb, ta, tb);
+        for (int k = 0; k < 3; k++) {
+            F[k] += i == b ? fb[k] : -fb[k];
+            T[k] += i == a ? ta[k] : tb[k];
+        }
+        double rl = sqrt(dot3(r, r));
+        double h = rl - sigma;
+        if (pp.lub_cut > 0 && h > 0 && h < pp.lub_cut) {
+            double rh[3] = {r[0] / rl, r[1] / rl, r[2] / rl};
+            double du[3] = {P.V[3 * a] - P.V[3 * b], P.V[3 * a + 1] - P.V[3 * b + 1],
+                            P.V[3 * a + 2] - P.V[3 * b + 2]};
+            double K = 3.0 * M_PI * pp.mu * sigma * sigma / 8.0;
+            double s = K * dot3(rh, du) * (1.0 / h - 1.0 / pp.lub_cut);
+            for (int k = 0; k < 3; k++) F[k] += i == a ? -s * rh[k] : s * rh[k];
+        }
+    }
+    for (int k = 0; k < 3; k++) {
+        P.Fpair[3 * i + k] = F[k];
+        P.Tpair[3 * i + k] = T[k];
+    }
+}
+
+// ------------------------------------------------------------ integrate
+// Leapfrog translation (V += F/M, X += V), explicit Euler of the body-frame
+// Euler equations, q <- normalise(q ⊗ exp(ω_body/2)).  The total force is
+// momentum exchange + pair forces + the fill/empty momentum of the last
+// coverage update.
+
+__device__ void qmul(const double a[4], const double b[4], double o[4])
+{
+    o[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    o[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    o[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    o[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+__device__ void rotate_by_body_omega(double q[4], const double wb[3])
+{
+    double h[3] = {0.5 * wb[0], 0.5 * wb[1], 0.5 * wb[2]};
+    double hn = sqrt(dot3(h, h));
+    double dq[4] = {1.0, 0.0, 0.0, 0.0};
+    if (hn > 0) {
+        double s = sin(hn) / hn;
+        dq[0] = cos(hn);
+        dq[1] = s * h[0];
+        dq[2] = s * h[1];
+        dq[3] = s * h[2];
+    }
+    double qn[4];
+    qmul(q, dq, qn);
+    double nn = sqrt(qn[0] * qn[0] + qn[1] * qn[1] + qn[2] * qn[2] + qn[3] * qn[3]);
+    for (int k = 0; k < 4; k++) q[k] = qn[k] / nn;
+}
+
+__global__ void k_integrate(Lat L, Parts P, int mode)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P.n) return;
+    double F[3], T[3];
+    for (int k = 0; k < 3; k++) {
+        F[k] = P.Flink[3 * p + k] + P.Fpair[3 * p + k] + P.Fpend[3 * p + k];
+        T[k] = P.Tlink[3 * p + k] + P.Tpair[3 * p + k] + P.Tpend[3 * p + k];
+        P.F[3 * p + k] = F[k];
+        P.T[3 * p + k] = T[k];
+        P.Fpend[3 * p + k] = 0.0;
+        P.Tpend[3 * p + k] = 0.0;
+        P.Xold[3 * p + k] = P.X[3 * p + k];
+    }
+    double q[4];
+    for (int k = 0; k < 4; k++) q[k] = P.qold[4 * p + k] = P.q[4 * p + k];
+    if (mode == LBE_PARTICLES_STATIC) return;
+    double X[3], V[3], W[3];
+    for (int k = 0; k < 3; k++) {
+        X[k] = P.X[3 * p + k];
+        V[k] = P.V[3 * p + k];
+        W[k] = P.W[3 * p + k];
+    }
+    double R[3][3];
+    rotmat(q, R);
+    double wb[3];
+    for (int k = 0; k < 3; k++) wb[k] = R[0][k] * W[0] + R[1][k] * W[1] + R[2][k] * W[2];
+    if (mode == LBE_PARTICLES_PRESCRIBED) {
+        for (int k = 0; k < 3; k++) X[k] += V[k];
+        rotate_by_body_omega(q, wb);
+    } else {
+        double M = P.M[p];
+        for (int k = 0; k < 3; k++) {
+            V[k] += F[k] / M;
+            X[k] += V[k];
+        }
+        double tb[3];
+        for (int k = 0; k < 3; k++) tb[k] = R[0][k] * T[0] + R[1][k] * T[1] + R[2][k] * T[2];
+        double I[3] = {P.Ipar[p], P.Iperp[p], P.Iperp[p]};
+        double Lb[3] = {I[0] * wb[0], I[1] * wb[1], I[2] * wb[2]};
+        double wl[3];
+        cross3(wb, Lb, wl);
+        for (int k = 0; k < 3; k++) wb[k] += (tb[k] - wl[k]) / I[k];
+        rotate_by_body_omega(q, wb);
+        rotmat(q, R);
+        for (int k = 0; k < 3; k++) W[k] = R[k][0] * wb[0] + R[k][1] * wb[1] + R[k][2] * wb[2];
+    }
+    for (int k = 0; k < 3; k++) {
+        if (periodic_dim(L, k)) {
+            double n = (double)ext_of(L, k);
+            if (X[k] < 0) X[k] += n;
+            if (X[k] >= n) X[k] -= n;
+        }
+        P.X[3 * p + k] = X[k];
+        P.X32[3 * p + k] = (float)X[k];
+        P.V[3 * p + k] = V[k];
+        P.W[3 * p + k] = W[k];
+    }
+    for (int k = 0; k < 4; k++) P.q[4 * p + k] = q[k];
+}
+
+// ---------------------------------------------------------------- claim
+// Every non-wall node inside a particle is claimed with atomicMin, so a
+// node inside several particles goes to the lowest index.
+
+__global__ void __launch_bounds__(PT) k_claim(Lat L, Parts P, uint32_t *__restrict__ owner_new)
+{
+    const int p = blockIdx.x;
+    __shared__ Box box;
+    __shared__ Geo geo;
+    __shared__ double sX[3];
+    if (threadIdx.x == 0) {
+        geo_of(P.q + 4 * p, P.rp[p], P.ro[p], geo);
+        int lo[3], hi[3];
+        box_of(L, P.X + 3 * p, geo.R, P.rp[p], P.ro[p], lo, hi);
+        finish_box(L, lo, hi, box);
+        for (int k = 0; k < 3; k++) sX[k] = P.X[3 * p + k];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < box.count; k += PT) {
+        int x, y, z;
+        box_node(L, box, k, x, y, z);
+        if (is_wall_z(L, z)) continue;
+        double dx[3] = {node_disp(L, 0, x, sX[0]), node_disp(L, 1, y, sX[1]), node_disp(L, 2, z, sX[2])};
+        if (inside(geo, dx)) atomicMin(owner_new + (x + L.nx * (y + L.ny * z)), (uint32_t)p);
+    }
+}
+
+// ------------------------------------------------------------ transition
+// Compare the old and new ownership.  A node whose owner changed is handled
+// by exactly one CTA: that of the lower of its old and new owner.
+//  - newly covered: its fluid (mass and momentum Σ f c) goes to the particle;
+//  - newly uncovered: f = f^eq(ρ̄^c, u_surf) with ρ̄^c the mean over
+//    neighbours fluid before and after (ρ_ref if none); the particle loses
+//    that momentum;  both through the pending force/torque.
+// With placement != 0 (particles just added) nodes only change type.
+
+template <class S>
+__global__ void __launch_bounds__(PT) k_transition(Lat L, Parts P, typename S::T *__restrict__ f,
+                                                   uint8_t *__restrict__ type,
+                                                   const uint32_t *__restrict__ own_old,
+                                                   const uint32_t *__restrict__ own_new,
+                                                   int placement)
+{
+    const int p = blockIdx.x;
+    __shared__ Box box;
+    __shared__ double sX[3], sV[3], sW[3];
+    __shared__ double red[6][PT / 32];
+    if (threadIdx.x == 0) {
+        double Ro[3][3], Rn[3][3];
+        rotmat(P.qold + 4 * p, Ro);
+        rotmat(P.q + 4 * p, Rn);
+        double Xo[3], Xu[3];
+        for (int k = 0; k < 3; k++) {
+            Xo[k] = P.Xold[3 * p + k];
+            Xu[k] = Xo[k] + pair_disp(L, k, Xo[k], P.X[3 * p + k]);
+        }
+        int lo[3], hi[3], lo2[3], hi2[3];
+        box_of(L, Xo, Ro, P.rp[p], P.ro[p], lo, hi);
+        box_of(L, Xu, Rn, P.rp[p], P.ro[p], lo2, hi2);
+        for (int k = 0; k < 3; k++) {
+            lo[k] = min(lo[k], lo2[k]);
+            hi[k] = max(hi[k], hi2[k]);
+        }
+        finish_box(L, lo, hi, box);
+        for (int k = 0; k < 3; k++) {
+            sX[k] = P.X[3 * p + k];
+            sV[k] = P.V[3 * p + k];
+            sW[k] = P.W[3 * p + k];
+        }
+    }
+    __syncthreads();
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = threadIdx.x; k < box.count; k += PT) {
+        int x, y, z;
+        box_node(L, box, k, x, y, z);
+        int n = x + L.nx * (y + L.ny * z);
+        uint32_t o = own_old[n], w = own_new[n];
+        if (o == w) continue;
+        if (min(o, w) != (uint32_t)p) continue;
+        if (o == NONE) {
+            type[n] = PART;
+            if (placement) continue;
+            double mom[3] = {0, 0, 0};
+#pragma unroll
+            for (int c = 0; c < 2; c++)
+#pragma unroll
+                for (int i = 0; i < Q; i++) {
+                    float v = S::ldc(slot<S>(f, L, c, i) + n, L.base[c][i]);
+                    if (cx(i)) mom[0] += cx(i) * (double)v;
+                    if (cy(i)) mom[1] += cy(i) * (double)v;
+                    if (cz(i)) mom[2] += cz(i) * (double)v;
+                }
+            double r[3] = {node_disp(L, 0, x, sX[0]), node_disp(L, 1, y, sX[1]), node_disp(L, 2, z, sX[2])};
+            double t[3];
+            cross3(r, mom, t);
+            for (int k2 = 0; k2 < 3; k2++) {
+                acc[k2] += mom[k2];
+                acc[3 + k2] += t[k2];
+            }
+        } else if (w == NONE) {
+            type[n] = FLUID;
+            if (placement) continue;
+            float sr0 = 0.f, sr1 = 0.f;
+            int cnt = 0;
+            for (int i = 1; i < Q; i++) {
+                int m = nbr_node(L, x, y, z, i);
+                if (m < 0) continue;
+                int mz = m / (L.nx * L.ny);
+                if (is_wall_z(L, mz) || own_old[m] != NONE || own_new[m] != NONE) continue;
+                float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                for (int j = 0; j < Q; j++) {
+                    a0 += S::ldc(slot<S>(f, L, 0, j) + m, L.base[0][j]);
+                    a1 += S::ldc(slot<S>(f, L, 1, j) + m, L.base[1][j]);
+                }
+                sr0 += a0;
+                sr1 += a1;
+                cnt++;
+            }
+            float rb0 = cnt ? sr0 / cnt : (float)L.rho_ref[0];
+            float rb1 = cnt ? sr1 / cnt : (float)L.rho_ref[1];
+            double r[3] = {node_disp(L, 0, x, sX[0]), node_disp(L, 1, y, sX[1]), node_disp(L, 2, z, sX[2])};
+            float us[3] = {(float)(sV[0] + sW[1] * r[2] - sW[2] * r[1]),
+                           (float)(sV[1] + sW[2] * r[0] - sW[0] * r[2]),
+                           (float)(sV[2] + sW[0] * r[1] - sW[1] * r[0])};
+            float uu = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
+            double mom[3] = {0, 0, 0};
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                float rc = c ? rb1 : rb0;
+#pragma unroll
+                for (int i = 0; i < Q; i++) {
+                    float cu = cx(i) * us[0] + cy(i) * us[1] + cz(i) * us[2];
+                    float fe = wgt(i) * rc * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
+                    S::st(slot<S>(f, L, c, i) + n, fe, L.base[c][i]);
+                    if (cx(i)) mom[0] += cx(i) * (double)fe;
+                    if (cy(i)) mom[1] += cy(i) * (double)fe;
+                    if (cz(i)) mom[2] += cz(i) * (double)fe;
+                }
+            }
+            double t[3];
+            cross3(r, mom, t);
+            for (int k2 = 0; k2 < 3; k2++) {
+                acc[k2] -= mom[k2];
+                acc[3 + k2] -= t[k2];
+            }
+        }
+    }
+    if (placement) return;
+    block_sum<6>(acc, red);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; k++) {
+            P.Fpend[3 * p + k] = acc[k];
+            P.Tpend[3 * p + k] = acc[3 + k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- reset
+// Clear an ownership map over every particle's box (old geometry when
+// use_old), so the map is all NONE again for the next claim.
+
+__global__ void __launch_bounds__(PT) k_reset(Lat L, Parts P, int use_old, uint32_t *__restrict__ owner)
+{
+    const int p = blockIdx.x;
+    __shared__ Box box;
+    if (threadIdx.x == 0) {
+        const double *q = use_old ? P.qold + 4 * p : P.q + 4 * p;
+        const double *X = use_old ? P.Xold + 3 * p : P.X + 3 * p;
+        double R[3][3];
+        rotmat(q, R);
+        int lo[3], hi[3];
+        box_of(L, X, R, P.rp[p], P.ro[p], lo, hi);
+        finish_box(L, lo, hi, box);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < box.count; k += PT) {
+        int x, y, z;
+        box_node(L, box, k, x, y, z);
+        owner[x + L.nx * (y + L.ny * z)] = NONE;
+    }
+}
+
+}  // namespace
+
+#define LBE_DISPATCH(storage, CALL)                                   \
+    do {                                                              \
+        switch (storage) {                                            \
+        case LBE_STORE_F16_OFS: { using S = StF16; CALL; } break;     \
+        case LBE_STORE_BF16_OFS: { using S = StBF16; CALL; } break;   \
+        default: { using S = StF32; CALL; } break;                    \
+        }                                                             \
+    } while (0)
+
+void launch_links(int storage, const Lat &L, const Parts &P, void *fnew, const float *rho,
+                  const uint8_t *type, const uint32_t *owner, cudaStream_t s)
+{
+    if (P.n == 0) return;
+    LBE_DISPATCH(storage, (k_links<S><<<P.n, PT, 0, s>>>(L, P, (typename S::T *)fnew, rho, type, owner)));
+}
+
+void launch_pairs(const Lat &L, const Parts &P, const Pair &pp, cudaStream_t s)
+{
+    if (P.n == 0) return;
+    k_pairs<<<(P.n + 127) / 128, 128, 0, s>>>(L, P, pp);
+}
+
+void launch_integrate(const Lat &L, const Parts &P, int mode, cudaStream_t s)
+{
+    if (P.n == 0) return;
+    k_integrate<<<(P.n + 127) / 128, 128, 0, s>>>(L, P, mode);
+}
+
+void launch_claim(const Lat &L, const Parts &P, int, uint32_t *owner_new, cudaStream_t s)
+{
+    if (P.n == 0) return;
+    k_claim<<<P.n, PT, 0, s>>>(L, P, owner_new);
+}
+
+void launch_transition(int storage, const Lat &L, const Parts &P, void *f, uint8_t *type,
+                       const uint32_t *owner_old, const uint32_t *owner_new, int placement,
+                       cudaStream_t s)
+{
+    if (P.n == 0) return;
+    LBE_DISPATCH(storage, (k_transition<S><<<P.n, PT, 0, s>>>(L, P, (typename S::T *)f, type, owner_old,
+                                                               owner_new, placement)));
+}
+
+void launch_reset(const Lat &L, const Parts &P, int use_old, uint32_t *owner, cudaStream_t s)
+{
+    if (P.n == 0) return;
+    k_reset<<<P.n, PT, 0, s>>>(L, P, use_old, owner);
+}
+
+}  // namespace lbe

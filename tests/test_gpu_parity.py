@@ -1,0 +1,218 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP32 storage and arithmetic against FP64.  One step from random
+populations agrees to 2e-6 absolute on populations of order 0.03 (a few FP32
+ulps of the largest intermediate); densities after many steps to 1e-5, the
+bound of the FP32 path after 200 steps; particle position and orientation to
+1e-5 lattice units."""
+import numpy as np
+import pytest
+
+from oracle import lbref
+from paper_1109_3277_gb300 import lbe
+from paper_1109_3277_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_F_ONE_STEP = 2e-6
+TOL_RHO = 1e-5
+TOL_PART = 1e-5
+
+
+def _pair(shape, rho0, **params):
+    mode = params.pop("particle_mode", "free")
+    g = lbe.Lattice(shape, rho0, particle_mode=mode, **params)
+    r = lbref.Lattice(shape, rho0, particle_mode=lbe.MODES[mode], **params)
+    return g, r
+
+
+def _add(g, r, **p):
+    for L in (g, r):
+        L.add_particles(p["pos"], p["quat"], p["r_par"], p["r_perp"], p["delta_rho"],
+                        vel=p.get("vel"), omega=p.get("omega"))
+
+
+@pytest.mark.parametrize("shape,walls,tau", [((8, 8, 8), False, (1.0, 1.0)),
+                                             ((13, 7, 5), True, (0.8, 1.3)),
+                                             ((33, 17, 9), False, (1.0, 0.7))])
+def test_one_step_populations(shape, walls, tau):
+    """Several tiles plus a ragged tail, walls or not, τ ≠ 1."""
+    nx, ny, nz = shape
+    f0 = W.random_populations(shape, seed=21)
+    g, r = _pair(shape, np.full((2, nz, ny, nx), 0.5), walls_z=walls, tau=tau, g_br=0.1,
+                 body_force=(1e-4, 0.0, -2e-4))
+    g.set_populations(f0)
+    r.set_populations(f0)
+    g.step(1)
+    r.step(1)
+    _, _, typ = r.read_fields()
+    fl = typ == 0
+    fg, fr = g.get_populations(), r.get_populations()
+    assert np.max(np.abs(fg[:, :, fl] - fr[:, :, fl])) < TOL_F_ONE_STEP
+
+
+def test_spinodal_densities_many_steps():
+    shape = (24, 20, 16)
+    rho0 = W.uniform_mixture(shape, 0.7, 0.01, seed=22)
+    g, r = _pair(shape, rho0, g_br=0.1)
+    g.step(60)
+    r.step(60)
+    rg, vg, _ = g.read_fields()
+    rr, vr, _ = r.read_fields()
+    assert np.max(np.abs(rg - rr)) < TOL_RHO
+    assert np.max(np.abs(vg - vr)) < TOL_RHO
+
+
+def test_static_particle_one_step():
+    shape = (12, 11, 10)
+    f0 = W.random_populations(shape, seed=23)
+    g, r = _pair(shape, np.full((2, 10, 11, 12), 0.5), walls_z=True, g_br=0.1,
+                 particle_mode="static")
+    _add(g, r, pos=[[5.6, 5.2, 4.9]], quat=[W.axis_tilt_quaternion(0.6, 0.3)], r_par=3.6,
+         r_perp=2.1, delta_rho=-0.15, vel=[[0.01, -0.02, 0.005]], omega=[[0.003, 0.002, -0.004]])
+    _, _, tg = g.read_fields()
+    _, _, tr = r.read_fields()
+    assert np.array_equal(tg, tr)
+    g.set_populations(f0)
+    r.set_populations(f0)
+    g.step(1)
+    r.step(1)
+    fl = tr == 0
+    fg, fr = g.get_populations(), r.get_populations()
+    assert np.max(np.abs(fg[:, :, fl] - fr[:, :, fl])) < TOL_F_ONE_STEP
+    pg, pr = g.read_particles(), r.read_particles()
+    scale = max(1.0, np.abs(pr["force"]).max())
+    assert np.max(np.abs(pg["force"] - pr["force"])) < 1e-5 * scale
+    assert np.max(np.abs(pg["torque"] - pr["torque"])) < 1e-5 * max(1.0, np.abs(pr["torque"]).max())
+
+
+def test_prescribed_motion_fill_empty():
+    """A particle driven through the lattice: coverage changes every few
+    steps, exercising fill and empty."""
+    shape = (24, 20, 20)
+    rho0 = W.flat_interface(shape, 10, 0.7, 0.04, 1e-3, seed=24)
+    g, r = _pair(shape, rho0, walls_z=True, g_br=0.1, particle_mode="prescribed")
+    _add(g, r, pos=[[8.2, 9.7, 10.3]], quat=[W.axis_tilt_quaternion(0.7, 0.2)], r_par=5.0,
+         r_perp=2.5, delta_rho=0.1, vel=[[0.06, 0.01, -0.02]], omega=[[0.0, 0.01, 0.004]])
+    for _ in range(4):
+        g.step(10)
+        r.step(10)
+        rg, _, tg = g.read_fields()
+        rr, _, tr = r.read_fields()
+        assert np.array_equal(tg, tr)
+        assert np.max(np.abs(rg - rr)) < TOL_RHO
+    pg, pr = g.read_particles(), r.read_particles()
+    assert np.max(np.abs(pg["pos"] - pr["pos"])) < 1e-9
+    assert np.max(np.abs(pg["force"] - pr["force"])) < 1e-4 * max(1.0, np.abs(pr["force"]).max())
+
+
+def test_adsorption_box_200_steps():
+    """The 32x32x48 adsorption box with one free prolate ellipsoid (r_par 6,
+    r_perp 3) tilted 45 degrees on the interface, 200 steps: densities within
+    1e-5, particle position and orientation within 1e-5."""
+    w = W.adsorption_box()
+    g, r = _pair(w.shape, w.rho0, **w.params)
+    p = w.particles
+    _add(g, r, **p)
+    g.step(w.steps)
+    r.step(w.steps)
+    rg, _, tg = g.read_fields()
+    rr, _, tr = r.read_fields()
+    both = (tg == 0) & (tr == 0)
+    assert (tg != tr).sum() == 0
+    assert np.max(np.abs(rg[:, both] - rr[:, both])) < TOL_RHO
+    pg, pr = g.read_particles(), r.read_particles()
+    assert np.max(np.abs(pg["pos"] - pr["pos"])) < TOL_PART
+    qg, qr = pg["quat"] * np.sign(pg["quat"][:, :1]), pr["quat"] * np.sign(pr["quat"][:, :1])
+    assert np.max(np.abs(qg - qr)) < TOL_PART
+    # the particle did move
+    assert np.linalg.norm(pr["pos"][0] - p["pos"][0]) > 1e-3
+
+
+def test_free_particles_pair_forces():
+    """Several free ellipsoids placed so that Hertz overlap and lubrication
+    gaps occur, periodic box."""
+    shape = (36, 30, 28)
+    rho0 = W.random_phases(shape, 0.5, seed=25)
+    g, r = _pair(shape, rho0, g_br=0.1)
+    pos = [[10.0, 10.0, 10.0], [10.0, 10.0, 17.6], [19.5, 10.5, 10.0], [30.0, 25.0, 3.0],
+           [1.0, 25.5, 2.5]]
+    quats = [W.axis_tilt_quaternion(0.0), W.axis_tilt_quaternion(0.1, 0.5),
+             W.axis_tilt_quaternion(np.pi / 2, 0.0), W.axis_tilt_quaternion(1.0, 2.0),
+             W.axis_tilt_quaternion(0.4, 1.0)]
+    _add(g, r, pos=pos, quat=quats, r_par=4.0, r_perp=2.0, delta_rho=[0.0, 0.1, -0.1, 0.05, 0.0],
+         vel=[[0.0, 0.0, 0.01], [0.0, 0.0, -0.01], [-0.005, 0, 0], [0.002, 0.001, 0.0],
+              [0.0, 0.0, 0.0]])
+    g.step(1)
+    r.step(1)
+    pg, pr = g.read_particles(), r.read_particles()
+    scale = np.abs(pr["force"]).max()
+    assert scale > 1.0  # Hertz overlap is active
+    assert np.max(np.abs(pg["force"] - pr["force"])) < 1e-5 * scale
+    g.step(49)
+    r.step(49)
+    pg, pr = g.read_particles(), r.read_particles()
+    assert np.max(np.abs(pg["pos"] - pr["pos"])) < TOL_PART
+    rg, _, tg = g.read_fields()
+    rr, _, tr = r.read_fields()
+    assert np.array_equal(tg, tr)
+    assert np.max(np.abs(rg - rr)) < TOL_RHO
+
+
+def test_mass_sums_and_conservation():
+    shape = (40, 36, 30)
+    rho0 = W.random_phases(shape, 0.5, seed=26)
+    g, r = _pair(shape, rho0, g_br=0.1)
+    m0 = g.mass()
+    assert np.allclose(m0, r.mass(), rtol=1e-7)
+    g.step(100)
+    m1 = g.mass()
+    assert np.all(np.abs(m1 - m0) / m0 < 1e-6)
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 2e-4), ("bf16", 2e-3)])
+def test_16bit_offset_storage(storage, tol):
+    """FP32 arithmetic with populations stored as 16-bit offsets from
+    w_i ρ_ref: error against the FP64 oracle bounded by the storage
+    precision after 20 steps."""
+    shape = (20, 18, 16)
+    rho0 = W.random_phases(shape, 0.5, seed=27)
+    g = lbe.Lattice(shape, rho0, g_br=0.1, storage=storage, rho_ref=(0.37, 0.37))
+    r = lbref.Lattice(shape, rho0, g_br=0.1)
+    g.step(20)
+    r.step(20)
+    rg, _, _ = g.read_fields()
+    rr, _, _ = r.read_fields()
+    assert np.max(np.abs(rg - rr)) < tol
+    m = g.mass()
+    assert np.allclose(m, r.mass(), rtol=5 * tol)
+
+
+def test_graph_and_direct_launches_agree():
+    """lbe_step(n) replays a captured 2-step graph; odd counts launch
+    directly.  Both routes give bit-identical results."""
+    shape = (16, 16, 16)
+    rho0 = W.uniform_mixture(shape, 0.7, 0.01, seed=28)
+    a = lbe.Lattice(shape, rho0, g_br=0.1)
+    b = lbe.Lattice(shape, rho0, g_br=0.1)
+    a.step(10)
+    for _ in range(10):
+        b.step(1)
+    fa, fb = a.get_populations(), b.get_populations()
+    assert np.array_equal(fa, fb)
+
+
+def test_invalid_arguments_are_rejected():
+    shape = (8, 8, 8)
+    rho0 = np.full((2, 8, 8, 8), 0.5)
+    with pytest.raises(lbe.LbeError):
+        lbe.Lattice(shape, rho0, tau=(0.4, 1.0))
+    with pytest.raises(lbe.LbeError):
+        lbe.Lattice((8, 8, 2), rho0[:, :2], walls_z=True)
+    g = lbe.Lattice(shape, rho0)
+    with pytest.raises(lbe.LbeError):
+        g.add_particles([[9.0, 1.0, 1.0]], [[1, 0, 0, 0]], 2.0, 1.0, 0.0)
+    with pytest.raises(lbe.LbeError):
+        g.add_particles([[4.0, 4.0, 4.0]], [[1, 0, 0, 0]], -2.0, 1.0, 0.0)
+    g.step(2)
+    assert np.all(np.isfinite(g.mass()))
