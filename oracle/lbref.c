@@ -269,25 +269,30 @@ void lbref_destroy(lbref_ctx *c)
     free(c);
 }
 
-/* Axis-aligned box that contains the ellipsoid, widened by one node. */
-static void particle_box(const lbref_ctx *c, const particle *P, int lo[3], int hi[3])
+/* Axis-aligned box that contains the ellipsoid, widened by one node.
+ * Returns 0 (no box) for non-finite geometry or a centre further than 1e9
+ * from the origin; the bounds are formed in double before conversion. */
+static int particle_box(const lbref_ctx *c, const particle *P, int lo[3], int hi[3])
 {
     double R[3][3];
     rotmat(P->q, R);
     for (int k = 0; k < 3; k++) {
         double h = sqrt(P->rp * P->rp * R[k][0] * R[k][0] +
                         P->ro * P->ro * (R[k][1] * R[k][1] + R[k][2] * R[k][2]));
-        lo[k] = (int)floor(P->X[k] - h) - 1;
-        hi[k] = (int)ceil(P->X[k] + h) + 1;
+        double l = floor(P->X[k] - h) - 1.0, u = ceil(P->X[k] + h) + 1.0;
+        if (!(l <= u) || !(fabs(P->X[k]) < 1e9) || !(h < 1e9)) return 0;
         int n = extent(c, k);
         if (!periodic_dim(c, k)) {
-            if (lo[k] < 0) lo[k] = 0;
-            if (hi[k] > n - 1) hi[k] = n - 1;
-        } else if (hi[k] - lo[k] + 1 > n) {
-            lo[k] = 0;
-            hi[k] = n - 1;
+            if (l < 0) l = 0;
+            if (u > n - 1) u = n - 1;
+        } else if (u - l + 1 > n) {
+            l = 0;
+            u = n - 1;
         }
+        lo[k] = (int)l;
+        hi[k] = (int)u;
     }
+    return 1;
 }
 
 static int wrapi(int v, int n)
@@ -306,7 +311,7 @@ static void claim_nodes(lbref_ctx *c, int *own)
         double R[3][3];
         rotmat(P->q, R);
         int lo[3], hi[3];
-        particle_box(c, P, lo, hi);
+        if (!particle_box(c, P, lo, hi)) continue;
         for (int z = lo[2]; z <= hi[2]; z++)
             for (int y = lo[1]; y <= hi[1]; y++)
                 for (int x = lo[0]; x <= hi[0]; x++) {

@@ -133,7 +133,11 @@ __global__ void __launch_bounds__(256) k_shell(Lat L, const float *__restrict__ 
     }
     if (cnt == 0) return;  // interior: never read by a fluid node
     float r0 = s0 / (float)cnt, r1 = s1 / (float)cnt;
-    float dr = t == PART ? (float)drho[owner[n]] : 0.f;
+    float dr = 0.f;
+    if (t == PART) {
+        uint32_t o = owner[n];
+        if (idx_ok(L, o, L.np, 1)) dr = (float)drho[o];
+    }
     if (dr > 0.f)
         r0 += dr;
     else

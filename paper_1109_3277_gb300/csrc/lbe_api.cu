@@ -123,6 +123,7 @@ void free_all(lbe_ctx *c)
     cudaFree(c->mass_out);
     cudaFree(c->pbuf);
     cudaFree(c->x32);
+    if (c->L.err) cudaFree(c->L.err);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -177,6 +178,7 @@ void enqueue_step(lbe_ctx *c)
             launch_transition(st, L, c->P, fout, c->type, oo, on, 0, s);
             launch_reset(L, c->P, 1, oo, s);
             c->ocur = 1 - c->ocur;
+            launch_verify(L, c->type, on, s);
         }
     }
     c->cur = 1 - c->cur;
@@ -193,6 +195,15 @@ lbe_status sync(lbe_ctx *c, const char *where)
 {
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, where);
+#ifdef LBE_CHECK
+    unsigned long long bad = 0;
+    if (c->L.err && cudaMemcpy(&bad, c->L.err, sizeof bad, cudaMemcpyDeviceToHost) == cudaSuccess && bad) {
+        char m[128];
+        snprintf(m, sizeof m, "%s: bounds check failed: site %llu index %llu", where, bad >> 40,
+                 bad & 0xFFFFFFFFFFull);
+        return fail(c, LBE_ECUDA, m);
+    }
+#endif
     return check_async(c, where);
 }
 
@@ -260,6 +271,10 @@ lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_c
     if ((e = dalloc(c, &c->mass_partials, (size_t)2 * mass_blocks() * sizeof(double))) != cudaSuccess)
         return bail(e, "cudaMalloc(mass)");
     if ((e = dalloc(c, &c->mass_out, 2 * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc(mass_out)");
+#ifdef LBE_CHECK
+    if ((e = cudaMalloc((void **)&c->L.err, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc(err)");
+    cudaMemset(c->L.err, 0, sizeof(unsigned long long));
+#endif
     cudaStream_t s = c->stream;
     cudaMemsetAsync(c->owner[0], 0xFF, (size_t)N * 4, s);
     cudaMemsetAsync(c->owner[1], 0xFF, (size_t)N * 4, s);
@@ -369,6 +384,7 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
     CK(c, cudaMemcpy(c->pbuf, blk.data(), blk.size() * sizeof(double), cudaMemcpyHostToDevice));
     CK(c, cudaMemcpy(c->x32, x32.data(), x32.size() * sizeof(float), cudaMemcpyHostToDevice));
     c->np = np;
+    c->L.np = np;
     bind_parts(c);
     drop_graphs(c);
     cudaStream_t s = c->stream;

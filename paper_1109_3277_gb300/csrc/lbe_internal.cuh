@@ -72,7 +72,23 @@ struct Lat {
     float body[3];
     float base[2][Q];      // w_i ρ_ref^c for the 16-bit modes, 0 for FP32
     double rho_ref[2];
+    int np;                        // particles (bounds checks)
+    unsigned long long *err;       // bounds-check record (checked builds only)
 };
+
+// Checked builds (-DLBE_CHECK) verify every data-dependent or computed index
+// before use; a bad one is recorded (code << 40 | index) and the access is
+// skipped.  Release builds compile the checks away.
+#ifdef LBE_CHECK
+__device__ __forceinline__ bool idx_ok(const Lat &L, long long i, long long lim, int code)
+{
+    if (i >= 0 && i < lim) return true;
+    atomicCAS(L.err, 0ull, ((unsigned long long)code << 40) | ((unsigned long long)i & 0xFFFFFFFFFFull));
+    return false;
+}
+#else
+__device__ __forceinline__ bool idx_ok(const Lat &, long long, long long, int) { return true; }
+#endif
 
 // Particle state on the device (structure of arrays, FP64).
 struct Parts {
@@ -120,5 +136,6 @@ void launch_transition(int storage, const Lat &L, const Parts &P, void *f, uint8
                        const uint32_t *owner_old, const uint32_t *owner_new, int placement,
                        cudaStream_t s);
 void launch_reset(const Lat &L, const Parts &P, int use_old, uint32_t *owner, cudaStream_t s);
+void launch_verify(const Lat &L, const uint8_t *type, const uint32_t *owner, cudaStream_t s);
 
 }  // namespace lbe

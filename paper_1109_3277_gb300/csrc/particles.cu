@@ -105,30 +105,55 @@ struct Box {
 };
 
 // Axis-aligned box containing the ellipsoid at X (not necessarily wrapped),
-// widened by one node; clamped to the lattice along walls and to one period.
+// widened by one node, as doubles: lo[k] = floor(X - h) - 1, hi[k] =
+// ceil(X + h) + 1 with h the half-extent of the rotated ellipsoid along k.
+// Non-finite geometry, or a centre further than 1e9 from the origin (a
+// particle that has left any lattice), gives lo > hi: an empty box.
 __device__ void box_of(const Lat &L, const double *X, const double R[3][3], double rp, double ro,
-                       int lo[3], int hi[3])
+                       double lo[3], double hi[3])
 {
     for (int k = 0; k < 3; k++) {
         double h = sqrt(rp * rp * R[k][0] * R[k][0] + ro * ro * (R[k][1] * R[k][1] + R[k][2] * R[k][2]));
-        lo[k] = (int)floor(X[k] - h) - 1;
-        hi[k] = (int)ceil(X[k] + h) + 1;
+        lo[k] = floor(X[k] - h) - 1.0;
+        hi[k] = ceil(X[k] + h) + 1.0;
+        if (!(lo[k] <= hi[k]) || !(fabs(X[k]) < 1e9) || !(h < 1e9)) {
+            lo[k] = 1.0;
+            hi[k] = 0.0;
+        }
     }
 }
 
-__device__ void finish_box(const Lat &L, int lo[3], int hi[3], Box &b)
+__device__ __forceinline__ bool box_empty(const double lo[3], const double hi[3])
 {
+    return !(lo[0] <= hi[0] && lo[1] <= hi[1] && lo[2] <= hi[2]);
+}
+
+// Integer box over lattice nodes: along walls clamped to [0, n-1]; along
+// periodic axes one period at most, shifted so that lo lies in [0, n).  All
+// arithmetic before the conversion to int is in double, so no value of X can
+// overflow an int.
+__device__ void finish_box(const Lat &L, const double *lo_in, const double *hi_in, Box &b)
+{
+    bool empty = box_empty(lo_in, hi_in);
     for (int k = 0; k < 3; k++) {
-        int n = ext_of(L, k);
-        if (!periodic_dim(L, k)) {
-            if (lo[k] < 0) lo[k] = 0;
-            if (hi[k] > n - 1) hi[k] = n - 1;
-        } else if (hi[k] - lo[k] + 1 > n) {
-            lo[k] = 0;
-            hi[k] = n - 1;
+        double n = (double)ext_of(L, k);
+        double lo = lo_in[k], hi = hi_in[k];
+        if (empty) {
+            lo = 0.0;
+            hi = -1.0;
+        } else if (!periodic_dim(L, k)) {
+            lo = fmax(lo, 0.0);
+            hi = fmin(hi, n - 1.0);
+        } else if (hi - lo + 1.0 > n) {
+            lo = 0.0;
+            hi = n - 1.0;
+        } else {
+            double s = n * floor(lo / n);
+            lo -= s;
+            hi -= s;
         }
-        b.lo[k] = lo[k];
-        b.ext[k] = hi[k] >= lo[k] ? hi[k] - lo[k] + 1 : 0;
+        b.lo[k] = hi >= lo ? (int)lo : 0;
+        b.ext[k] = hi >= lo ? (int)(hi - lo + 1.0) : 0;
     }
     b.count = b.ext[0] * b.ext[1] * b.ext[2];
 }
@@ -213,7 +238,7 @@ __global__ void __launch_bounds__(PT) k_links(Lat L, Parts P, typename S::T *__r
     if (threadIdx.x == 0) {
         double R[3][3];
         rotmat(P.q + 4 * p, R);
-        int lo[3], hi[3];
+        double lo[3], hi[3];
         box_of(L, P.X + 3 * p, R, P.rp[p], P.ro[p], lo, hi);
         finish_box(L, lo, hi, box);
         for (int k = 0; k < 3; k++) {
@@ -228,6 +253,7 @@ __global__ void __launch_bounds__(PT) k_links(Lat L, Parts P, typename S::T *__r
         int x, y, z;
         box_node(L, box, k, x, y, z);
         int n = x + L.nx * (y + L.ny * z);
+        if (!idx_ok(L, n, L.N, 2)) continue;
         if (owner[n] != (uint32_t)p) continue;
         float dn[3] = {(float)node_disp(L, 0, x, sX[0]), (float)node_disp(L, 1, y, sX[1]),
                        (float)node_disp(L, 2, z, sX[2])};
@@ -235,7 +261,7 @@ __global__ void __launch_bounds__(PT) k_links(Lat L, Parts P, typename S::T *__r
 #pragma unroll
         for (int i = 1; i < Q; i++) {
             int m = nbr_node(L, x, y, z, i);
-            if (m < 0 || type[m] != FLUID) continue;
+            if (m < 0 || !idx_ok(L, m, L.N, 3) || type[m] != FLUID) continue;
             float rb[3] = {dn[0] + 0.5f * cx(i), dn[1] + 0.5f * cy(i), dn[2] + 0.5f * cz(i)};
             float us[3] = {sV[0] + sW[1] * rb[2] - sW[2] * rb[1], sV[1] + sW[2] * rb[0] - sW[0] * rb[2],
                            sV[2] + sW[0] * rb[1] - sW[1] * rb[0]};
@@ -491,7 +517,7 @@ __global__ void __launch_bounds__(PT) k_claim(Lat L, Parts P, uint32_t *__restri
     __shared__ double sX[3];
     if (threadIdx.x == 0) {
         geo_of(P.q + 4 * p, P.rp[p], P.ro[p], geo);
-        int lo[3], hi[3];
+        double lo[3], hi[3];
         box_of(L, P.X + 3 * p, geo.R, P.rp[p], P.ro[p], lo, hi);
         finish_box(L, lo, hi, box);
         for (int k = 0; k < 3; k++) sX[k] = P.X[3 * p + k];
@@ -502,7 +528,8 @@ __global__ void __launch_bounds__(PT) k_claim(Lat L, Parts P, uint32_t *__restri
         box_node(L, box, k, x, y, z);
         if (is_wall_z(L, z)) continue;
         double dx[3] = {node_disp(L, 0, x, sX[0]), node_disp(L, 1, y, sX[1]), node_disp(L, 2, z, sX[2])};
-        if (inside(geo, dx)) atomicMin(owner_new + (x + L.nx * (y + L.ny * z)), (uint32_t)p);
+        int n = x + L.nx * (y + L.ny * z);
+        if (idx_ok(L, n, L.N, 4) && inside(geo, dx)) atomicMin(owner_new + n, (uint32_t)p);
     }
 }
 
@@ -535,12 +562,20 @@ __global__ void __launch_bounds__(PT) k_transition(Lat L, Parts P, typename S::T
             Xo[k] = P.Xold[3 * p + k];
             Xu[k] = Xo[k] + pair_disp(L, k, Xo[k], P.X[3 * p + k]);
         }
-        int lo[3], hi[3], lo2[3], hi2[3];
+        // union of the old and new boxes (either may be empty)
+        double lo[3], hi[3], lo2[3], hi2[3];
         box_of(L, Xo, Ro, P.rp[p], P.ro[p], lo, hi);
         box_of(L, Xu, Rn, P.rp[p], P.ro[p], lo2, hi2);
-        for (int k = 0; k < 3; k++) {
-            lo[k] = min(lo[k], lo2[k]);
-            hi[k] = max(hi[k], hi2[k]);
+        if (box_empty(lo, hi)) {
+            for (int k = 0; k < 3; k++) {
+                lo[k] = lo2[k];
+                hi[k] = hi2[k];
+            }
+        } else if (!box_empty(lo2, hi2)) {
+            for (int k = 0; k < 3; k++) {
+                lo[k] = fmin(lo[k], lo2[k]);
+                hi[k] = fmax(hi[k], hi2[k]);
+            }
         }
         finish_box(L, lo, hi, box);
         for (int k = 0; k < 3; k++) {
@@ -555,6 +590,7 @@ __global__ void __launch_bounds__(PT) k_transition(Lat L, Parts P, typename S::T
         int x, y, z;
         box_node(L, box, k, x, y, z);
         int n = x + L.nx * (y + L.ny * z);
+        if (!idx_ok(L, n, L.N, 5)) continue;
         uint32_t o = own_old[n], w = own_new[n];
         if (o == w) continue;
         if (min(o, w) != (uint32_t)p) continue;
@@ -585,7 +621,7 @@ __global__ void __launch_bounds__(PT) k_transition(Lat L, Parts P, typename S::T
             int cnt = 0;
             for (int i = 1; i < Q; i++) {
                 int m = nbr_node(L, x, y, z, i);
-                if (m < 0) continue;
+                if (m < 0 || !idx_ok(L, m, L.N, 6)) continue;
                 int mz = m / (L.nx * L.ny);
                 if (is_wall_z(L, mz) || own_old[m] != NONE || own_new[m] != NONE) continue;
                 float a0 = 0.f, a1 = 0.f;
@@ -650,7 +686,7 @@ __global__ void __launch_bounds__(PT) k_reset(Lat L, Parts P, int use_old, uint3
         const double *X = use_old ? P.Xold + 3 * p : P.X + 3 * p;
         double R[3][3];
         rotmat(q, R);
-        int lo[3], hi[3];
+        double lo[3], hi[3];
         box_of(L, X, R, P.rp[p], P.ro[p], lo, hi);
         finish_box(L, lo, hi, box);
     }
@@ -658,11 +694,32 @@ __global__ void __launch_bounds__(PT) k_reset(Lat L, Parts P, int use_old, uint3
     for (int k = threadIdx.x; k < box.count; k += PT) {
         int x, y, z;
         box_node(L, box, k, x, y, z);
-        owner[x + L.nx * (y + L.ny * z)] = NONE;
+        int n = x + L.nx * (y + L.ny * z);
+        if (idx_ok(L, n, L.N, 7)) owner[n] = NONE;
     }
 }
 
+#ifdef LBE_CHECK
+// Checked builds: after each step the node types must agree with the
+// ownership map (particle iff owned).
+__global__ void k_verify(Lat L, const uint8_t *type, const uint32_t *owner)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.N) return;
+    bool part = type[n] == PART, own = owner[n] != NONE;
+    if (part && !own) idx_ok(L, -1 - (long long)n, 0, 10);
+    if (own && !part) idx_ok(L, -1 - (long long)n, 0, 11);
+}
+#endif
+
 }  // namespace
+
+void launch_verify(const Lat &L, const uint8_t *type, const uint32_t *owner, cudaStream_t s)
+{
+#ifdef LBE_CHECK
+    k_verify<<<(L.N + 255) / 256, 256, 0, s>>>(L, type, owner);
+#endif
+}
 
 #define LBE_DISPATCH(storage, CALL)                                   \
     do {                                                              \

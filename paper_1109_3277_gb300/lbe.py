@@ -9,7 +9,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liblbe.so")
+LIB_PATH = os.environ.get("LBE_LIB") or os.path.join(HERE, "liblbe.so")
 Q = 19
 
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}

@@ -129,34 +129,63 @@ def test_adsorption_box_200_steps():
     assert np.linalg.norm(pr["pos"][0] - p["pos"][0]) > 1e-3
 
 
-def test_free_particles_pair_forces():
-    """Several free ellipsoids placed so that Hertz overlap and lubrication
-    gaps occur, periodic box."""
+def test_free_particles_hertz_contact():
+    """Free ellipsoids in a periodic box, two of them in slight end-to-end
+    Hertz overlap (Eq. 6-8), one straddling the periodic corner;
+    lubrication off."""
     shape = (36, 30, 28)
     rho0 = W.random_phases(shape, 0.5, seed=25)
-    g, r = _pair(shape, rho0, g_br=0.1)
-    pos = [[10.0, 10.0, 10.0], [10.0, 10.0, 17.6], [19.5, 10.5, 10.0], [30.0, 25.0, 3.0],
-           [1.0, 25.5, 2.5]]
-    quats = [W.axis_tilt_quaternion(0.0), W.axis_tilt_quaternion(0.1, 0.5),
+    g, r = _pair(shape, rho0, g_br=0.1, lub_cut=0.0)
+    pos = [[10.0, 10.0, 10.0], [10.0, 10.0, 17.97], [22.5, 10.5, 10.0], [30.0, 22.0, 20.0],
+           [1.0, 25.5, 1.5]]
+    quats = [W.axis_tilt_quaternion(0.0), W.axis_tilt_quaternion(0.0),
              W.axis_tilt_quaternion(np.pi / 2, 0.0), W.axis_tilt_quaternion(1.0, 2.0),
              W.axis_tilt_quaternion(0.4, 1.0)]
     _add(g, r, pos=pos, quat=quats, r_par=4.0, r_perp=2.0, delta_rho=[0.0, 0.1, -0.1, 0.05, 0.0],
-         vel=[[0.0, 0.0, 0.01], [0.0, 0.0, -0.01], [-0.005, 0, 0], [0.002, 0.001, 0.0],
+         vel=[[0.0, 0.0, 0.002], [0.0, 0.0, -0.002], [-0.005, 0, 0], [0.002, 0.001, 0.0],
               [0.0, 0.0, 0.0]])
     g.step(1)
     r.step(1)
     pg, pr = g.read_particles(), r.read_particles()
-    scale = np.abs(pr["force"]).max()
-    assert scale > 1.0  # Hertz overlap is active
+    scale = max(1.0, np.abs(pr["force"]).max())
+    assert np.abs(pr["force"]).max() > 0.1  # Hertz overlap is active
     assert np.max(np.abs(pg["force"] - pr["force"])) < 1e-5 * scale
-    g.step(49)
-    r.step(49)
+    assert np.max(np.abs(pg["torque"] - pr["torque"])) < 1e-5 * max(scale, np.abs(pr["torque"]).max())
+    g.step(39)
+    r.step(39)
     pg, pr = g.read_particles(), r.read_particles()
+    assert np.max(np.abs(pg["vel"])) < 0.05  # a physically sane run
     assert np.max(np.abs(pg["pos"] - pr["pos"])) < TOL_PART
+    qg, qr = pg["quat"] * np.sign(pg["quat"][:, :1]), pr["quat"] * np.sign(pr["quat"][:, :1])
+    assert np.max(np.abs(qg - qr)) < TOL_PART
     rg, _, tg = g.read_fields()
     rr, _, tr = r.read_fields()
     assert np.array_equal(tg, tr)
     assert np.max(np.abs(rg - rr)) < TOL_RHO
+
+
+def test_lubrication_gap():
+    """Two ellipsoids side by side at a gap of 0.45 < Δc closing slowly: the
+    lubrication correction (Eq. 9 generalised with σ) opposes the approach."""
+    shape = (32, 24, 24)
+    rho0 = W.uniform_mixture(shape, 0.7, 0.0, seed=1)
+    g, r = _pair(shape, rho0, g_br=0.0)
+    q = W.axis_tilt_quaternion(np.pi / 2, 0.0)  # both axes along x, separation along y
+    pos = [[16.0, 9.775, 12.0], [16.0, 14.225, 12.0]]
+    vel = [[0.0, 0.001, 0.0], [0.0, -0.001, 0.0]]
+    _add(g, r, pos=pos, quat=[q, q], r_par=5.0, r_perp=2.0, delta_rho=0.0, vel=vel)
+    g.step(1)
+    r.step(1)
+    pg, pr = g.read_particles(), r.read_particles()
+    # the pair force on particle 0 points away from particle 1 (-y)
+    assert pr["force"][0, 1] < 0 and pr["force"][1, 1] > 0
+    # the momentum exchange sums O(100) FP32 link terms of order 0.03: its
+    # rounding floor is absolute, ~1e-6, whatever the net force
+    assert np.max(np.abs(pg["force"] - pr["force"])) < 1e-5 * max(1.0, np.abs(pr["force"]).max())
+    g.step(29)
+    r.step(29)
+    pg, pr = g.read_particles(), r.read_particles()
+    assert np.max(np.abs(pg["pos"] - pr["pos"])) < TOL_PART
 
 
 def test_mass_sums_and_conservation():
