@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the two-component Shan–Chen D3Q19 BGK step with rigid
+ellipsoids (Günther et al., arXiv:1109.3277, §2) on GB300.
+
+Metric: MLUPS, lattice-node updates per second over ALL nodes (fluid and
+solid), as the paper counts LUPS for its two-component suspension benchmark.
+Default workload: the 512^3 Pickering emulsion (periodic, nodes red-rich with
+probability 0.8, ~25,000 prolate ellipsoids r_par=8, r_perp=4 at volume
+fraction 0.10, colour Δρ=0.1) with populations stored as FP16 offsets, FP32
+arithmetic and FP64 particles.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line is printed by rank 0.  With N > 1 (torchrun) every rank runs an
+independent replica of the workload (weak scaling; the path has no exchange
+step on one GPU per box) and the slowest rank's time counts.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1109_3277_gb300 import workloads as W  # noqa: E402
+
+METRIC = "MLUPS (2-comp D3Q19+ellipsoids)"
+UNIT = "MLUPS"
+ESIZE = {"f32": 4, "f16": 2, "bf16": 2}
+DTYPE = {"f32": "f32", "f16": "f32 arithmetic, f16-offset storage",
+         "bf16": "f32 arithmetic, bf16-offset storage"}
+
+
+def parse(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["pickering", "spinodal", "bijel", "adsorption"],
+                    default="pickering")
+    ap.add_argument("--n", type=int, default=None, help="lattice edge (default: the workload's)")
+    ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args(argv)
+
+
+def make_workload(name, n=None, storage=None):
+    if name == "pickering":
+        w = W.pickering(n=n or 512)
+    elif name == "spinodal":
+        w = W.spinodal(n=n or 128)
+    elif name == "bijel":
+        w = W.bijel(n=n or 256)
+    else:
+        w = W.adsorption_box()
+    if storage:
+        w.storage = storage
+    return w
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Dist:
+    """Barrier and max-reduction across ranks (torch.distributed when the
+    job has more than one rank)."""
+
+    def __init__(self, backend=None):
+        self.world, self.rank, self.local = dist_info()
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as td
+            td.init_process_group(backend=backend or "nccl")
+            self.td = td
+
+    def barrier(self):
+        if self.world > 1:
+            self.td.barrier()
+
+    def max(self, v):
+        if self.world == 1:
+            return v
+        import torch
+        dev = "cuda" if self.td.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(v)], dtype=torch.float64, device=dev)
+        self.td.all_reduce(t, op=self.td.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.world > 1:
+            self.td.destroy_process_group()
+
+
+def weak_scaling_value(nodes_per_rank, steps, world, max_seconds):
+    """Whole-job MLUPS: all ranks' node updates over the slowest rank's time."""
+    return world * nodes_per_rank * steps / max_seconds / 1e6
+
+
+class Clocks:
+    """nvidia-smi sampler (200 ms) running while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.out.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_digest():
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_1109_3277_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        with open(os.path.join(cs, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(f"{kernel}:{workload}")
+    if not e or e.get("source_digest") != source_digest():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def add_particles(lat, w):
+    p = w.particles
+    if p:
+        lat.add_particles(p["pos"], p["quat"], p["r_par"], p["r_perp"], p["delta_rho"])
+
+
+def cpu_sample_workload(w):
+    """A bounded sample of the workload for the CPU oracle: a sub-box with
+    the same node mix, particle shape and particle number density."""
+    if w.name.startswith("pickering"):
+        return W.pickering(seed=1113, n=64), "64^3 sub-box of the same recipe"
+    if w.name.startswith("bijel"):
+        return W.bijel(seed=1112, n=64), "64^3 sub-box of the same recipe"
+    if w.name.startswith("spinodal"):
+        return W.spinodal(seed=1111, n=64), "64^3 sub-box of the same recipe"
+    return w, "the full workload"
+
+
+def time_oracle(w, steps, warmup=1):
+    from oracle import lbref
+    params = dict(w.params)
+    lat = lbref.Lattice(w.shape, w.rho0, **params)
+    p = w.particles
+    if p:
+        lat.add_particles(p["pos"], p["quat"], p["r_par"], p["r_perp"], p["delta_rho"])
+    if warmup:
+        lat.step(warmup)
+    t = time.perf_counter()
+    lat.step(steps)
+    dt = time.perf_counter() - t
+    n = int(np.prod(w.shape))
+    lat.close()
+    return n * steps / dt / 1e6, dt
+
+
+def run_ours(args):
+    import torch
+    from paper_1109_3277_gb300 import lbe
+    from paper_1109_3277_gb300 import build as lbe_build
+
+    dist = Dist()
+    torch.cuda.set_device(dist.local)
+    lbe_build.build()
+    w = make_workload(args.workload, args.n, args.storage)
+    storage = w.storage
+    stream = torch.cuda.Stream()
+    nodes = int(np.prod(w.shape))
+    # ---------------- device-resident throughput
+    lat = lbe.Lattice(w.shape, w.rho0, storage=storage, stream=stream.cuda_stream, device=dist.local,
+                      **w.params)
+    add_particles(lat, w)
+    lat.step(args.warmup)
+    torch.cuda.synchronize()
+    lat.profile_enable(True)
+    clocks = Clocks(dist.local)
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lat.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    kern_ms, launches = lat.profile_read()
+    lat.profile_enable(False)
+    kernels_per_step = lat.kernels_per_step()
+    m = lat.mass()
+    lat.close()
+    del lat
+    ms_max = dist.max(ms) if dist.world > 1 else ms
+    value = weak_scaling_value(nodes, args.steps, dist.world, ms_max / 1e3)
+    # ---------------- roofline of the dominant kernel (fluid collide+stream)
+    peak, peak_kind = measured_peaks()
+    bytes_per_launch = nodes * 2 * 2 * 19 * ESIZE[storage]
+    avg_s = kern_ms / max(launches, 1) / 1e3
+    achieved = bytes_per_launch / avg_s / 1e9
+    traffic = committed_traffic("collide_stream", w.name)
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "kernel": "k_collide_stream", "bytes_per_launch": bytes_per_launch,
+            "kernel_ms_avg": round(avg_s * 1e3, 4), "peak_kind": peak_kind,
+            "kernel_share_of_step": round(kern_ms / ms, 4)}
+    # ---------------- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        dist.barrier()
+        pinned = torch.empty(w.rho0.shape, dtype=torch.float64, pin_memory=True)
+        pinned.numpy()[...] = w.rho0
+        t0 = time.perf_counter()
+        lat2 = lbe.Lattice(w.shape, pinned.numpy(), storage=storage, stream=stream.cuda_stream,
+                           device=dist.local, **w.params)
+        add_particles(lat2, w)
+        d2h = 0
+        for _ in range(args.steps):
+            lat2.step(1)
+            if w.particles:
+                out = lat2.read_particles()
+                d2h += sum(a.nbytes for a in out.values())
+            else:
+                d2h += lat2.mass().nbytes
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        lat2.close()
+        e2e_s = dist.max(t1 - t0)
+        h2d = w.rho0.nbytes + sum(np.asarray(a).nbytes for a in w.particles.values()) if w.particles \
+            else w.rho0.nbytes
+        e2e = {"value": round(weak_scaling_value(nodes, args.steps, dist.world, e2e_s), 1), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d // args.steps), "d2h_bytes_per_step": int(d2h // args.steps),
+               "timed": "init_lattice from pinned host densities + add_particles + steps, "
+                        "each step followed by read_particles (or mass)"}
+    # ---------------- CPU oracle baseline (rank 0, N = 1)
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
+        ws, what = cpu_sample_workload(w)
+        v, dt = time_oracle(ws, steps=3, warmup=1)
+        cpu = {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{what}: {ws.name}, 3 steps after 1 warm-up ({dt:.1f} s, FP64, 1 thread)"}
+    if dist.rank == 0:
+        line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": dist.world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": DTYPE[storage], "data": "synthetic (seeded recipe of the paper's workload)",
+                "config": {"workload": w.name, "lattice": list(w.shape),
+                           "particles": int(len(w.particles["pos"])) if w.particles else 0,
+                           "storage": storage, "bytes_per_node_update": 2 * 2 * 19 * ESIZE[storage],
+                           "parallelism": f"replicas x{dist.world}",
+                           "l2": "inputs larger than L2 (populations %.1f GB)" % (
+                               2 * nodes * 2 * 19 * ESIZE[storage] / 1e9)},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(kernels_per_step * args.steps), "clocks": clk,
+                "mass": [float(x) for x in m]}
+        print(json.dumps(line), flush=True)
+    dist.close()
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on the host cores on a bounded sample
+    of the same workload; rank 0 only."""
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return
+    w = make_workload(args.workload, args.n, args.storage)
+    ws, what = cpu_sample_workload(w)
+    from oracle import lbref
+    lat = lbref.Lattice(ws.shape, ws.rho0, **ws.params)
+    p = ws.particles
+    if p:
+        lat.add_particles(p["pos"], p["quat"], p["r_par"], p["r_perp"], p["delta_rho"])
+    lat.step(args.warmup)
+    t = time.perf_counter()
+    lat.step(args.steps)
+    dt = time.perf_counter() - t
+    nodes = int(np.prod(ws.shape))
+    v = nodes * args.steps / dt / 1e6
+    sample = f"{what}: {ws.name}, {args.steps} steps after {args.warmup} warm-up, FP64, 1 thread"
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded recipe of the paper's workload)",
+            "config": {"workload": w.name, "lattice": list(w.shape), "sample_lattice": list(ws.shape),
+                       "storage": "f64"},
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main(argv=None):
+    args = parse(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

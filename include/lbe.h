@@ -83,7 +83,9 @@ typedef struct {
     double  k_hertz;         /* K_H of the Hertz potential (§2: 100) */
     double  lub_cut;         /* Δc of the lubrication correction (§2: 2/3); 0 disables it */
     double  lub_rho;         /* density in μ = ν ρ of the lubrication correction */
-    void   *cuda_stream;     /* cudaStream_t to enqueue on, or NULL */
+    void   *cuda_stream;     /* cudaStream_t to enqueue on (of the chosen device), or NULL */
+    int32_t device;          /* CUDA device ordinal; -1 = the library's current device */
+    int32_t reserved;        /* must be 0 */
 } lbe_lattice_desc;
 
 /* Create a lattice on the current CUDA device with populations at the rest

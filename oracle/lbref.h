@@ -41,6 +41,8 @@ typedef struct {
     double  lub_cut;           /* Δc of the lubrication correction (§2: 2/3); 0 disables */
     double  lub_rho;           /* density in μ = ν ρ for the lubrication correction */
     void   *cuda_stream;       /* unused by the oracle */
+    int32_t device;            /* unused by the oracle */
+    int32_t reserved;
 } lbref_lattice_desc;
 
 /* Create a lattice with populations at rest-equilibrium f_i = w_i rho0 (Eq. 2

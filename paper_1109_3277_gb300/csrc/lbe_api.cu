@@ -13,6 +13,7 @@ using namespace lbe;
 
 struct lbe_ctx {
     lbe_lattice_desc d{};
+    int device = 0;
     Lat L{};
     Pair pair{};
     cudaStream_t stream = nullptr;
@@ -222,9 +223,16 @@ lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_c
     if (d->particle_mode < 0 || d->particle_mode > 2) return LBE_EINVAL;
     long long N = (long long)d->nx * d->ny * d->nz;
     if (N > 0x7fffffffLL) return LBE_EINVAL;
+    int dev = d->device;
+    if (dev >= 0) {
+        if (cudaSetDevice(dev) != cudaSuccess) return LBE_EINVAL;
+    } else if (cudaGetDevice(&dev) != cudaSuccess) {
+        return LBE_ECUDA;
+    }
     lbe_ctx *c = new (std::nothrow) lbe_ctx();
     if (!c) return LBE_ENOMEM;
     c->d = *d;
+    c->device = dev;
     Lat &L = c->L;
     L.nx = d->nx;
     L.ny = d->ny;
@@ -301,6 +309,7 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
                              const double *r_perp, const double *delta_rho)
 {
     if (!c) return LBE_EINVAL;
+    cudaSetDevice(c->device);
     if (n < 0 || (n > 0 && (!pos || !quat || !r_par || !r_perp || !delta_rho)))
         return fail(c, LBE_EINVAL, "add_particles: bad arguments");
     if (n == 0) return LBE_OK;
@@ -399,6 +408,7 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
 lbe_status lbe_step(lbe_ctx *c, int32_t nsteps)
 {
     if (!c || nsteps < 0) return LBE_EINVAL;
+    cudaSetDevice(c->device);
     if (nsteps == 0) return LBE_OK;
     if (c->profiling) {
         for (int k = 0; k < nsteps; k++) enqueue_step(c);
@@ -430,6 +440,7 @@ lbe_status lbe_step(lbe_ctx *c, int32_t nsteps)
 lbe_status lbe_read_fields(lbe_ctx *c, double *rho, double *vel, uint8_t *node_type)
 {
     if (!c) return LBE_EINVAL;
+    cudaSetDevice(c->device);
     cudaStream_t s = c->stream;
     const Lat &L = c->L;
     size_t N = (size_t)L.N;
@@ -457,6 +468,7 @@ lbe_status lbe_read_particles(lbe_ctx *c, double *pos, double *quat, double *vel
                               double *force, double *torque)
 {
     if (!c) return LBE_EINVAL;
+    cudaSetDevice(c->device);
     lbe_status st = sync(c, "read_particles");
     if (st != LBE_OK || c->np == 0) return st;
     size_t cp = (size_t)c->cap;
@@ -472,6 +484,7 @@ lbe_status lbe_read_particles(lbe_ctx *c, double *pos, double *quat, double *vel
 lbe_status lbe_mass(lbe_ctx *c, double out[2])
 {
     if (!c || !out) return LBE_EINVAL;
+    cudaSetDevice(c->device);
     launch_mass(c->d.storage, c->L, c->f[c->cur], c->type, c->mass_partials, mass_blocks(), c->mass_out,
                 c->stream);
     CK(c, cudaMemcpyAsync(out, c->mass_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -485,6 +498,7 @@ lbe_status lbe_mass(lbe_ctx *c, double out[2])
 lbe_status lbe_get_populations(lbe_ctx *c, double *f)
 {
     if (!c || !f) return LBE_EINVAL;
+    cudaSetDevice(c->device);
     size_t tot = (size_t)2 * Q * c->L.N;
     double *d = nullptr;
     CK(c, cudaMallocAsync((void **)&d, tot * sizeof(double), c->stream));
@@ -497,6 +511,7 @@ lbe_status lbe_get_populations(lbe_ctx *c, double *f)
 lbe_status lbe_set_populations(lbe_ctx *c, const double *f)
 {
     if (!c || !f) return LBE_EINVAL;
+    cudaSetDevice(c->device);
     size_t tot = (size_t)2 * Q * c->L.N;
     double *d = nullptr;
     CK(c, cudaMallocAsync((void **)&d, tot * sizeof(double), c->stream));
@@ -509,6 +524,7 @@ lbe_status lbe_set_populations(lbe_ctx *c, const double *f)
 lbe_status lbe_profile_enable(lbe_ctx *c, int32_t enable)
 {
     if (!c) return LBE_EINVAL;
+    cudaSetDevice(c->device);
     lbe_status st = sync(c, "profile_enable");
     if (st != LBE_OK) return st;
     c->profiling = enable != 0;
@@ -519,6 +535,7 @@ lbe_status lbe_profile_enable(lbe_ctx *c, int32_t enable)
 lbe_status lbe_profile_read(lbe_ctx *c, double *ms_total, int64_t *launches)
 {
     if (!c || !ms_total || !launches) return LBE_EINVAL;
+    cudaSetDevice(c->device);
     lbe_status st = sync(c, "profile_read");
     if (st != LBE_OK) return st;
     double tot = 0.0;
@@ -550,6 +567,7 @@ const char *lbe_last_error(const lbe_ctx *c) { return c ? c->err.c_str() : "null
 void lbe_destroy(lbe_ctx *c)
 {
     if (!c) return;
+    cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_all(c);
     delete c;

@@ -39,6 +39,8 @@ class LatticeDesc(ctypes.Structure):
         ("lub_cut", ctypes.c_double),
         ("lub_rho", ctypes.c_double),
         ("cuda_stream", ctypes.c_void_p),
+        ("device", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 
@@ -92,7 +94,7 @@ def _f64(a, shape=None):
 
 def make_desc(shape, walls_z=False, tau=(1.0, 1.0), g_br=0.1, body_force=(0.0, 0.0, 0.0),
               rho_ref=(0.37, 0.37), storage="f32", particle_mode="free", k_hertz=100.0,
-              lub_cut=2.0 / 3.0, lub_rho=1.4, stream=None):
+              lub_cut=2.0 / 3.0, lub_rho=1.4, stream=None, device=-1):
     nx, ny, nz = shape
     d = LatticeDesc()
     d.nx, d.ny, d.nz = nx, ny, nz
@@ -108,6 +110,8 @@ def make_desc(shape, walls_z=False, tau=(1.0, 1.0), g_br=0.1, body_force=(0.0, 0
     d.lub_cut = lub_cut
     d.lub_rho = lub_rho
     d.cuda_stream = stream
+    d.device = int(device)
+    d.reserved = 0
     return d
 
 
