@@ -302,14 +302,11 @@ __global__ void __launch_bounds__(MASS_THREADS) k_mass(Lat L, const typename S::
     double a0 = 0.0, a1 = 0.0;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < L.N; n += gridDim.x * blockDim.x) {
         if (type[n] != FLUID) continue;
-        float r0 = 0.f, r1 = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            r0 += S::ld(slot<S>(f, L, 0, i) + n, L.base[0][i]);
-            r1 += S::ld(slot<S>(f, L, 1, i) + n, L.base[1][i]);
+            a0 += (double)S::ld(slot<S>(f, L, 0, i) + n, L.base[0][i]);
+            a1 += (double)S::ld(slot<S>(f, L, 1, i) + n, L.base[1][i]);
         }
-        a0 += (double)r0;
-        a1 += (double)r1;
     }
     __shared__ double sh[2][MASS_THREADS];
     sh[0][threadIdx.x] = a0;
