@@ -216,19 +216,24 @@ __global__ void __launch_bounds__(256) k_collide_stream(Lat L, const typename S:
         }
         float uu = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
         float it = L.itau[c];
+        // The rest equilibrium is taken as ρ - Σ_{i>0} f^eq_i, equal to the
+        // formula in exact arithmetic; in FP32 it keeps Σ f^eq = ρ free of
+        // the systematic error of the rounded weights (Σ w_i = 1 + 1.5e-8).
+        float seq = 0.f;
 #pragma unroll
-        for (int i = 0; i < Q; i++) {
+        for (int i = 1; i < Q; i++) {
             float cu = cx(i) * ue[0] + cy(i) * ue[1] + cz(i) * ue[2];
             float feq = wgt(i) * r * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
+            seq += feq;
             float fs = f[c][i] - (f[c][i] - feq) * it;
-            if (i == 0) {
-                S::st(slot<S>(fout, L, c, 0) + n, fs, L.base[c][0]);
-            } else if (!solid_nb[i]) {
+            if (!solid_nb[i]) {
                 S::st(slot<S>(fout, L, c, i) + nb[i], fs, L.base[c][i]);
             } else {
                 S::st(slot<S>(fout, L, c, opp(i)) + n, fs, L.base[c][opp(i)]);
             }
         }
+        float fs0 = f[c][0] - (f[c][0] - (r - seq)) * it;
+        S::st(slot<S>(fout, L, c, 0) + n, fs0, L.base[c][0]);
     }
 }
 
