@@ -85,8 +85,14 @@ typedef struct {
     double  lub_rho;         /* density in μ = ν ρ of the lubrication correction */
     void   *cuda_stream;     /* cudaStream_t to enqueue on (of the chosen device), or NULL */
     int32_t device;          /* CUDA device ordinal; -1 = the library's current device */
-    int32_t reserved;        /* must be 0 */
+    int32_t flags;           /* 0, or LBE_FLAG_TWO_PASS */
 } lbe_lattice_desc;
+
+/* Run the fluid update as two passes (densities and ψ of every node to
+ * memory, then collide+stream) instead of the fused single pass.  Same
+ * results up to FP32 rounding; kept as the comparison point of the fused
+ * kernel. */
+#define LBE_FLAG_TWO_PASS 1
 
 /* Create a lattice on the current CUDA device with populations at the rest
  * equilibrium f_i^c = w_i rho0^c (Eq. 2 at u = 0).

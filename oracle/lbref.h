@@ -42,7 +42,7 @@ typedef struct {
     double  lub_rho;           /* density in μ = ν ρ for the lubrication correction */
     void   *cuda_stream;       /* unused by the oracle */
     int32_t device;            /* unused by the oracle */
-    int32_t reserved;
+    int32_t flags;             /* unused by the oracle */
 } lbref_lattice_desc;
 
 /* Create a lattice with populations at rest-equilibrium f_i = w_i rho0 (Eq. 2

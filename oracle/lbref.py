@@ -49,7 +49,7 @@ class LatticeDesc(ctypes.Structure):
         ("lub_rho", ctypes.c_double),
         ("cuda_stream", ctypes.c_void_p),
         ("device", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
     ]
 
 
@@ -121,7 +121,7 @@ def make_desc(shape, walls_z=False, tau=(1.0, 1.0), g_br=0.1, body_force=(0.0, 0
     d.lub_rho = lub_rho
     d.cuda_stream = None
     d.device = -1
-    d.reserved = 0
+    d.flags = 0
     return d
 
 

@@ -104,6 +104,35 @@ __global__ void __launch_bounds__(256) k_moments(Lat L, const typename S::T *__r
     }
 }
 
+// ------------------------------------------------------ boundary densities
+// ρ^c on the fluid nodes that have a solid neighbour: the only densities the
+// shell fill and the moving bounce-back read (the fused kernel computes the
+// others itself).
+
+template <class S>
+__global__ void __launch_bounds__(256) k_bnd_rho(Lat L, const typename S::T *__restrict__ f,
+                                                 const uint8_t *__restrict__ type, float *__restrict__ rho)
+{
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= L.N || type[n] != FLUID) return;
+    Coord c = coord_of(L, n);
+    Nbr b = nbr_of(L, c);
+    bool bnd = false;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        int m = nidx(L, b, i);
+        bnd |= m < 0 || type[m] != FLUID;
+    }
+    if (!bnd) return;
+#pragma unroll
+    for (int cc = 0; cc < 2; cc++) {
+        float r = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; i++) r += S::ld(slot<S>(f, L, cc, i) + n, L.base[cc][i]);
+        rho[(size_t)cc * L.N + n] = r;
+    }
+}
+
 // ---------------------------------------------------------- shell fill
 // Solid nodes with at least one fluid neighbour take the mean ρ^c of those
 // neighbours (Eq. 10); the colour Δρ of the owning particle is added to red
@@ -403,6 +432,13 @@ void launch_moments(int storage, const Lat &L, const void *f, const uint8_t *typ
 {
     LBE_DISPATCH(storage, (k_moments<S><<<blocks_for(L.N, 256), 256, 0, s>>>(
                               L, (const typename S::T *)f, type, rho, psi)));
+}
+
+void launch_bnd_rho(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho,
+                    cudaStream_t s)
+{
+    LBE_DISPATCH(storage, (k_bnd_rho<S><<<blocks_for(L.N, 256), 256, 0, s>>>(
+                              L, (const typename S::T *)f, type, rho)));
 }
 
 void launch_shell(const Lat &L, const float *rho, float *psi, const uint8_t *type,

@@ -29,7 +29,7 @@ struct lbe_ctx {
     // particles
     int np = 0, cap = 0;
     double *pbuf = nullptr;
-    float *x32 = nullptr;
+    float4 *x32 = nullptr;
     Parts P{};
     // graphs keyed by (cur, ocur)
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -151,7 +151,11 @@ void enqueue_step(lbe_ctx *c)
     const Lat &L = c->L;
     int st = c->d.storage;
     void *fin = c->f[c->cur], *fout = c->f[1 - c->cur];
-    launch_moments(st, L, fin, c->type, c->rho, c->psi, s);
+    const bool two_pass = (c->d.flags & LBE_FLAG_TWO_PASS) != 0;
+    if (two_pass)
+        launch_moments(st, L, fin, c->type, c->rho, c->psi, s);
+    else
+        launch_bnd_rho(st, L, fin, c->type, c->rho, s);
     launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, s);
     if (c->profiling) {
         if (c->ev_used + 2 > c->ev.size()) {
@@ -163,7 +167,10 @@ void enqueue_step(lbe_ctx *c)
         }
         cudaEventRecord(c->ev[c->ev_used], s);
     }
-    launch_collide_stream(st, L, fin, fout, c->psi, c->type, s);
+    if (two_pass)
+        launch_collide_stream(st, L, fin, fout, c->psi, c->type, s);
+    else
+        launch_fused(st, L, fin, fout, c->psi, c->type, s);
     if (c->profiling) {
         cudaEventRecord(c->ev[c->ev_used + 1], s);
         c->ev_used += 2;
@@ -221,6 +228,7 @@ lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_c
     if (!(d->tau[0] > 0.5) || !(d->tau[1] > 0.5)) return LBE_EINVAL;
     if (d->storage < LBE_STORE_F32 || d->storage > LBE_STORE_F16_OFS) return LBE_EINVAL;
     if (d->particle_mode < 0 || d->particle_mode > 2) return LBE_EINVAL;
+    if (d->flags & ~LBE_FLAG_TWO_PASS) return LBE_EINVAL;
     long long N = (long long)d->nx * d->ny * d->nz;
     if (N > 0x7fffffffLL) return LBE_EINVAL;
     int dev = d->device;
@@ -368,14 +376,15 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
         for (int j = 0; j < 3; j++) blk[OXO * cp + 3 * p + j] = blk[OX * cp + 3 * p + j];
         for (int j = 0; j < 4; j++) blk[OQO * cp + 4 * p + j] = blk[OQ * cp + 4 * p + j];
     }
-    std::vector<float> x32((size_t)3 * ncap, 0.f);
+    std::vector<float4> x32((size_t)ncap, make_float4(0.f, 0.f, 0.f, 0.f));
     for (int p = 0; p < np; p++)
-        for (int j = 0; j < 3; j++) x32[3 * p + j] = (float)blk[OX * cp + 3 * p + j];
+        x32[p] = make_float4((float)blk[OX * cp + 3 * p], (float)blk[OX * cp + 3 * p + 1],
+                             (float)blk[OX * cp + 3 * p + 2], (float)std::fmax(blk[ORP * cp + p], blk[ORO * cp + p]));
     if (ncap != cap) {
         double *nb = nullptr;
-        float *nx32 = nullptr;
+        float4 *nx32 = nullptr;
         CK(c, cudaMalloc((void **)&nb, blk.size() * sizeof(double)));
-        cudaError_t e = cudaMalloc((void **)&nx32, x32.size() * sizeof(float));
+        cudaError_t e = cudaMalloc((void **)&nx32, x32.size() * sizeof(float4));
         if (e != cudaSuccess) {
             cudaFree(nb);
             return cuda_fail(c, e, "add_particles: cudaMalloc");
@@ -383,15 +392,15 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
         if (c->pbuf) {
             cudaFree(c->pbuf);
             cudaFree(c->x32);
-            c->bytes -= (size_t)cap * (PSTRIDE * sizeof(double) + 3 * sizeof(float));
+            c->bytes -= (size_t)cap * (PSTRIDE * sizeof(double) + sizeof(float4));
         }
         c->pbuf = nb;
         c->x32 = nx32;
         c->cap = ncap;
-        c->bytes += (size_t)ncap * (PSTRIDE * sizeof(double) + 3 * sizeof(float));
+        c->bytes += (size_t)ncap * (PSTRIDE * sizeof(double) + sizeof(float4));
     }
     CK(c, cudaMemcpy(c->pbuf, blk.data(), blk.size() * sizeof(double), cudaMemcpyHostToDevice));
-    CK(c, cudaMemcpy(c->x32, x32.data(), x32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->x32, x32.data(), x32.size() * sizeof(float4), cudaMemcpyHostToDevice));
     c->np = np;
     c->L.np = np;
     bind_parts(c);

@@ -101,7 +101,7 @@ struct Parts {
     double *Fpair, *Tpair;          // pair forces of the current step
     double *Fpend, *Tpend;          // fill/empty momentum for the next update
     double *F, *T;                  // total of the last update
-    float *X32;                     // FP32 copy of X for the pair prefilter
+    float4 *X32;                    // FP32 (x, y, z, max radius) for the pair prefilter
 };
 
 struct Pair {
@@ -114,6 +114,8 @@ void launch_init_f(int storage, const Lat &L, const double *rho0, void *f, const
                    cudaStream_t s);
 void launch_moments(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho,
                     float *psi, cudaStream_t s);
+void launch_bnd_rho(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho,
+                    cudaStream_t s);
 void launch_shell(const Lat &L, const float *rho, float *psi, const uint8_t *type,
                   const uint32_t *owner, const double *drho, cudaStream_t s);
 void launch_collide_stream(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
@@ -125,6 +127,11 @@ void launch_mass(int storage, const Lat &L, const void *f, const uint8_t *type, 
 void launch_get_f(int storage, const Lat &L, const void *f, double *out, cudaStream_t s);
 void launch_set_f(int storage, const Lat &L, const double *in, void *f, cudaStream_t s);
 int mass_blocks();
+
+// ---- launchers (fused.cu) -------------------------------------------------
+void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
+                  const uint8_t *type, cudaStream_t s);
+int fused_zchunk(const Lat &L);
 
 // ---- launchers (particles.cu) ---------------------------------------------
 void launch_links(int storage, const Lat &L, const Parts &P, void *fnew, const float *rho,

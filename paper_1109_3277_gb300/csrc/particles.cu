@@ -82,15 +82,19 @@ __device__ void geo_of(const double *q, double rp, double ro, Geo &g)
 
 // Inside test: an FP32 evaluation decides unless it lies within 1e-3 of the
 // surface, where the exact FP64 evaluation (oracle operation order) decides.
-__device__ __forceinline__ bool inside(const Geo &g, const double dx[3])
+// d32 is the displacement in FP32 (error ~1e-7 lattice units); dx the exact
+// FP64 displacement, formed only when needed.
+__device__ __forceinline__ bool inside_q32(const Geo &g, const float d[3], float &q32)
 {
-    float d32[3];
-    float x0 = (float)dx[0], x1 = (float)dx[1], x2 = (float)dx[2];
+    float e[3];
 #pragma unroll
-    for (int k = 0; k < 3; k++) d32[k] = g.R32[0][k] * x0 + g.R32[1][k] * x1 + g.R32[2][k] * x2;
-    float q32 = d32[0] * d32[0] * g.ip2f + (d32[1] * d32[1] + d32[2] * d32[2]) * g.io2f;
-    if (q32 < 0.999f) return true;
-    if (q32 > 1.001f) return false;
+    for (int k = 0; k < 3; k++) e[k] = g.R32[0][k] * d[0] + g.R32[1][k] * d[1] + g.R32[2][k] * d[2];
+    q32 = e[0] * e[0] * g.ip2f + (e[1] * e[1] + e[2] * e[2]) * g.io2f;
+    return q32 < 0.999f;
+}
+
+__device__ __forceinline__ bool inside_exact(const Geo &g, const double dx[3])
+{
     double d[3];
 #pragma unroll
     for (int k = 0; k < 3; k++)
@@ -100,7 +104,8 @@ __device__ __forceinline__ bool inside(const Geo &g, const double dx[3])
 }
 
 struct Box {
-    int lo[3], ext[3];
+    int lo[3], ext[3];  // lower corner in unwrapped coordinates, extents
+    int full[3];        // the axis spans a whole period (nearest image taken per node)
     int count;
 };
 
@@ -129,15 +134,19 @@ __device__ __forceinline__ bool box_empty(const double lo[3], const double hi[3]
 }
 
 // Integer box over lattice nodes: along walls clamped to [0, n-1]; along
-// periodic axes one period at most, shifted so that lo lies in [0, n).  All
-// arithmetic before the conversion to int is in double, so no value of X can
-// overflow an int.
+// periodic axes at most one period.  Coordinates stay unwrapped (relative to
+// the particle, as the box was formed around it), so a node's displacement
+// from the particle is one exact subtraction; an axis clamped to a whole
+// period is flagged and takes the nearest image per node instead.  All
+// arithmetic before the conversion to int is in double and |lo|, |hi| are
+// below ~1e9 (box_of), so no int overflows.
 __device__ void finish_box(const Lat &L, const double *lo_in, const double *hi_in, Box &b)
 {
     bool empty = box_empty(lo_in, hi_in);
     for (int k = 0; k < 3; k++) {
         double n = (double)ext_of(L, k);
         double lo = lo_in[k], hi = hi_in[k];
+        b.full[k] = 0;
         if (empty) {
             lo = 0.0;
             hi = -1.0;
@@ -147,10 +156,7 @@ __device__ void finish_box(const Lat &L, const double *lo_in, const double *hi_i
         } else if (hi - lo + 1.0 > n) {
             lo = 0.0;
             hi = n - 1.0;
-        } else {
-            double s = n * floor(lo / n);
-            lo -= s;
-            hi -= s;
+            b.full[k] = 1;
         }
         b.lo[k] = hi >= lo ? (int)lo : 0;
         b.ext[k] = hi >= lo ? (int)(hi - lo + 1.0) : 0;
@@ -164,15 +170,27 @@ __device__ __forceinline__ int wrapi(int v, int n)
     return v < 0 ? v + n : v;
 }
 
-__device__ __forceinline__ void box_node(const Lat &L, const Box &b, int k, int &x, int &y, int &z)
+// Box entry k: unwrapped coordinates u[3] and the wrapped node (x, y, z).
+__device__ __forceinline__ void box_node(const Lat &L, const Box &b, int k, int u[3], int &x, int &y,
+                                         int &z)
 {
     int bx = k % b.ext[0];
     int t = k / b.ext[0];
     int by = t % b.ext[1];
     int bz = t / b.ext[1];
-    x = wrapi(b.lo[0] + bx, L.nx);
-    y = wrapi(b.lo[1] + by, L.ny);
-    z = wrapi(b.lo[2] + bz, L.nz);
+    u[0] = b.lo[0] + bx;
+    u[1] = b.lo[1] + by;
+    u[2] = b.lo[2] + bz;
+    x = wrapi(u[0], L.nx);
+    y = wrapi(u[1], L.ny);
+    z = wrapi(u[2], L.nz);
+}
+
+// Displacement of a box node from the particle centre X (the centre the box
+// was formed around), equal to the nearest-image displacement.
+__device__ __forceinline__ double box_disp(const Lat &L, const Box &b, int k, int u, int w, double X)
+{
+    return b.full[k] ? node_disp(L, k, w, X) : s_((double)u, X);
 }
 
 __device__ __forceinline__ bool is_wall_z(const Lat &L, int z) { return L.walls && (z == 0 || z == L.nz - 1); }
@@ -250,13 +268,13 @@ __global__ void __launch_bounds__(PT) k_links(Lat L, Parts P, typename S::T *__r
     __syncthreads();
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int k = threadIdx.x; k < box.count; k += PT) {
-        int x, y, z;
-        box_node(L, box, k, x, y, z);
+        int x, y, z, u[3];
+        box_node(L, box, k, u, x, y, z);
         int n = x + L.nx * (y + L.ny * z);
         if (!idx_ok(L, n, L.N, 2)) continue;
         if (owner[n] != (uint32_t)p) continue;
-        float dn[3] = {(float)node_disp(L, 0, x, sX[0]), (float)node_disp(L, 1, y, sX[1]),
-                       (float)node_disp(L, 2, z, sX[2])};
+        float dn[3] = {(float)box_disp(L, box, 0, u[0], x, sX[0]), (float)box_disp(L, box, 1, u[1], y, sX[1]),
+                       (float)box_disp(L, box, 2, u[2], z, sX[2])};
         float aF[3] = {0.f, 0.f, 0.f}, aT[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int i = 1; i < Q; i++) {
@@ -356,60 +374,83 @@ __device__ double hertz_bp(double K, double rp, double ro, const double r[3], co
 
 // One thread per particle i sums the Hertz and lubrication (Eq. 9 with 2R
 // -> σ, R^2 -> (σ/2)^2, only for gaps 0 < r - σ < Δc, opposing the normal
-// approach) contributions of every other particle in index order; an FP32
-// distance test skips pairs beyond reach.
-__global__ void k_pairs(Lat L, Parts P, Pair pp)
+// approach) contributions of every other particle in index order.  The
+// other particles stream through shared memory as FP32 (x, y, z, reach)
+// tiles; a pair is evaluated in FP64 only when the FP32 distance is within
+// reach_i + reach_j + Δc (+0.05 for the FP32 error).
+constexpr int PAIR_T = 128;
+
+__device__ void pair_term(const Lat &L, const Parts &P, const Pair &pp, int i, int j, const double oi[3],
+                          double F[3], double T[3])
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.n) return;
-    double Xi[3] = {P.X[3 * i], P.X[3 * i + 1], P.X[3 * i + 2]};
-    float xi32[3] = {P.X32[3 * i], P.X32[3 * i + 1], P.X32[3 * i + 2]};
-    double Ri[3][3];
-    rotmat(P.q + 4 * i, Ri);
-    double oi[3] = {Ri[0][0], Ri[1][0], Ri[2][0]};
-    double rpi = P.rp[i], roi = P.ro[i];
-    float reach_i = (float)fmax(rpi, roi);
-    float nlat[3] = {(float)L.nx, (float)L.ny, (float)L.nz};
-    double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-    for (int j = 0; j < P.n; j++) {
-        if (j == i) continue;
-        float d2 = 0.f;
-        for (int k = 0; k < 3; k++) {
-            float d = P.X32[3 * j + k] - xi32[k];
-            if (k < 2 || !L.walls) d -= nlat[k] * rintf(d / nlat[k]);
-            d2 += d * d;
-        }
-        float reach = reach_i + (float)fmax(P.rp[j], P.ro[j]) + (float)pp.lub_cut + 0.01f;
-        if (d2 > reach * reach) continue;
-        int a = i < j ? i : j, b = i < j ? j : i;  // pair taken as (a, b), a < b
-        double r[3];
-        for (int k = 0; k < 3; k++) r[k] = pair_disp(L, k, P.X[3 * a + k], P.X[3 * b + k]);
-        double Rj[3][3];
-        rotmat(P.q + 4 * j, Rj);
-        double oj[3] = {Rj[0][0], Rj[1][0], Rj[2][0]};
-        const double *oa = i < j ? oi : oj, *ob = i < j ? oj : oi;
-        double rp = 0.5 * (P.rp[a] + P.rp[b]), ro = 0.5 * (P.ro[a] + P.ro[b]);
-        double fb[3], ta[3], tb[3];
-        double sigma = hertz_bp(pp.k_hertz, rp, ro, r, oa, ob, fb, ta, tb);
-        for (int k = 0; k < 3; k++) {
-            F[k] += i == b ? fb[k] : -fb[k];
-            T[k] += i == a ? ta[k] : tb[k];
-        }
-        double rl = sqrt(dot3(r, r));
-        double h = rl - sigma;
-        if (pp.lub_cut > 0 && h > 0 && h < pp.lub_cut) {
-            double rh[3] = {r[0] / rl, r[1] / rl, r[2] / rl};
-            double du[3] = {P.V[3 * a] - P.V[3 * b], P.V[3 * a + 1] - P.V[3 * b + 1],
-                            P.V[3 * a + 2] - P.V[3 * b + 2]};
-            double K = 3.0 * M_PI * pp.mu * sigma * sigma / 8.0;
-            double s = K * dot3(rh, du) * (1.0 / h - 1.0 / pp.lub_cut);
-            for (int k = 0; k < 3; k++) F[k] += i == a ? -s * rh[k] : s * rh[k];
-        }
-    }
+    int a = i < j ? i : j, b = i < j ? j : i;  // the pair is taken as (a, b), a < b
+    double r[3];
+    for (int k = 0; k < 3; k++) r[k] = pair_disp(L, k, P.X[3 * a + k], P.X[3 * b + k]);
+    double Rj[3][3];
+    rotmat(P.q + 4 * j, Rj);
+    double oj[3] = {Rj[0][0], Rj[1][0], Rj[2][0]};
+    const double *oa = i < j ? oi : oj, *ob = i < j ? oj : oi;
+    double rp = 0.5 * (P.rp[a] + P.rp[b]), ro = 0.5 * (P.ro[a] + P.ro[b]);
+    double fb[3], ta[3], tb[3];
+    double sigma = hertz_bp(pp.k_hertz, rp, ro, r, oa, ob, fb, ta, tb);
     for (int k = 0; k < 3; k++) {
-        P.Fpair[3 * i + k] = F[k];
-        P.Tpair[3 * i + k] = T[k];
+        F[k] += i == b ? fb[k] : -fb[k];
+        T[k] += i == a ? ta[k] : tb[k];
     }
+    double rl = sqrt(dot3(r, r));
+    double h = rl - sigma;
+    if (pp.lub_cut > 0 && h > 0 && h < pp.lub_cut) {
+        double rh[3] = {r[0] / rl, r[1] / rl, r[2] / rl};
+        double du[3] = {P.V[3 * a] - P.V[3 * b], P.V[3 * a + 1] - P.V[3 * b + 1], P.V[3 * a + 2] - P.V[3 * b + 2]};
+        double K = 3.0 * M_PI * pp.mu * sigma * sigma / 8.0;
+        double s = K * dot3(rh, du) * (1.0 / h - 1.0 / pp.lub_cut);
+        for (int k = 0; k < 3; k++) F[k] += i == a ? -s * rh[k] : s * rh[k];
+    }
+}
+
+__global__ void __launch_bounds__(PAIR_T) k_pairs(Lat L, Parts P, Pair pp)
+{
+    __shared__ float4 tile[PAIR_T];
+    int i = blockIdx.x * PAIR_T + threadIdx.x;
+    bool act = i < P.n;
+    float4 me = act ? P.X32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    double oi[3] = {0, 0, 0};
+    if (act) {
+        double Ri[3][3];
+        rotmat(P.q + 4 * i, Ri);
+        oi[0] = Ri[0][0];
+        oi[1] = Ri[1][0];
+        oi[2] = Ri[2][0];
+    }
+    float nl[3] = {(float)L.nx, (float)L.ny, (float)L.nz};
+    float inv[3] = {1.f / nl[0], 1.f / nl[1], 1.f / nl[2]};
+    bool per_z = !L.walls;
+    float extra = (float)pp.lub_cut + 0.05f;
+    double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+    for (int base = 0; base < P.n; base += PAIR_T) {
+        int j = base + threadIdx.x;
+        tile[threadIdx.x] = j < P.n ? P.X32[j] : make_float4(0.f, 0.f, 0.f, -1e30f);
+        __syncthreads();
+        if (act) {
+            int lim = min(PAIR_T, P.n - base);
+            for (int t = 0; t < lim; t++) {
+                float4 o = tile[t];
+                float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
+                dx -= nl[0] * rintf(dx * inv[0]);
+                dy -= nl[1] * rintf(dy * inv[1]);
+                if (per_z) dz -= nl[2] * rintf(dz * inv[2]);
+                float reach = me.w + o.w + extra;
+                if (dx * dx + dy * dy + dz * dz <= reach * reach && base + t != i)
+                    pair_term(L, P, pp, i, base + t, oi, F, T);
+            }
+        }
+        __syncthreads();
+    }
+    if (act)
+        for (int k = 0; k < 3; k++) {
+            P.Fpair[3 * i + k] = F[k];
+            P.Tpair[3 * i + k] = T[k];
+        }
 }
 
 // ------------------------------------------------------------ integrate
@@ -498,11 +539,15 @@ __global__ void k_integrate(Lat L, Parts P, int mode)
             if (X[k] >= n) X[k] -= n;
         }
         P.X[3 * p + k] = X[k];
-        P.X32[3 * p + k] = (float)X[k];
         P.V[3 * p + k] = V[k];
         P.W[3 * p + k] = W[k];
     }
     for (int k = 0; k < 4; k++) P.q[4 * p + k] = q[k];
+    float4 x32 = P.X32[p];
+    x32.x = (float)X[0];
+    x32.y = (float)X[1];
+    x32.z = (float)X[2];
+    P.X32[p] = x32;
 }
 
 // ---------------------------------------------------------------- claim
@@ -515,21 +560,41 @@ __global__ void __launch_bounds__(PT) k_claim(Lat L, Parts P, uint32_t *__restri
     __shared__ Box box;
     __shared__ Geo geo;
     __shared__ double sX[3];
+    __shared__ int sXi[3];
+    __shared__ float sXf[3];
     if (threadIdx.x == 0) {
         geo_of(P.q + 4 * p, P.rp[p], P.ro[p], geo);
         double lo[3], hi[3];
         box_of(L, P.X + 3 * p, geo.R, P.rp[p], P.ro[p], lo, hi);
         finish_box(L, lo, hi, box);
-        for (int k = 0; k < 3; k++) sX[k] = P.X[3 * p + k];
+        for (int k = 0; k < 3; k++) {
+            sX[k] = P.X[3 * p + k];
+            // X = Xi + Xf, Xi integral: the FP32 displacement (u - Xi) - Xf
+            // carries no large cancellation (box_of bounds |X| < 1e9)
+            double fl = floor(sX[k]);
+            sXi[k] = box.count ? (int)fl : 0;
+            sXf[k] = (float)(sX[k] - fl);
+        }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < box.count; k += PT) {
-        int x, y, z;
-        box_node(L, box, k, x, y, z);
+        int x, y, z, u[3];
+        box_node(L, box, k, u, x, y, z);
         if (is_wall_z(L, z)) continue;
-        double dx[3] = {node_disp(L, 0, x, sX[0]), node_disp(L, 1, y, sX[1]), node_disp(L, 2, z, sX[2])};
+        float d32[3];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            d32[a] = box.full[a] ? (float)node_disp(L, a, a == 0 ? x : (a == 1 ? y : z), sX[a])
+                                 : (float)(u[a] - sXi[a]) - sXf[a];
+        float q32;
+        bool in = inside_q32(geo, d32, q32);
+        if (!in && q32 <= 1.001f) {
+            double dx[3] = {box_disp(L, box, 0, u[0], x, sX[0]), box_disp(L, box, 1, u[1], y, sX[1]),
+                            box_disp(L, box, 2, u[2], z, sX[2])};
+            in = inside_exact(geo, dx);
+        }
         int n = x + L.nx * (y + L.ny * z);
-        if (idx_ok(L, n, L.N, 4) && inside(geo, dx)) atomicMin(owner_new + n, (uint32_t)p);
+        if (in && idx_ok(L, n, L.N, 4)) atomicMin(owner_new + n, (uint32_t)p);
     }
 }
 
@@ -587,8 +652,8 @@ __global__ void __launch_bounds__(PT) k_transition(Lat L, Parts P, typename S::T
     __syncthreads();
     double acc[6] = {0, 0, 0, 0, 0, 0};
     for (int k = threadIdx.x; k < box.count; k += PT) {
-        int x, y, z;
-        box_node(L, box, k, x, y, z);
+        int x, y, z, u[3];
+        box_node(L, box, k, u, x, y, z);
         int n = x + L.nx * (y + L.ny * z);
         if (!idx_ok(L, n, L.N, 5)) continue;
         uint32_t o = own_old[n], w = own_new[n];
@@ -692,8 +757,8 @@ __global__ void __launch_bounds__(PT) k_reset(Lat L, Parts P, int use_old, uint3
     }
     __syncthreads();
     for (int k = threadIdx.x; k < box.count; k += PT) {
-        int x, y, z;
-        box_node(L, box, k, x, y, z);
+        int x, y, z, u[3];
+        box_node(L, box, k, u, x, y, z);
         int n = x + L.nx * (y + L.ny * z);
         if (idx_ok(L, n, L.N, 7)) owner[n] = NONE;
     }
@@ -740,7 +805,7 @@ void launch_links(int storage, const Lat &L, const Parts &P, void *fnew, const f
 void launch_pairs(const Lat &L, const Parts &P, const Pair &pp, cudaStream_t s)
 {
     if (P.n == 0) return;
-    k_pairs<<<(P.n + 127) / 128, 128, 0, s>>>(L, P, pp);
+    k_pairs<<<(P.n + PAIR_T - 1) / PAIR_T, PAIR_T, 0, s>>>(L, P, pp);
 }
 
 void launch_integrate(const Lat &L, const Parts &P, int mode, cudaStream_t s)

@@ -14,6 +14,7 @@ Q = 19
 
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 MODES = {"free": 0, "static": 1, "prescribed": 2}
+FLAG_TWO_PASS = 1
 
 STATUS = {0: "LBE_OK", -1: "LBE_EINVAL", -2: "LBE_ENOMEM", -3: "LBE_ECUDA", -4: "LBE_ENUMERIC",
           -5: "LBE_EOVERLAP", -6: "LBE_ETIMEOUT", -7: "LBE_EBUSY"}
@@ -40,7 +41,7 @@ class LatticeDesc(ctypes.Structure):
         ("lub_rho", ctypes.c_double),
         ("cuda_stream", ctypes.c_void_p),
         ("device", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("flags", ctypes.c_int32),
     ]
 
 
@@ -94,7 +95,7 @@ def _f64(a, shape=None):
 
 def make_desc(shape, walls_z=False, tau=(1.0, 1.0), g_br=0.1, body_force=(0.0, 0.0, 0.0),
               rho_ref=(0.37, 0.37), storage="f32", particle_mode="free", k_hertz=100.0,
-              lub_cut=2.0 / 3.0, lub_rho=1.4, stream=None, device=-1):
+              lub_cut=2.0 / 3.0, lub_rho=1.4, stream=None, device=-1, flags=0):
     nx, ny, nz = shape
     d = LatticeDesc()
     d.nx, d.ny, d.nz = nx, ny, nz
@@ -111,7 +112,7 @@ def make_desc(shape, walls_z=False, tau=(1.0, 1.0), g_br=0.1, body_force=(0.0, 0
     d.lub_rho = lub_rho
     d.cuda_stream = stream
     d.device = int(device)
-    d.reserved = 0
+    d.flags = int(flags)
     return d
 
 

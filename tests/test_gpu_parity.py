@@ -32,15 +32,21 @@ def _add(g, r, **p):
                         vel=p.get("vel"), omega=p.get("omega"))
 
 
+@pytest.mark.parametrize("flags", [0, lbe.FLAG_TWO_PASS])
 @pytest.mark.parametrize("shape,walls,tau", [((8, 8, 8), False, (1.0, 1.0)),
                                              ((13, 7, 5), True, (0.8, 1.3)),
-                                             ((33, 17, 9), False, (1.0, 0.7))])
-def test_one_step_populations(shape, walls, tau):
-    """Several tiles plus a ragged tail, walls or not, τ ≠ 1."""
+                                             ((33, 17, 9), False, (1.0, 0.7)),
+                                             ((70, 35, 40), True, (1.0, 1.0))])
+def test_one_step_populations(shape, walls, tau, flags):
+    """Several tiles plus a ragged tail (the fused kernel's tiles are 32x16
+    and walk z in chunks), walls or not, τ ≠ 1; fused and two-pass fluid
+    kernels."""
     nx, ny, nz = shape
     f0 = W.random_populations(shape, seed=21)
-    g, r = _pair(shape, np.full((2, nz, ny, nx), 0.5), walls_z=walls, tau=tau, g_br=0.1,
-                 body_force=(1e-4, 0.0, -2e-4))
+    g = lbe.Lattice(shape, np.full((2, nz, ny, nx), 0.5), walls_z=walls, tau=tau, g_br=0.1,
+                    body_force=(1e-4, 0.0, -2e-4), flags=flags)
+    r = lbref.Lattice(shape, np.full((2, nz, ny, nx), 0.5), walls_z=walls, tau=tau, g_br=0.1,
+                      body_force=(1e-4, 0.0, -2e-4))
     g.set_populations(f0)
     r.set_populations(f0)
     g.step(1)
@@ -51,10 +57,12 @@ def test_one_step_populations(shape, walls, tau):
     assert np.max(np.abs(fg[:, :, fl] - fr[:, :, fl])) < TOL_F_ONE_STEP
 
 
-def test_spinodal_densities_many_steps():
+@pytest.mark.parametrize("flags", [0, lbe.FLAG_TWO_PASS])
+def test_spinodal_densities_many_steps(flags):
     shape = (24, 20, 16)
     rho0 = W.uniform_mixture(shape, 0.7, 0.01, seed=22)
-    g, r = _pair(shape, rho0, g_br=0.1)
+    g = lbe.Lattice(shape, rho0, g_br=0.1, flags=flags)
+    r = lbref.Lattice(shape, rho0, g_br=0.1)
     g.step(60)
     r.step(60)
     rg, vg, _ = g.read_fields()
@@ -106,12 +114,14 @@ def test_prescribed_motion_fill_empty():
     assert np.max(np.abs(pg["force"] - pr["force"])) < 1e-4 * max(1.0, np.abs(pr["force"]).max())
 
 
-def test_adsorption_box_200_steps():
+@pytest.mark.parametrize("flags", [0, lbe.FLAG_TWO_PASS])
+def test_adsorption_box_200_steps(flags):
     """The 32x32x48 adsorption box with one free prolate ellipsoid (r_par 6,
     r_perp 3) tilted 45 degrees on the interface, 200 steps: densities within
     1e-5, particle position and orientation within 1e-5."""
     w = W.adsorption_box()
-    g, r = _pair(w.shape, w.rho0, **w.params)
+    g = lbe.Lattice(w.shape, w.rho0, flags=flags, **w.params)
+    r = lbref.Lattice(w.shape, w.rho0, **w.params)
     p = w.particles
     _add(g, r, **p)
     g.step(w.steps)
