@@ -59,12 +59,12 @@ template <class S>
 __device__ __forceinline__ const typename S::T *slot(const typename S::T *f, const Lat &L, int c,
                                                      int i)
 {
-    return f + (size_t)(c * Q + i) * (size_t)L.N;
+    return f + (size_t)(c * Q + i) * (size_t)L.S;
 }
 template <class S>
 __device__ __forceinline__ typename S::T *slot(typename S::T *f, const Lat &L, int c, int i)
 {
-    return f + (size_t)(c * Q + i) * (size_t)L.N;
+    return f + (size_t)(c * Q + i) * (size_t)L.S;
 }
 
 // ---------------------------------------------------------------- init
@@ -392,7 +392,8 @@ __global__ void k_get_f(Lat L, const typename S::T *__restrict__ f, double *__re
     size_t tot = (size_t)2 * Q * L.N;
     if (k >= tot) return;
     int ci = (int)(k / L.N);
-    out[k] = (double)S::cvt(f[k], L.base[ci / Q][ci % Q]);
+    size_t n = k - (size_t)ci * L.N;
+    out[k] = (double)S::cvt(f[(size_t)ci * L.S + n], L.base[ci / Q][ci % Q]);
 }
 
 template <class S>
@@ -402,7 +403,8 @@ __global__ void k_set_f(Lat L, const double *__restrict__ in, typename S::T *__r
     size_t tot = (size_t)2 * Q * L.N;
     if (k >= tot) return;
     int ci = (int)(k / L.N);
-    f[k] = S::enc((float)in[k], L.base[ci / Q][ci % Q]);
+    size_t n = k - (size_t)ci * L.N;
+    f[(size_t)ci * L.S + n] = S::enc((float)in[k], L.base[ci / Q][ci % Q]);
 }
 
 inline unsigned blocks_for(size_t n, int t) { return (unsigned)((n + t - 1) / t); }

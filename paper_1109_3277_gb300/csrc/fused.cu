@@ -6,29 +6,30 @@
 // A CTA owns a TX x TY column of nodes and walks a chunk of z planes.  For
 // every plane it computes ρ and ψ of the tile plus a one-node halo into a
 // three-plane ring in shared memory (solid nodes take the shell ψ written by
-// the shell-fill kernel), together with the moments of its own nodes; the
-// force at a node then reads its 18 neighbours' ψ from shared memory.  The
-// populations of a plane are read from HBM once (the ρ pass) and again from
-// L1/L2 by the collision; the halo costs re-reads that the neighbouring
-// CTAs' own loads keep in L2.
+// the shell-fill kernel), together with the moments of its own nodes.  The
+// own nodes' populations are read from HBM once, in that density pass, and
+// staged in shared memory (two plane buffers) for the collision one plane
+// later; the force at a node reads its 18 neighbours' ψ from shared memory.
+// The halo densities re-read neighbouring tiles' populations, which their
+// own CTAs are streaming through L2 at the same time.
 #include "lbe_internal.cuh"
 
 namespace lbe {
 
 namespace {
 
-constexpr int TX = 32, TY = 16, NT = TX * TY;
+constexpr int TX = 32, TY = 8, NT = TX * TY;
 constexpr int HX = TX + 2, HY = TY + 2, HN = HX * HY, NHALO = HN - NT;
 
 template <class S>
 __device__ __forceinline__ const typename S::T *cslot(const typename S::T *f, const Lat &L, int c, int i)
 {
-    return f + (size_t)(c * Q + i) * (size_t)L.N;
+    return f + (size_t)(c * Q + i) * (size_t)L.S;
 }
 template <class S>
 __device__ __forceinline__ typename S::T *wslot(typename S::T *f, const Lat &L, int c, int i)
 {
-    return f + (size_t)(c * Q + i) * (size_t)L.N;
+    return f + (size_t)(c * Q + i) * (size_t)L.S;
 }
 
 __device__ __forceinline__ int wrapc(int v, int n)
@@ -37,23 +38,37 @@ __device__ __forceinline__ int wrapc(int v, int n)
     return v < 0 ? v + n : v;
 }
 
+// Dynamic shared memory layout (bytes).
 template <class S>
-__global__ void __launch_bounds__(NT, 2) k_fused(Lat L, const typename S::T *__restrict__ fin,
+struct Smem {
+    static constexpr size_t fbuf = 0;                                          // T [2][2Q][NT]
+    static constexpr size_t sps = fbuf + 2 * 2 * Q * NT * sizeof(typename S::T);  // float [3][2][HN]
+    static constexpr size_t smo = sps + 3 * 2 * HN * sizeof(float);             // float [2][5][NT]
+    static constexpr size_t sty = smo + 2 * 5 * NT * sizeof(float);             // uint8 [3][HN]
+    static constexpr size_t bytes = sty + 3 * HN;
+};
+
+template <class S>
+__global__ void __launch_bounds__(NT) k_fused(Lat L, const typename S::T *__restrict__ fin,
                                               typename S::T *__restrict__ fout,
                                               const float *__restrict__ psi,
                                               const uint8_t *__restrict__ type, int zc)
 {
-    __shared__ float sps[3][2][HN];   // ψ ring, indexed by plane mod 3
-    __shared__ uint8_t sty[3][HN];    // node types, same ring
-    __shared__ float smo[2][5][NT];   // own-node ρ0, ρ1, u' (by plane parity)
+    using T = typename S::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *fbuf = reinterpret_cast<T *>(smem + Smem<S>::fbuf);        // [parity][c*Q+i][tid]
+    float *sps = reinterpret_cast<float *>(smem + Smem<S>::sps);  // [slot][c][e]
+    float *smo = reinterpret_cast<float *>(smem + Smem<S>::smo);  // [parity][k][tid]
+    uint8_t *sty = smem + Smem<S>::sty;                           // [slot][e]
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int zb = blockIdx.z * zc, ze = min(zb + zc, L.nz);
     const int gx = wrapc(x0 + tx, L.nx), gy = wrapc(y0 + ty, L.ny);
     const bool active = (x0 + tx < L.nx) && (y0 + ty < L.ny);
 
-    // ρ and ψ (and for own nodes the moments) of plane zz into the ring.
-    auto load_plane = [&](int zz, bool own_moments) {
+    // ρ and ψ of plane zz (tile + halo) into the ring; for own nodes also
+    // the moments and, when own_pops, the raw populations (plane parity).
+    auto load_plane = [&](int zz, bool own_pops) {
         const int slot = (zz + 3) % 3;
         bool zin = true;
         int gz = zz;
@@ -62,7 +77,6 @@ __global__ void __launch_bounds__(NT, 2) k_fused(Lat L, const typename S::T *__r
         } else {
             gz = zz < 0 ? zz + L.nz : (zz >= L.nz ? zz - L.nz : zz);
         }
-        // own node
         {
             const int e = (ty + 1) * HX + (tx + 1);
             float p0 = 0.f, p1 = 0.f;
@@ -71,13 +85,17 @@ __global__ void __launch_bounds__(NT, 2) k_fused(Lat L, const typename S::T *__r
                 const int n = gx + L.nx * (gy + L.ny * gz);
                 t = type[n];
                 if (t == FLUID) {
+                    const int par = zz & 1;
+                    T *fb = fbuf + (size_t)par * 2 * Q * NT + tid;
                     float r[2], j[2][3];
 #pragma unroll
                     for (int c = 0; c < 2; c++) {
                         float a = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
                         for (int i = 0; i < Q; i++) {
-                            float v = S::ld(cslot<S>(fin, L, c, i) + n, L.base[c][i]);
+                            const T raw = __ldg(cslot<S>(fin, L, c, i) + n);
+                            if (own_pops) fb[(c * Q + i) * NT] = raw;
+                            const float v = S::cvt(raw, L.base[c][i]);
                             a += v;
                             if (cx(i)) jx += cx(i) * v;
                             if (cy(i)) jy += cy(i) * v;
@@ -90,24 +108,23 @@ __global__ void __launch_bounds__(NT, 2) k_fused(Lat L, const typename S::T *__r
                     }
                     p0 = 1.f - expf(-r[0]);
                     p1 = 1.f - expf(-r[1]);
-                    if (own_moments) {
-                        const int par = zz & 1;
-                        float den = r[0] * L.itau[0] + r[1] * L.itau[1];
-                        smo[par][0][tid] = r[0];
-                        smo[par][1][tid] = r[1];
+                    if (own_pops) {
+                        float *mo = smo + (size_t)par * 5 * NT + tid;
+                        const float den = r[0] * L.itau[0] + r[1] * L.itau[1];
+                        mo[0] = r[0];
+                        mo[NT] = r[1];
 #pragma unroll
                         for (int k = 0; k < 3; k++)
-                            smo[par][2 + k][tid] =
-                                den > 0.f ? (j[0][k] * L.itau[0] + j[1][k] * L.itau[1]) / den : 0.f;
+                            mo[(2 + k) * NT] = den > 0.f ? (j[0][k] * L.itau[0] + j[1][k] * L.itau[1]) / den : 0.f;
                     }
                 } else {
                     p0 = psi[n];
                     p1 = psi[(size_t)L.N + n];
                 }
             }
-            sps[slot][0][e] = p0;
-            sps[slot][1][e] = p1;
-            sty[slot][e] = t;
+            sps[(slot * 2 + 0) * HN + e] = p0;
+            sps[(slot * 2 + 1) * HN + e] = p1;
+            sty[slot * HN + e] = t;
         }
         // halo ring: top row, bottom row, left column, right column
         if (tid < NHALO) {
@@ -146,22 +163,22 @@ __global__ void __launch_bounds__(NT, 2) k_fused(Lat L, const typename S::T *__r
                     p1 = psi[(size_t)L.N + n];
                 }
             }
-            sps[slot][0][e] = p0;
-            sps[slot][1][e] = p1;
-            sty[slot][e] = t;
+            sps[(slot * 2 + 0) * HN + e] = p0;
+            sps[(slot * 2 + 1) * HN + e] = p1;
+            sty[slot * HN + e] = t;
         }
     };
 
     load_plane(zb - 1, false);
     load_plane(zb, true);
-    // neighbour coordinates of the own node (x, y fixed for the column)
     const int xs[3] = {gx == 0 ? L.nx - 1 : gx - 1, gx, gx == L.nx - 1 ? 0 : gx + 1};
     const int ys[3] = {gy == 0 ? L.ny - 1 : gy - 1, gy, gy == L.ny - 1 ? 0 : gy + 1};
+    const int ec = (ty + 1) * HX + (tx + 1);
     for (int z = zb; z < ze; z++) {
         load_plane(z + 1, z + 1 < ze);
         __syncthreads();
-        const int sc = z % 3, ec = (ty + 1) * HX + (tx + 1);
-        if (active && sty[sc][ec] == FLUID) {
+        const int sc = z % 3;
+        if (active && sty[sc * HN + ec] == FLUID) {
             const int n = gx + L.nx * (gy + L.ny * z);
             int zs[3];
             if (L.walls) {
@@ -173,22 +190,23 @@ __global__ void __launch_bounds__(NT, 2) k_fused(Lat L, const typename S::T *__r
             }
             zs[1] = z;
             const int par = z & 1;
-            const float rho[2] = {smo[par][0][tid], smo[par][1][tid]};
-            const float up[3] = {smo[par][2][tid], smo[par][3][tid], smo[par][4][tid]};
-            // Σ_i ψ^{c'}(x + c_i) c_i from shared memory; neighbour types
+            const float *mo = smo + (size_t)par * 5 * NT + tid;
+            const float rho[2] = {mo[0], mo[NT]};
+            const float up[3] = {mo[2 * NT], mo[3 * NT], mo[4 * NT]};
+            const T *fb = fbuf + (size_t)par * 2 * Q * NT + tid;
             float s[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
             uint32_t solid = 0;  // bit i: neighbour i is not fluid
 #pragma unroll
             for (int i = 1; i < Q; i++) {
                 const int sl = (z + cz(i) + 3) % 3;
                 const int e = (ty + 1 + cy(i)) * HX + (tx + 1 + cx(i));
-                const float p0 = sps[sl][0][e], p1 = sps[sl][1][e];
-                if (sty[sl][e] != FLUID) solid |= 1u << i;
+                const float p0 = sps[(sl * 2 + 0) * HN + e], p1 = sps[(sl * 2 + 1) * HN + e];
+                if (sty[sl * HN + e] != FLUID) solid |= 1u << i;
                 if (cx(i)) { s[0][0] += cx(i) * p1; s[1][0] += cx(i) * p0; }
                 if (cy(i)) { s[0][1] += cy(i) * p1; s[1][1] += cy(i) * p0; }
                 if (cz(i)) { s[0][2] += cz(i) * p1; s[1][2] += cz(i) * p0; }
             }
-            const float pc[2] = {sps[sc][0][ec], sps[sc][1][ec]};
+            const float pc[2] = {sps[(sc * 2 + 0) * HN + ec], sps[(sc * 2 + 1) * HN + ec]};
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 const float r = rho[c];
@@ -203,7 +221,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused(Lat L, const typename S::T *__r
                 float seq = 0.f;
 #pragma unroll
                 for (int i = 1; i < Q; i++) {
-                    const float fi = S::ld(cslot<S>(fin, L, c, i) + n, L.base[c][i]);
+                    const float fi = S::cvt(fb[(c * Q + i) * NT], L.base[c][i]);
                     const float cu = cx(i) * ue[0] + cy(i) * ue[1] + cz(i) * ue[2];
                     const float feq = wgt(i) * r * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
                     seq += feq;
@@ -216,7 +234,7 @@ __global__ void __launch_bounds__(NT, 2) k_fused(Lat L, const typename S::T *__r
                     }
                 }
                 // rest population: equilibrium ρ - Σ_{i>0} f^eq_i (exact mass)
-                const float f0 = S::ld(cslot<S>(fin, L, c, 0) + n, L.base[c][0]);
+                const float f0 = S::cvt(fb[(c * Q) * NT], L.base[c][0]);
                 const float fs0 = f0 - (f0 - (r - seq)) * it;
                 S::st(wslot<S>(fout, L, c, 0) + n, fs0, L.base[c][0]);
             }
@@ -246,13 +264,24 @@ int fused_zchunk(const Lat &L)
     return zc;
 }
 
+template <class S>
+static void launch_fused_t(const Lat &L, const void *fin, void *fout, const float *psi, const uint8_t *type,
+                           cudaStream_t s)
+{
+    static bool configured = false;  // the attribute is per function, set once per process
+    if (!configured) {
+        cudaFuncSetAttribute(k_fused<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem<S>::bytes);
+        configured = true;
+    }
+    const int zc = fused_zchunk(L);
+    dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
+    k_fused<S><<<grid, NT, Smem<S>::bytes, s>>>(L, (const typename S::T *)fin, (typename S::T *)fout, psi, type, zc);
+}
+
 void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
                   const uint8_t *type, cudaStream_t s)
 {
-    const int zc = fused_zchunk(L);
-    dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
-    LBE_DISPATCH(storage, (k_fused<S><<<grid, NT, 0, s>>>(L, (const typename S::T *)fin, (typename S::T *)fout,
-                                                          psi, type, zc)));
+    LBE_DISPATCH(storage, (launch_fused_t<S>(L, fin, fout, psi, type, s)));
 }
 
 }  // namespace lbe

@@ -247,6 +247,7 @@ lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_c
     L.nz = d->nz;
     L.walls = d->walls_z ? 1 : 0;
     L.N = (int)N;
+    L.S = ((N + 127) / 128) * 128 + 384;
     for (int k = 0; k < 2; k++) {
         L.tau[k] = (float)d->tau[k];
         L.itau[k] = (float)(1.0 / d->tau[k]);
@@ -276,7 +277,7 @@ lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_c
         if (e != cudaSuccess) return bail(e, "cudaStreamCreate");
         c->own_stream = true;
     }
-    size_t fbytes = (size_t)2 * Q * N * c->esize;
+    size_t fbytes = (size_t)2 * Q * L.S * c->esize;
     if ((e = dalloc(c, &c->f[0], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f0)");
     if ((e = dalloc(c, &c->f[1], fbytes)) != cudaSuccess) return bail(e, "cudaMalloc(f1)");
     if ((e = dalloc(c, &c->rho, (size_t)2 * N * sizeof(float))) != cudaSuccess) return bail(e, "cudaMalloc(rho)");

@@ -67,6 +67,8 @@ struct StBF16 {
 struct Lat {
     int nx, ny, nz, walls;
     int N;                 // nodes (< 2^31)
+    long long S;           // elements per population array (>= N, padded so the
+                           // 38 arrays are not a power of two apart)
     float tau[2], itau[2];
     float g;
     float body[3];

@@ -219,7 +219,7 @@ __device__ void block_sum(double (&v)[K], double (*sh)[PT / 32])
 template <class S>
 __device__ __forceinline__ typename S::T *slot(typename S::T *f, const Lat &L, int c, int i)
 {
-    return f + (size_t)(c * Q + i) * (size_t)L.N;
+    return f + (size_t)(c * Q + i) * (size_t)L.S;
 }
 
 __device__ __forceinline__ int nbr_node(const Lat &L, int x, int y, int z, int i)
