@@ -12,6 +12,12 @@
 // later; the force at a node reads its 18 neighbours' ψ from shared memory.
 // The halo densities re-read neighbouring tiles' populations, which their
 // own CTAs are streaming through L2 at the same time.
+//
+// Links into particle nodes get the moving bounce-back term C (Eq. 4) in
+// registers as they are reflected, and their momentum exchange (Eq. 5) and
+// torque go to a per-CTA table of per-particle sums in shared memory (FP32
+// atomics), flushed to the FP64 per-particle totals with atomics at the end:
+// the sums are exact to FP32 rounding but their order is not fixed.
 #include "lbe_internal.cuh"
 
 namespace lbe {
@@ -38,33 +44,95 @@ __device__ __forceinline__ int wrapc(int v, int n)
     return v < 0 ? v + n : v;
 }
 
+constexpr int TAB = 128;  // per-CTA particle table (power of two)
+
 // Dynamic shared memory layout (bytes).
 template <class S>
 struct Smem {
     static constexpr size_t fbuf = 0;                                          // T [2][2Q][NT]
     static constexpr size_t sps = fbuf + 2 * 2 * Q * NT * sizeof(typename S::T);  // float [3][2][HN]
     static constexpr size_t smo = sps + 3 * 2 * HN * sizeof(float);             // float [2][5][NT]
-    static constexpr size_t sty = smo + 2 * 5 * NT * sizeof(float);             // uint8 [3][HN]
+    static constexpr size_t tacc = smo + 2 * 5 * NT * sizeof(float);           // float [6][TAB]
+    static constexpr size_t tid_ = tacc + 6 * TAB * sizeof(float);              // int [TAB]
+    static constexpr size_t sty = tid_ + TAB * sizeof(int);                     // uint8 [3][HN]
     static constexpr size_t bytes = sty + 3 * HN;
+};
+
+// Slot of particle p in the CTA's table (linear probing, at most TAB
+// probes); -1 when the table is full.
+__device__ __forceinline__ int tab_slot(int *ids, int p)
+{
+    int h = (int)(((unsigned)p * 2654435761u) >> 25) & (TAB - 1);
+    for (int k = 0; k < TAB; k++) {
+        int cur = *(volatile int *)&ids[h];
+        if (cur == p) return h;
+        if (cur == -1) {
+            int old = atomicCAS(&ids[h], -1, p);
+            if (old == -1 || old == p) return h;
+        }
+        h = (h + 1) & (TAB - 1);
+    }
+    return -1;
+}
+
+// Offsets of the population arrays, per lattice, passed with the launch:
+// pop[c*Q+i] = (c*Q+i)*S and push[c*Q+i] = pop[c*Q+i] + (cx + cy*nx + cz*nx*ny),
+// so the address of a load or of an interior push is one add.
+struct FusedOfs {
+    long long pop[2 * Q];
+    long long push[2 * Q];
 };
 
 template <class S>
 __global__ void __launch_bounds__(NT) k_fused(Lat L, const typename S::T *__restrict__ fin,
                                               typename S::T *__restrict__ fout,
                                               const float *__restrict__ psi,
-                                              const uint8_t *__restrict__ type, int zc)
+                                              const uint8_t *__restrict__ type, int zc, Links lk,
+                                              FusedOfs ofs)
 {
     using T = typename S::T;
     extern __shared__ __align__(16) unsigned char smem[];
-    T *fbuf = reinterpret_cast<T *>(smem + Smem<S>::fbuf);        // [parity][c*Q+i][tid]
-    float *sps = reinterpret_cast<float *>(smem + Smem<S>::sps);  // [slot][c][e]
-    float *smo = reinterpret_cast<float *>(smem + Smem<S>::smo);  // [parity][k][tid]
-    uint8_t *sty = smem + Smem<S>::sty;                           // [slot][e]
+    T *fbuf = reinterpret_cast<T *>(smem + Smem<S>::fbuf);          // [parity][c*Q+i][tid]
+    float *sps = reinterpret_cast<float *>(smem + Smem<S>::sps);    // [slot][c][e]
+    float *smo = reinterpret_cast<float *>(smem + Smem<S>::smo);    // [parity][k][tid]
+    uint8_t *sty = smem + Smem<S>::sty;                             // [slot][e]
+    float *tacc = reinterpret_cast<float *>(smem + Smem<S>::tacc);  // [k][TAB]
+    int *tids = reinterpret_cast<int *>(smem + Smem<S>::tid_);      // [TAB]
+    for (int e = threadIdx.x; e < TAB; e += NT) {
+        tids[e] = -1;
+#pragma unroll
+        for (int k = 0; k < 6; k++) tacc[k * TAB + e] = 0.f;
+    }
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int zb = blockIdx.z * zc, ze = min(zb + zc, L.nz);
     const int gx = wrapc(x0 + tx, L.nx), gy = wrapc(y0 + ty, L.ny);
     const bool active = (x0 + tx < L.nx) && (y0 + ty < L.ny);
+    const int nxy = L.nx * L.ny;
+    const int ec = (ty + 1) * HX + (tx + 1);
+
+    // halo entry of this thread (threads tid < NHALO): top row, bottom row,
+    // left column, right column of the (TX+2) x (TY+2) tile
+    int he = 0, hn2 = 0;
+    if (tid < NHALO) {
+        int hx, hy;
+        if (tid < HX) {
+            hx = tid;
+            hy = 0;
+        } else if (tid < 2 * HX) {
+            hx = tid - HX;
+            hy = HY - 1;
+        } else if (tid < 2 * HX + TY) {
+            hx = 0;
+            hy = tid - 2 * HX + 1;
+        } else {
+            hx = HX - 1;
+            hy = tid - 2 * HX - TY + 1;
+        }
+        he = hy * HX + hx;
+        hn2 = wrapc(x0 + hx - 1, L.nx) + L.nx * wrapc(y0 + hy - 1, L.ny);
+    }
+    const int own2 = gx + L.nx * gy;
 
     // ρ and ψ of plane zz (tile + halo) into the ring; for own nodes also
     // the moments and, when own_pops, the raw populations (plane parity).
@@ -77,31 +145,41 @@ __global__ void __launch_bounds__(NT) k_fused(Lat L, const typename S::T *__rest
         } else {
             gz = zz < 0 ? zz + L.nz : (zz >= L.nz ? zz - L.nz : zz);
         }
+        float *ps = sps + slot * 2 * HN;
+        uint8_t *ts = sty + slot * HN;
         {
-            const int e = (ty + 1) * HX + (tx + 1);
             float p0 = 0.f, p1 = 0.f;
             uint8_t t = WALL;
             if (zin) {
-                const int n = gx + L.nx * (gy + L.ny * gz);
+                const int n = own2 + nxy * gz;
                 t = type[n];
                 if (t == FLUID) {
                     const int par = zz & 1;
-                    T *fb = fbuf + (size_t)par * 2 * Q * NT + tid;
+                    T *fb = fbuf + par * 2 * Q * NT + tid;
+                    const T *src = fin + n;
                     float r[2], j[2][3];
 #pragma unroll
                     for (int c = 0; c < 2; c++) {
-                        float a = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+                        float v[Q];
 #pragma unroll
                         for (int i = 0; i < Q; i++) {
-                            const T raw = __ldg(cslot<S>(fin, L, c, i) + n);
+                            const T raw = __ldg(src + ofs.pop[c * Q + i]);
                             if (own_pops) fb[(c * Q + i) * NT] = raw;
-                            const float v = S::cvt(raw, L.base[c][i]);
-                            a += v;
-                            if (cx(i)) jx += cx(i) * v;
-                            if (cy(i)) jy += cy(i) * v;
-                            if (cz(i)) jz += cz(i) * v;
+                            v[i] = S::cvt(raw, L.base[c][i]);
                         }
+                        float a = v[0];
+#pragma unroll
+                        for (int i = 1; i < Q; i++) a += v[i];
                         r[c] = a;
+                        // opposite pairs (i, i+1): c_{i+1} = -c_i
+                        float jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+                        for (int i = 1; i < Q; i += 2) {
+                            const float d = v[i] - v[i + 1];
+                            if (cx(i)) jx += cx(i) * d;
+                            if (cy(i)) jy += cy(i) * d;
+                            if (cz(i)) jz += cz(i) * d;
+                        }
                         j[c][0] = jx;
                         j[c][1] = jy;
                         j[c][2] = jz;
@@ -109,52 +187,36 @@ __global__ void __launch_bounds__(NT) k_fused(Lat L, const typename S::T *__rest
                     p0 = 1.f - expf(-r[0]);
                     p1 = 1.f - expf(-r[1]);
                     if (own_pops) {
-                        float *mo = smo + (size_t)par * 5 * NT + tid;
+                        float *mo = smo + par * 5 * NT + tid;
                         const float den = r[0] * L.itau[0] + r[1] * L.itau[1];
+                        const float iden = den > 0.f ? 1.f / den : 0.f;
                         mo[0] = r[0];
                         mo[NT] = r[1];
 #pragma unroll
-                        for (int k = 0; k < 3; k++)
-                            mo[(2 + k) * NT] = den > 0.f ? (j[0][k] * L.itau[0] + j[1][k] * L.itau[1]) / den : 0.f;
+                        for (int k = 0; k < 3; k++) mo[(2 + k) * NT] = (j[0][k] * L.itau[0] + j[1][k] * L.itau[1]) * iden;
                     }
                 } else {
                     p0 = psi[n];
                     p1 = psi[(size_t)L.N + n];
                 }
             }
-            sps[(slot * 2 + 0) * HN + e] = p0;
-            sps[(slot * 2 + 1) * HN + e] = p1;
-            sty[slot * HN + e] = t;
+            ps[ec] = p0;
+            ps[HN + ec] = p1;
+            ts[ec] = t;
         }
-        // halo ring: top row, bottom row, left column, right column
         if (tid < NHALO) {
-            int hx, hy;
-            if (tid < HX) {
-                hx = tid;
-                hy = 0;
-            } else if (tid < 2 * HX) {
-                hx = tid - HX;
-                hy = HY - 1;
-            } else if (tid < 2 * HX + TY) {
-                hx = 0;
-                hy = tid - 2 * HX + 1;
-            } else {
-                hx = HX - 1;
-                hy = tid - 2 * HX - TY + 1;
-            }
-            const int e = hy * HX + hx;
             float p0 = 0.f, p1 = 0.f;
             uint8_t t = WALL;
             if (zin) {
-                const int hxg = wrapc(x0 + hx - 1, L.nx), hyg = wrapc(y0 + hy - 1, L.ny);
-                const int n = hxg + L.nx * (hyg + L.ny * gz);
+                const int n = hn2 + nxy * gz;
                 t = type[n];
                 if (t == FLUID) {
+                    const T *src = fin + n;
                     float r0 = 0.f, r1 = 0.f;
 #pragma unroll
                     for (int i = 0; i < Q; i++) {
-                        r0 += S::ld(cslot<S>(fin, L, 0, i) + n, L.base[0][i]);
-                        r1 += S::ld(cslot<S>(fin, L, 1, i) + n, L.base[1][i]);
+                        r0 += S::cvt(__ldg(src + ofs.pop[i]), L.base[0][i]);
+                        r1 += S::cvt(__ldg(src + ofs.pop[Q + i]), L.base[1][i]);
                     }
                     p0 = 1.f - expf(-r0);
                     p1 = 1.f - expf(-r1);
@@ -163,83 +225,145 @@ __global__ void __launch_bounds__(NT) k_fused(Lat L, const typename S::T *__rest
                     p1 = psi[(size_t)L.N + n];
                 }
             }
-            sps[(slot * 2 + 0) * HN + e] = p0;
-            sps[(slot * 2 + 1) * HN + e] = p1;
-            sty[slot * HN + e] = t;
+            ps[he] = p0;
+            ps[HN + he] = p1;
+            ts[he] = t;
         }
     };
 
     load_plane(zb - 1, false);
     load_plane(zb, true);
-    const int xs[3] = {gx == 0 ? L.nx - 1 : gx - 1, gx, gx == L.nx - 1 ? 0 : gx + 1};
-    const int ys[3] = {gy == 0 ? L.ny - 1 : gy - 1, gy, gy == L.ny - 1 ? 0 : gy + 1};
-    const int ec = (ty + 1) * HX + (tx + 1);
+    const bool xy_inner = gx >= 1 && gx <= L.nx - 2 && gy >= 1 && gy <= L.ny - 2;
     for (int z = zb; z < ze; z++) {
         load_plane(z + 1, z + 1 < ze);
         __syncthreads();
-        const int sc = z % 3;
-        if (active && sty[sc * HN + ec] == FLUID) {
-            const int n = gx + L.nx * (gy + L.ny * z);
-            int zs[3];
-            if (L.walls) {
-                zs[0] = z - 1;
-                zs[2] = z + 1;
-            } else {
-                zs[0] = z == 0 ? L.nz - 1 : z - 1;
-                zs[2] = z == L.nz - 1 ? 0 : z + 1;
-            }
-            zs[1] = z;
+        // ring slots of planes z-1, z, z+1
+        const float *pl[3] = {sps + ((z + 2) % 3) * 2 * HN, sps + (z % 3) * 2 * HN, sps + ((z + 1) % 3) * 2 * HN};
+        const uint8_t *tl[3] = {sty + ((z + 2) % 3) * HN, sty + (z % 3) * HN, sty + ((z + 1) % 3) * HN};
+        if (active && tl[1][ec] == FLUID) {
+            const int n = own2 + nxy * z;
+            const bool inner = xy_inner && z >= 1 && z <= L.nz - 2;
             const int par = z & 1;
-            const float *mo = smo + (size_t)par * 5 * NT + tid;
+            const float *mo = smo + par * 5 * NT + tid;
             const float rho[2] = {mo[0], mo[NT]};
             const float up[3] = {mo[2 * NT], mo[3 * NT], mo[4 * NT]};
-            const T *fb = fbuf + (size_t)par * 2 * Q * NT + tid;
+            const T *fb = fbuf + par * 2 * Q * NT + tid;
             float s[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-            uint32_t solid = 0;  // bit i: neighbour i is not fluid
+            uint32_t solid = 0, part = 0;  // bit i: neighbour i is not fluid / is a particle node
 #pragma unroll
             for (int i = 1; i < Q; i++) {
-                const int sl = (z + cz(i) + 3) % 3;
-                const int e = (ty + 1 + cy(i)) * HX + (tx + 1 + cx(i));
-                const float p0 = sps[(sl * 2 + 0) * HN + e], p1 = sps[(sl * 2 + 1) * HN + e];
-                if (sty[sl * HN + e] != FLUID) solid |= 1u << i;
+                const int e = ec + cy(i) * HX + cx(i);
+                const float *pp = pl[cz(i) + 1];
+                const float p0 = pp[e], p1 = pp[HN + e];
+                const uint8_t tn = tl[cz(i) + 1][e];
+                solid |= (uint32_t)(tn != FLUID) << i;
+                part |= (uint32_t)(tn == PART) << i;
                 if (cx(i)) { s[0][0] += cx(i) * p1; s[1][0] += cx(i) * p0; }
                 if (cy(i)) { s[0][1] += cy(i) * p1; s[1][1] += cy(i) * p0; }
                 if (cz(i)) { s[0][2] += cz(i) * p1; s[1][2] += cz(i) * p0; }
             }
-            const float pc[2] = {sps[(sc * 2 + 0) * HN + ec], sps[(sc * 2 + 1) * HN + ec]};
+            const float pc[2] = {pl[1][ec], pl[1][HN + ec]};
+            T *dst = fout + n;
+            // wrapped neighbour index, only for nodes on the lattice boundary
+            auto nbr = [&](int i) {
+                int x = gx + cx(i), y = gy + cy(i), zz = z + cz(i);
+                x = x < 0 ? x + L.nx : (x >= L.nx ? x - L.nx : x);
+                y = y < 0 ? y + L.ny : (y >= L.ny ? y - L.ny : y);
+                zz = zz < 0 ? zz + L.nz : (zz >= L.nz ? zz - L.nz : zz);
+                return x + L.nx * (y + L.ny * zz);
+            };
+            // the link to a particle node through direction i (see below)
+            auto link = [&](int i, int c, float fs, float r) {
+                const int m = inner ? n + (int)(ofs.push[i] - ofs.pop[i]) : nbr(i);
+                const int p = (int)lk.owner[m];
+                const float4 X = lk.X32[p], V = lk.K32[2 * p], W = lk.K32[2 * p + 1];
+                float rb[3] = {(float)gx - X.x, (float)gy - X.y, (float)z - X.z};
+                const float nl[3] = {(float)L.nx, (float)L.ny, (float)L.nz};
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    if (k < 2 || !L.walls) rb[k] -= nl[k] * rintf(rb[k] / nl[k]);
+                rb[0] += 0.5f * cx(i);
+                rb[1] += 0.5f * cy(i);
+                rb[2] += 0.5f * cz(i);
+                const float us[3] = {V.x + W.y * rb[2] - W.z * rb[1], V.y + W.z * rb[0] - W.x * rb[2],
+                                     V.z + W.x * rb[1] - W.y * rb[0]};
+                const float uci = us[0] * cx(i) + us[1] * cy(i) + us[2] * cz(i);
+                const float C = -6.f * wgt(i) * r * uci;
+                const float a = 2.f * fs + C;
+                const float F[3] = {a * cx(i), a * cy(i), a * cz(i)};
+                const float Tq[3] = {rb[1] * F[2] - rb[2] * F[1], rb[2] * F[0] - rb[0] * F[2],
+                                     rb[0] * F[1] - rb[1] * F[0]};
+                const int h = tab_slot(tids, p);
+                if (h >= 0) {
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        atomicAdd(&tacc[k * TAB + h], F[k]);
+                        atomicAdd(&tacc[(3 + k) * TAB + h], Tq[k]);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        atomicAdd(&lk.Flink[3 * p + k], (double)F[k]);
+                        atomicAdd(&lk.Tlink[3 * p + k], (double)Tq[k]);
+                    }
+                }
+                return fs + C;
+            };
+            // store of the post-collision population fs of direction i:
+            // streamed to the neighbour, or reflected into slot opp(i) of
+            // this node; a reflection off a particle node takes the moving
+            // bounce-back term C = 6 w_i ρ^c u_surf.(-c_i) (Eq. 4) and gives
+            // the particle (2 f* + C) c_i and r_b x that (Eq. 5), with
+            // u_surf = V + ω x r_b at the link midpoint r_b = x + c_i/2 - X.
+            auto put = [&](int c, int i, float fs, float r) {
+                const int ci = c * Q + i;
+                if (!(solid & (1u << i))) {
+                    T *q = inner ? dst + ofs.push[ci] : fout + ofs.pop[ci] + nbr(i);
+                    S::st(q, fs, L.base[c][i]);
+                } else {
+                    const float v = (part & (1u << i)) ? link(i, c, fs, r) : fs;
+                    S::st(dst + ofs.pop[c * Q + opp(i)], v, L.base[c][opp(i)]);
+                }
+            };
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 const float r = rho[c];
                 float ue[3];
+                const float ir = r > 0.f ? L.tau[c] / r : 0.f;
 #pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    const float F = -L.g * pc[c] * s[c][k] + r * L.body[k];
-                    ue[k] = r > 0.f ? up[k] + L.tau[c] * F / r : up[k];
-                }
-                const float uu = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
+                for (int k = 0; k < 3; k++) ue[k] = up[k] + ir * (-L.g * pc[c] * s[c][k] + r * L.body[k]);
+                const float uu15 = 1.f - 1.5f * (ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2]);
                 const float it = L.itau[c];
                 float seq = 0.f;
+                // opposite pairs share the even part of the equilibrium
 #pragma unroll
-                for (int i = 1; i < Q; i++) {
-                    const float fi = S::cvt(fb[(c * Q + i) * NT], L.base[c][i]);
+                for (int i = 1; i < Q; i += 2) {
                     const float cu = cx(i) * ue[0] + cy(i) * ue[1] + cz(i) * ue[2];
-                    const float feq = wgt(i) * r * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
-                    seq += feq;
-                    const float fs = fi - (fi - feq) * it;
-                    if (!(solid & (1u << i))) {
-                        const int m = xs[cx(i) + 1] + L.nx * (ys[cy(i) + 1] + L.ny * zs[cz(i) + 1]);
-                        S::st(wslot<S>(fout, L, c, i) + m, fs, L.base[c][i]);
-                    } else {
-                        S::st(wslot<S>(fout, L, c, opp(i)) + n, fs, L.base[c][opp(i)]);
-                    }
+                    const float wr = wgt(i) * r;
+                    const float even = wr * (uu15 + 4.5f * cu * cu);
+                    const float odd = 3.f * wr * cu;
+                    const float fa = S::cvt(fb[(c * Q + i) * NT], L.base[c][i]);
+                    const float fbv = S::cvt(fb[(c * Q + i + 1) * NT], L.base[c][i + 1]);
+                    seq += 2.f * even;
+                    put(c, i, fa - (fa - (even + odd)) * it, r);
+                    put(c, i + 1, fbv - (fbv - (even - odd)) * it, r);
                 }
                 // rest population: equilibrium ρ - Σ_{i>0} f^eq_i (exact mass)
                 const float f0 = S::cvt(fb[(c * Q) * NT], L.base[c][0]);
-                const float fs0 = f0 - (f0 - (r - seq)) * it;
-                S::st(wslot<S>(fout, L, c, 0) + n, fs0, L.base[c][0]);
+                S::st(dst + ofs.pop[c * Q], f0 - (f0 - (r - seq)) * it, L.base[c][0]);
             }
         }
         __syncthreads();
+    }
+    // flush the per-particle link sums of this CTA
+    for (int e = threadIdx.x; e < TAB; e += NT) {
+        const int p = tids[e];
+        if (p < 0) continue;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            atomicAdd(&lk.Flink[3 * p + k], (double)tacc[k * TAB + e]);
+            atomicAdd(&lk.Tlink[3 * p + k], (double)tacc[(3 + k) * TAB + e]);
+        }
     }
 }
 
@@ -266,7 +390,7 @@ int fused_zchunk(const Lat &L)
 
 template <class S>
 static void launch_fused_t(const Lat &L, const void *fin, void *fout, const float *psi, const uint8_t *type,
-                           cudaStream_t s)
+                           const Links &lk, cudaStream_t s)
 {
     static bool configured = false;  // the attribute is per function, set once per process
     if (!configured) {
@@ -275,13 +399,21 @@ static void launch_fused_t(const Lat &L, const void *fin, void *fout, const floa
     }
     const int zc = fused_zchunk(L);
     dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
-    k_fused<S><<<grid, NT, Smem<S>::bytes, s>>>(L, (const typename S::T *)fin, (typename S::T *)fout, psi, type, zc);
+    FusedOfs ofs;
+    for (int c = 0; c < 2; c++)
+        for (int i = 0; i < Q; i++) {
+            long long o = (long long)(c * Q + i) * L.S;
+            ofs.pop[c * Q + i] = o;
+            ofs.push[c * Q + i] = o + cx(i) + (long long)cy(i) * L.nx + (long long)cz(i) * L.nx * L.ny;
+        }
+    k_fused<S><<<grid, NT, Smem<S>::bytes, s>>>(L, (const typename S::T *)fin, (typename S::T *)fout, psi, type,
+                                                 zc, lk, ofs);
 }
 
 void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
-                  const uint8_t *type, cudaStream_t s)
+                  const uint8_t *type, const Links &lk, cudaStream_t s)
 {
-    LBE_DISPATCH(storage, (launch_fused_t<S>(L, fin, fout, psi, type, s)));
+    LBE_DISPATCH(storage, (launch_fused_t<S>(L, fin, fout, psi, type, lk, s)));
 }
 
 }  // namespace lbe

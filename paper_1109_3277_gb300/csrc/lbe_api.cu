@@ -106,6 +106,7 @@ void bind_parts(lbe_ctx *c)
     P.F = at(OF);
     P.T = at(OT);
     P.X32 = c->x32;
+    P.K32 = c->x32 ? c->x32 + c->cap : nullptr;
 }
 
 void free_all(lbe_ctx *c)
@@ -167,17 +168,19 @@ void enqueue_step(lbe_ctx *c)
         }
         cudaEventRecord(c->ev[c->ev_used], s);
     }
-    if (two_pass)
+    if (two_pass) {
         launch_collide_stream(st, L, fin, fout, c->psi, c->type, s);
-    else
-        launch_fused(st, L, fin, fout, c->psi, c->type, s);
+    } else {
+        Links lk{c->owner[c->ocur], c->P.X32, c->P.K32, c->P.Flink, c->P.Tlink};
+        launch_fused(st, L, fin, fout, c->psi, c->type, lk, s);
+    }
     if (c->profiling) {
         cudaEventRecord(c->ev[c->ev_used + 1], s);
         c->ev_used += 2;
     }
     if (c->np > 0) {
         c->P.n = c->np;
-        launch_links(st, L, c->P, fout, c->rho, c->type, c->owner[c->ocur], s);
+        if (two_pass) launch_links(st, L, c->P, fout, c->rho, c->type, c->owner[c->ocur], s);
         launch_pairs(L, c->P, c->pair, s);
         launch_integrate(L, c->P, c->d.particle_mode, s);
         if (c->d.particle_mode != LBE_PARTICLES_STATIC) {
@@ -377,10 +380,16 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
         for (int j = 0; j < 3; j++) blk[OXO * cp + 3 * p + j] = blk[OX * cp + 3 * p + j];
         for (int j = 0; j < 4; j++) blk[OQO * cp + 4 * p + j] = blk[OQ * cp + 4 * p + j];
     }
-    std::vector<float4> x32((size_t)ncap, make_float4(0.f, 0.f, 0.f, 0.f));
-    for (int p = 0; p < np; p++)
+    // FP32 copies: [0, ncap) position and reach, then velocity and ω pairs
+    std::vector<float4> x32((size_t)3 * ncap, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int p = 0; p < np; p++) {
         x32[p] = make_float4((float)blk[OX * cp + 3 * p], (float)blk[OX * cp + 3 * p + 1],
                              (float)blk[OX * cp + 3 * p + 2], (float)std::fmax(blk[ORP * cp + p], blk[ORO * cp + p]));
+        x32[ncap + 2 * p] = make_float4((float)blk[OV * cp + 3 * p], (float)blk[OV * cp + 3 * p + 1],
+                                        (float)blk[OV * cp + 3 * p + 2], 0.f);
+        x32[ncap + 2 * p + 1] = make_float4((float)blk[OW * cp + 3 * p], (float)blk[OW * cp + 3 * p + 1],
+                                            (float)blk[OW * cp + 3 * p + 2], 0.f);
+    }
     if (ncap != cap) {
         double *nb = nullptr;
         float4 *nx32 = nullptr;
@@ -393,12 +402,12 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
         if (c->pbuf) {
             cudaFree(c->pbuf);
             cudaFree(c->x32);
-            c->bytes -= (size_t)cap * (PSTRIDE * sizeof(double) + sizeof(float4));
+            c->bytes -= (size_t)cap * (PSTRIDE * sizeof(double) + 3 * sizeof(float4));
         }
         c->pbuf = nb;
         c->x32 = nx32;
         c->cap = ncap;
-        c->bytes += (size_t)ncap * (PSTRIDE * sizeof(double) + sizeof(float4));
+        c->bytes += (size_t)ncap * (PSTRIDE * sizeof(double) + 3 * sizeof(float4));
     }
     CK(c, cudaMemcpy(c->pbuf, blk.data(), blk.size() * sizeof(double), cudaMemcpyHostToDevice));
     CK(c, cudaMemcpy(c->x32, x32.data(), x32.size() * sizeof(float4), cudaMemcpyHostToDevice));
@@ -562,9 +571,10 @@ lbe_status lbe_profile_read(lbe_ctx *c, double *ms_total, int64_t *launches)
 int32_t lbe_kernels_per_step(const lbe_ctx *c)
 {
     if (!c) return 0;
-    int k = 3;  // moments, shell, collide+stream
+    const bool two_pass = (c->d.flags & LBE_FLAG_TWO_PASS) != 0;
+    int k = 3;  // densities (boundary or all), shell fill, fused fluid (or collide+stream)
     if (c->np > 0) {
-        k += 3;  // links, pairs, integrate
+        k += two_pass ? 3 : 2;  // (links), pairs, integrate
         if (c->d.particle_mode != LBE_PARTICLES_STATIC) k += 3;  // claim, transition, reset
     }
     return k;

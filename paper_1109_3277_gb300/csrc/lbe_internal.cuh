@@ -104,6 +104,15 @@ struct Parts {
     double *Fpend, *Tpend;          // fill/empty momentum for the next update
     double *F, *T;                  // total of the last update
     float4 *X32;                    // FP32 (x, y, z, max radius) for the pair prefilter
+    float4 *K32;                    // FP32 velocity [2p] and ω [2p+1] for the fused links
+};
+
+// What the fused fluid kernel needs for the moving bounce-back (Eq. 4) and
+// the momentum exchange (Eq. 5) of the links it streams.
+struct Links {
+    const uint32_t *owner;          // current ownership map
+    const float4 *X32, *K32;        // particle position / velocity / ω (FP32)
+    double *Flink, *Tlink;          // per-particle sums, accumulated with atomics
 };
 
 struct Pair {
@@ -132,7 +141,7 @@ int mass_blocks();
 
 // ---- launchers (fused.cu) -------------------------------------------------
 void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
-                  const uint8_t *type, cudaStream_t s);
+                  const uint8_t *type, const Links &lk, cudaStream_t s);
 int fused_zchunk(const Lat &L);
 
 // ---- launchers (particles.cu) ---------------------------------------------

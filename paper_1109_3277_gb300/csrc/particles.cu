@@ -497,6 +497,8 @@ __global__ void k_integrate(Lat L, Parts P, int mode)
         P.T[3 * p + k] = T[k];
         P.Fpend[3 * p + k] = 0.0;
         P.Tpend[3 * p + k] = 0.0;
+        P.Flink[3 * p + k] = 0.0;  // the fused kernel accumulates into these
+        P.Tlink[3 * p + k] = 0.0;
         P.Xold[3 * p + k] = P.X[3 * p + k];
     }
     double q[4];
@@ -548,6 +550,8 @@ __global__ void k_integrate(Lat L, Parts P, int mode)
     x32.y = (float)X[1];
     x32.z = (float)X[2];
     P.X32[p] = x32;
+    P.K32[2 * p] = make_float4((float)V[0], (float)V[1], (float)V[2], 0.f);
+    P.K32[2 * p + 1] = make_float4((float)W[0], (float)W[1], (float)W[2], 0.f);
 }
 
 // ---------------------------------------------------------------- claim
