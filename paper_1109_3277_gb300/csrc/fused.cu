@@ -15,9 +15,9 @@
 //
 // Links into particle nodes get the moving bounce-back term C (Eq. 4) in
 // registers as they are reflected, and their momentum exchange (Eq. 5) and
-// torque go to a per-CTA table of per-particle sums in shared memory (FP32
+// torque go to a per-CTA table of per-particle sums in shared memory (FP64
 // atomics), flushed to the FP64 per-particle totals with atomics at the end:
-// the sums are exact to FP32 rounding but their order is not fixed.
+// each link term is FP32, the sums are FP64, and their order is not fixed.
 #include "lbe_internal.cuh"
 
 namespace lbe {
@@ -52,8 +52,8 @@ struct Smem {
     static constexpr size_t fbuf = 0;                                          // T [2][2Q][NT]
     static constexpr size_t sps = fbuf + 2 * 2 * Q * NT * sizeof(typename S::T);  // float [3][2][HN]
     static constexpr size_t smo = sps + 3 * 2 * HN * sizeof(float);             // float [2][5][NT]
-    static constexpr size_t tacc = smo + 2 * 5 * NT * sizeof(float);           // float [6][TAB]
-    static constexpr size_t tid_ = tacc + 6 * TAB * sizeof(float);              // int [TAB]
+    static constexpr size_t tacc = smo + 2 * 5 * NT * sizeof(float);           // double [6][TAB]
+    static constexpr size_t tid_ = tacc + 6 * TAB * sizeof(double);             // int [TAB]
     static constexpr size_t sty = tid_ + TAB * sizeof(int);                     // uint8 [3][HN]
     static constexpr size_t bytes = sty + 3 * HN;
 };
@@ -84,7 +84,7 @@ struct FusedOfs {
 };
 
 template <class S>
-__global__ void __launch_bounds__(NT) k_fused(Lat L, const typename S::T *__restrict__ fin,
+__global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__restrict__ fin,
                                               typename S::T *__restrict__ fout,
                                               const float *__restrict__ psi,
                                               const uint8_t *__restrict__ type, int zc, Links lk,
@@ -96,12 +96,12 @@ __global__ void __launch_bounds__(NT) k_fused(Lat L, const typename S::T *__rest
     float *sps = reinterpret_cast<float *>(smem + Smem<S>::sps);    // [slot][c][e]
     float *smo = reinterpret_cast<float *>(smem + Smem<S>::smo);    // [parity][k][tid]
     uint8_t *sty = smem + Smem<S>::sty;                             // [slot][e]
-    float *tacc = reinterpret_cast<float *>(smem + Smem<S>::tacc);  // [k][TAB]
+    double *tacc = reinterpret_cast<double *>(smem + Smem<S>::tacc);  // [k][TAB]
     int *tids = reinterpret_cast<int *>(smem + Smem<S>::tid_);      // [TAB]
     for (int e = threadIdx.x; e < TAB; e += NT) {
         tids[e] = -1;
 #pragma unroll
-        for (int k = 0; k < 6; k++) tacc[k * TAB + e] = 0.f;
+        for (int k = 0; k < 6; k++) tacc[k * TAB + e] = 0.0;
     }
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -297,8 +297,8 @@ __global__ void __launch_bounds__(NT) k_fused(Lat L, const typename S::T *__rest
                 if (h >= 0) {
 #pragma unroll
                     for (int k = 0; k < 3; k++) {
-                        atomicAdd(&tacc[k * TAB + h], F[k]);
-                        atomicAdd(&tacc[(3 + k) * TAB + h], Tq[k]);
+                        atomicAdd(&tacc[k * TAB + h], (double)F[k]);
+                        atomicAdd(&tacc[(3 + k) * TAB + h], (double)Tq[k]);
                     }
                 } else {
 #pragma unroll
@@ -361,8 +361,8 @@ __global__ void __launch_bounds__(NT) k_fused(Lat L, const typename S::T *__rest
         if (p < 0) continue;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            atomicAdd(&lk.Flink[3 * p + k], (double)tacc[k * TAB + e]);
-            atomicAdd(&lk.Tlink[3 * p + k], (double)tacc[(3 + k) * TAB + e]);
+            atomicAdd(&lk.Flink[3 * p + k], tacc[k * TAB + e]);
+            atomicAdd(&lk.Tlink[3 * p + k], tacc[(3 + k) * TAB + e]);
         }
     }
 }
