@@ -14,10 +14,11 @@
 // own CTAs are streaming through L2 at the same time.
 //
 // Links into particle nodes get the moving bounce-back term C (Eq. 4) in
-// registers as they are reflected, and their momentum exchange (Eq. 5) and
-// torque go to a per-CTA table of per-particle sums in shared memory (FP64
-// atomics), flushed to the FP64 per-particle totals with atomics at the end:
-// each link term is FP32, the sums are FP64, and their order is not fixed.
+// registers as they are reflected.  Their momentum exchange (Eq. 5) and
+// torque are summed per particle in 64-bit fixed point (2^-40 units): each
+// FP32 link term is rounded once to an integer, and integer atomics in a
+// per-CTA shared-memory table, then in the per-particle totals, add them
+// exactly, so the sums do not depend on the order the links are met in.
 #include "lbe_internal.cuh"
 
 namespace lbe {
@@ -52,11 +53,20 @@ struct Smem {
     static constexpr size_t fbuf = 0;                                          // T [2][2Q][NT]
     static constexpr size_t sps = fbuf + 2 * 2 * Q * NT * sizeof(typename S::T);  // float [3][2][HN]
     static constexpr size_t smo = sps + 3 * 2 * HN * sizeof(float);             // float [2][5][NT]
-    static constexpr size_t tacc = smo + 2 * 5 * NT * sizeof(float);           // double [6][TAB]
-    static constexpr size_t tid_ = tacc + 6 * TAB * sizeof(double);             // int [TAB]
+    static constexpr size_t tacc = smo + 2 * 5 * NT * sizeof(float);           // int64 [6][TAB]
+    static constexpr size_t tid_ = tacc + 6 * TAB * sizeof(long long);          // int [TAB]
     static constexpr size_t sty = tid_ + TAB * sizeof(int);                     // uint8 [3][HN]
     static constexpr size_t bytes = sty + 3 * HN;
 };
+
+// FP32 value to 64-bit fixed point in units of 2^-40 (two's complement in an
+// unsigned word, so that wrap-around addition is exact); |v| is clamped to
+// 2^22, far beyond any link term.
+__device__ __forceinline__ unsigned long long to_fixed(float v)
+{
+    v = fminf(fmaxf(v, -4194304.f), 4194304.f);
+    return (unsigned long long)__float2ll_rn(v * 1099511627776.f);
+}
 
 // Slot of particle p in the CTA's table (linear probing, at most TAB
 // probes); -1 when the table is full.
@@ -96,12 +106,12 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
     float *sps = reinterpret_cast<float *>(smem + Smem<S>::sps);    // [slot][c][e]
     float *smo = reinterpret_cast<float *>(smem + Smem<S>::smo);    // [parity][k][tid]
     uint8_t *sty = smem + Smem<S>::sty;                             // [slot][e]
-    double *tacc = reinterpret_cast<double *>(smem + Smem<S>::tacc);  // [k][TAB]
+    unsigned long long *tacc = reinterpret_cast<unsigned long long *>(smem + Smem<S>::tacc);  // [k][TAB]
     int *tids = reinterpret_cast<int *>(smem + Smem<S>::tid_);      // [TAB]
     for (int e = threadIdx.x; e < TAB; e += NT) {
         tids[e] = -1;
 #pragma unroll
-        for (int k = 0; k < 6; k++) tacc[k * TAB + e] = 0.0;
+        for (int k = 0; k < 6; k++) tacc[k * TAB + e] = 0ull;
     }
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -294,18 +304,13 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
                 const float Tq[3] = {rb[1] * F[2] - rb[2] * F[1], rb[2] * F[0] - rb[0] * F[2],
                                      rb[0] * F[1] - rb[1] * F[0]};
                 const int h = tab_slot(tids, p);
-                if (h >= 0) {
 #pragma unroll
-                    for (int k = 0; k < 3; k++) {
-                        atomicAdd(&tacc[k * TAB + h], (double)F[k]);
-                        atomicAdd(&tacc[(3 + k) * TAB + h], (double)Tq[k]);
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 3; k++) {
-                        atomicAdd(&lk.Flink[3 * p + k], (double)F[k]);
-                        atomicAdd(&lk.Tlink[3 * p + k], (double)Tq[k]);
-                    }
+                for (int k = 0; k < 6; k++) {
+                    const unsigned long long q = to_fixed(k < 3 ? F[k] : Tq[k - 3]);
+                    if (h >= 0)
+                        atomicAdd(&tacc[k * TAB + h], q);
+                    else
+                        atomicAdd(&lk.fix[6 * p + k], q);
                 }
                 return fs + C;
             };
@@ -361,8 +366,8 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
         if (p < 0) continue;
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            atomicAdd(&lk.Flink[3 * p + k], tacc[k * TAB + e]);
-            atomicAdd(&lk.Tlink[3 * p + k], tacc[(3 + k) * TAB + e]);
+            atomicAdd(&lk.fix[6 * p + k], tacc[k * TAB + e]);
+            atomicAdd(&lk.fix[6 * p + 3 + k], tacc[(3 + k) * TAB + e]);
         }
     }
 }

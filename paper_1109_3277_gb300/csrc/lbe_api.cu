@@ -75,7 +75,7 @@ void drop_graphs(lbe_ctx *c)
 // Field offsets inside the particle buffer (doubles per particle).
 enum { OX = 0, OQ = 3, OV = 7, OW = 10, OXO = 13, OQO = 16, ORP = 20, ORO = 21, ODR = 22, OM = 23,
        OIP = 24, OIQ = 25, OFL = 26, OTL = 29, OFP = 32, OTP = 35, OFE = 38, OTE = 41, OF = 44,
-       OT = 47, PSTRIDE = 50 };
+       OT = 47, OFX = 50, PSTRIDE = 56 };
 
 void bind_parts(lbe_ctx *c)
 {
@@ -105,6 +105,7 @@ void bind_parts(lbe_ctx *c)
     P.Tpend = at(OTE);
     P.F = at(OF);
     P.T = at(OT);
+    P.fix = reinterpret_cast<unsigned long long *>(at(OFX));
     P.X32 = c->x32;
     P.K32 = c->x32 ? c->x32 + c->cap : nullptr;
 }
@@ -171,7 +172,7 @@ void enqueue_step(lbe_ctx *c)
     if (two_pass) {
         launch_collide_stream(st, L, fin, fout, c->psi, c->type, s);
     } else {
-        Links lk{c->owner[c->ocur], c->P.X32, c->P.K32, c->P.Flink, c->P.Tlink};
+        Links lk{c->owner[c->ocur], c->P.X32, c->P.K32, c->P.fix};
         launch_fused(st, L, fin, fout, c->psi, c->type, lk, s);
     }
     if (c->profiling) {
@@ -339,7 +340,8 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
     if (st != LBE_OK) return st;
     static const int FIELDS[][2] = {{OX, 3},  {OQ, 4},  {OV, 3},  {OW, 3},  {OXO, 3}, {OQO, 4}, {ORP, 1},
                                     {ORO, 1}, {ODR, 1}, {OM, 1},  {OIP, 1}, {OIQ, 1}, {OFL, 3}, {OTL, 3},
-                                    {OFP, 3}, {OTP, 3}, {OFE, 3}, {OTE, 3}, {OF, 3},  {OT, 3}};
+                                    {OFP, 3}, {OTP, 3}, {OFE, 3}, {OTE, 3}, {OF, 3},  {OT, 3},
+                                    {OFX, 6}};
     // Each field of width k occupies k*cap doubles starting at off*cap; the
     // live state of existing particles is read back and re-laid for the new
     // capacity.

@@ -103,6 +103,7 @@ struct Parts {
     double *Fpair, *Tpair;          // pair forces of the current step
     double *Fpend, *Tpend;          // fill/empty momentum for the next update
     double *F, *T;                  // total of the last update
+    unsigned long long *fix;        // [6n] link force and torque in 2^-40 fixed point
     float4 *X32;                    // FP32 (x, y, z, max radius) for the pair prefilter
     float4 *K32;                    // FP32 velocity [2p] and ω [2p+1] for the fused links
 };
@@ -112,8 +113,10 @@ struct Parts {
 struct Links {
     const uint32_t *owner;          // current ownership map
     const float4 *X32, *K32;        // particle position / velocity / ω (FP32)
-    double *Flink, *Tlink;          // per-particle sums, accumulated with atomics
+    unsigned long long *fix;        // per-particle force, torque sums (2^-40 fixed point)
 };
+
+constexpr double FIXED_UNIT = 1.0 / 1099511627776.0;  // 2^-40
 
 struct Pair {
     double k_hertz, lub_cut, mu;

@@ -491,13 +491,19 @@ __global__ void k_integrate(Lat L, Parts P, int mode)
     if (p >= P.n) return;
     double F[3], T[3];
     for (int k = 0; k < 3; k++) {
-        F[k] = P.Flink[3 * p + k] + P.Fpair[3 * p + k] + P.Fpend[3 * p + k];
-        T[k] = P.Tlink[3 * p + k] + P.Tpair[3 * p + k] + P.Tpend[3 * p + k];
+        // link sums: FP64 from the two-pass link kernel, or 2^-40 fixed point
+        // from the fused kernel (the other one is zero)
+        const double fl = P.Flink[3 * p + k] + (double)(long long)P.fix[6 * p + k] * FIXED_UNIT;
+        const double tl = P.Tlink[3 * p + k] + (double)(long long)P.fix[6 * p + 3 + k] * FIXED_UNIT;
+        P.fix[6 * p + k] = 0ull;
+        P.fix[6 * p + 3 + k] = 0ull;
+        F[k] = fl + P.Fpair[3 * p + k] + P.Fpend[3 * p + k];
+        T[k] = tl + P.Tpair[3 * p + k] + P.Tpend[3 * p + k];
         P.F[3 * p + k] = F[k];
         P.T[3 * p + k] = T[k];
         P.Fpend[3 * p + k] = 0.0;
         P.Tpend[3 * p + k] = 0.0;
-        P.Flink[3 * p + k] = 0.0;  // the fused kernel accumulates into these
+        P.Flink[3 * p + k] = 0.0;
         P.Tlink[3 * p + k] = 0.0;
         P.Xold[3 * p + k] = P.X[3 * p + k];
     }
