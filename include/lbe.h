@@ -70,7 +70,8 @@ typedef enum {
 } lbe_particle_mode;
 
 typedef struct {
-    int32_t nx, ny, nz;      /* lattice extent, each >= 1 (nz >= 3 with walls) */
+    int32_t nx, ny, nz;      /* lattice extent, each >= 1, ny and nz <= 65535, nx*ny*nz < 2^31
+                                (nz >= 3 with walls) */
     int32_t walls_z;         /* 0: periodic in z; 1: one-node walls at z=0 and z=nz-1
                                 (the impenetrable walls of the §4 adsorption box) */
     double  tau[2];          /* BGK relaxation time per component, > 1/2 (Eq. 2) */

@@ -106,21 +106,47 @@ __global__ void __launch_bounds__(256) k_moments(Lat L, const typename S::T *__r
 
 // ------------------------------------------------------ boundary densities
 // ρ^c on the fluid nodes that have a solid neighbour: the only densities the
-// shell fill and the moving bounce-back read (the fused kernel computes the
-// others itself).
+// shell fill reads (the fused kernel computes the others itself).  Both this
+// kernel and the shell fill run on a 3D grid (x per thread, one y row and z
+// plane per block row), so no index division is needed, and interior nodes
+// reach their neighbours by a fixed offset.
+
+__device__ __forceinline__ int nb_off(const Lat &L, int i) { return cx(i) + L.nx * (cy(i) + L.ny * cz(i)); }
+
+struct Site {
+    int x, y, z, n;
+    bool inner;
+};
+
+__device__ __forceinline__ bool site_of(const Lat &L, Site &s)
+{
+    s.x = blockIdx.x * blockDim.x + threadIdx.x;
+    s.y = blockIdx.y;
+    s.z = blockIdx.z;
+    if (s.x >= L.nx) return false;
+    s.n = s.x + L.nx * (s.y + L.ny * s.z);
+    s.inner = s.x >= 1 && s.x <= L.nx - 2 && s.y >= 1 && s.y <= L.ny - 2 && s.z >= 1 && s.z <= L.nz - 2;
+    return true;
+}
+
+__device__ __forceinline__ int site_nb(const Lat &L, const Site &s, int i)
+{
+    if (s.inner) return s.n + nb_off(L, i);
+    Coord c{s.x, s.y, s.z};
+    Nbr b = nbr_of(L, c);
+    return nidx(L, b, i);
+}
 
 template <class S>
-__global__ void __launch_bounds__(256) k_bnd_rho(Lat L, const typename S::T *__restrict__ f,
+__global__ void __launch_bounds__(128) k_bnd_rho(Lat L, const typename S::T *__restrict__ f,
                                                  const uint8_t *__restrict__ type, float *__restrict__ rho)
 {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= L.N || type[n] != FLUID) return;
-    Coord c = coord_of(L, n);
-    Nbr b = nbr_of(L, c);
+    Site s;
+    if (!site_of(L, s) || type[s.n] != FLUID) return;
     bool bnd = false;
 #pragma unroll
     for (int i = 1; i < Q; i++) {
-        int m = nidx(L, b, i);
+        int m = site_nb(L, s, i);
         bnd |= m < 0 || type[m] != FLUID;
     }
     if (!bnd) return;
@@ -128,8 +154,8 @@ __global__ void __launch_bounds__(256) k_bnd_rho(Lat L, const typename S::T *__r
     for (int cc = 0; cc < 2; cc++) {
         float r = 0.f;
 #pragma unroll
-        for (int i = 0; i < Q; i++) r += S::ld(slot<S>(f, L, cc, i) + n, L.base[cc][i]);
-        rho[(size_t)cc * L.N + n] = r;
+        for (int i = 0; i < Q; i++) r += S::ld(slot<S>(f, L, cc, i) + s.n, L.base[cc][i]);
+        rho[(size_t)cc * L.N + s.n] = r;
     }
 }
 
@@ -138,23 +164,22 @@ __global__ void __launch_bounds__(256) k_bnd_rho(Lat L, const typename S::T *__r
 // neighbours (Eq. 10); the colour Δρ of the owning particle is added to red
 // if positive, else |Δρ| to blue.  Walls take Δρ = 0.
 
-__global__ void __launch_bounds__(256) k_shell(Lat L, const float *__restrict__ rho,
+__global__ void __launch_bounds__(128) k_shell(Lat L, const float *__restrict__ rho,
                                                float *__restrict__ psi,
                                                const uint8_t *__restrict__ type,
                                                const uint32_t *__restrict__ owner,
                                                const double *__restrict__ drho)
 {
-    int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= L.N) return;
+    Site s;
+    if (!site_of(L, s)) return;
+    const int n = s.n;
     uint8_t t = type[n];
     if (t == FLUID) return;
-    Coord c = coord_of(L, n);
-    Nbr b = nbr_of(L, c);
     float s0 = 0.f, s1 = 0.f;
     int cnt = 0;
 #pragma unroll
     for (int i = 1; i < Q; i++) {
-        int m = nidx(L, b, i);
+        int m = site_nb(L, s, i);
         if (m < 0 || type[m] != FLUID) continue;
         s0 += rho[m];
         s1 += rho[(size_t)L.N + m];
@@ -439,14 +464,15 @@ void launch_moments(int storage, const Lat &L, const void *f, const uint8_t *typ
 void launch_bnd_rho(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho,
                     cudaStream_t s)
 {
-    LBE_DISPATCH(storage, (k_bnd_rho<S><<<blocks_for(L.N, 256), 256, 0, s>>>(
-                              L, (const typename S::T *)f, type, rho)));
+    dim3 grid((L.nx + 127) / 128, L.ny, L.nz);
+    LBE_DISPATCH(storage, (k_bnd_rho<S><<<grid, 128, 0, s>>>(L, (const typename S::T *)f, type, rho)));
 }
 
 void launch_shell(const Lat &L, const float *rho, float *psi, const uint8_t *type,
                   const uint32_t *owner, const double *drho, cudaStream_t s)
 {
-    k_shell<<<blocks_for(L.N, 256), 256, 0, s>>>(L, rho, psi, type, owner, drho);
+    dim3 grid((L.nx + 127) / 128, L.ny, L.nz);
+    k_shell<<<grid, 128, 0, s>>>(L, rho, psi, type, owner, drho);
 }
 
 void launch_collide_stream(int storage, const Lat &L, const void *fin, void *fout, const float *psi,

@@ -47,6 +47,10 @@ __device__ __forceinline__ int wrapc(int v, int n)
 
 constexpr int TAB = 128;  // per-CTA particle table (power of two)
 
+__constant__ int c_x[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+__constant__ int c_y[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+__constant__ int c_z[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+
 // Dynamic shared memory layout (bytes).
 template <class S>
 struct Smem {
@@ -83,6 +87,57 @@ __device__ __forceinline__ int tab_slot(int *ids, int p)
         h = (h + 1) & (TAB - 1);
     }
     return -1;
+}
+
+// Link from fluid node (gx, gy, z) to particle node m = node + c_i (called
+// off the hot path, so that the unrolled collision stays small): the
+// reflected population fs leaving the node along -c_i gains
+// C = 6 w_i ρ^c u_surf.(-c_i), u_surf = V + ω x r_b at the link midpoint
+// r_b = node + c_i/2 - X, and the particle receives (2 fs + C) c_i and
+// r_b x that, added in 2^-40 fixed point.  Returns fs + C.
+__device__ __noinline__ float link_term(const Lat &L, const Links &lk, int i, int m, int gx, int gy, int z,
+                                        float fs, float r, int *tids, unsigned long long *tacc)
+{
+    const float ci[3] = {(float)c_x[i], (float)c_y[i], (float)c_z[i]};
+    const int p = (int)lk.owner[m];
+    const float4 X = lk.X32[p], V = lk.K32[2 * p], W = lk.K32[2 * p + 1];
+    float rb[3] = {(float)gx - X.x, (float)gy - X.y, (float)z - X.z};
+    const float nl[3] = {(float)L.nx, (float)L.ny, (float)L.nz};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (k < 2 || !L.walls) {
+            if (rb[k] > 0.5f * nl[k]) rb[k] -= nl[k];
+            if (rb[k] < -0.5f * nl[k]) rb[k] += nl[k];
+        }
+        rb[k] += 0.5f * ci[k];
+    }
+    const float us[3] = {V.x + W.y * rb[2] - W.z * rb[1], V.y + W.z * rb[0] - W.x * rb[2],
+                         V.z + W.x * rb[1] - W.y * rb[0]};
+    const float uci = us[0] * ci[0] + us[1] * ci[1] + us[2] * ci[2];
+    const float w = i < 7 ? 1.f / 18.f : 1.f / 36.f;
+    const float C = -6.f * w * r * uci;
+    const float a = 2.f * fs + C;
+    const float F[3] = {a * ci[0], a * ci[1], a * ci[2]};
+    const float Tq[3] = {rb[1] * F[2] - rb[2] * F[1], rb[2] * F[0] - rb[0] * F[2], rb[0] * F[1] - rb[1] * F[0]};
+    const int h = tab_slot(tids, p);
+    for (int k = 0; k < 6; k++) {
+        const unsigned long long q = to_fixed(k < 3 ? F[k] : Tq[k - 3]);
+        if (h >= 0)
+            atomicAdd(&tacc[k * TAB + h], q);
+        else
+            atomicAdd(&lk.fix[6 * p + k], q);
+    }
+    return fs + C;
+}
+
+// Wrapped neighbour index of a node on the lattice boundary (off the hot path).
+__device__ __noinline__ int wrapped_nbr(const Lat &L, int gx, int gy, int z, int i)
+{
+    int x = gx + c_x[i], y = gy + c_y[i], zz = z + c_z[i];
+    x = x < 0 ? x + L.nx : (x >= L.nx ? x - L.nx : x);
+    y = y < 0 ? y + L.ny : (y >= L.ny ? y - L.ny : y);
+    zz = zz < 0 ? zz + L.nz : (zz >= L.nz ? zz - L.nz : zz);
+    return x + L.nx * (y + L.ny * zz);
 }
 
 // Offsets of the population arrays, per lattice, passed with the launch:
@@ -274,59 +329,21 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
             }
             const float pc[2] = {pl[1][ec], pl[1][HN + ec]};
             T *dst = fout + n;
-            // wrapped neighbour index, only for nodes on the lattice boundary
-            auto nbr = [&](int i) {
-                int x = gx + cx(i), y = gy + cy(i), zz = z + cz(i);
-                x = x < 0 ? x + L.nx : (x >= L.nx ? x - L.nx : x);
-                y = y < 0 ? y + L.ny : (y >= L.ny ? y - L.ny : y);
-                zz = zz < 0 ? zz + L.nz : (zz >= L.nz ? zz - L.nz : zz);
-                return x + L.nx * (y + L.ny * zz);
-            };
-            // the link to a particle node through direction i (see below)
-            auto link = [&](int i, int c, float fs, float r) {
-                const int m = inner ? n + (int)(ofs.push[i] - ofs.pop[i]) : nbr(i);
-                const int p = (int)lk.owner[m];
-                const float4 X = lk.X32[p], V = lk.K32[2 * p], W = lk.K32[2 * p + 1];
-                float rb[3] = {(float)gx - X.x, (float)gy - X.y, (float)z - X.z};
-                const float nl[3] = {(float)L.nx, (float)L.ny, (float)L.nz};
-#pragma unroll
-                for (int k = 0; k < 3; k++)
-                    if (k < 2 || !L.walls) rb[k] -= nl[k] * rintf(rb[k] / nl[k]);
-                rb[0] += 0.5f * cx(i);
-                rb[1] += 0.5f * cy(i);
-                rb[2] += 0.5f * cz(i);
-                const float us[3] = {V.x + W.y * rb[2] - W.z * rb[1], V.y + W.z * rb[0] - W.x * rb[2],
-                                     V.z + W.x * rb[1] - W.y * rb[0]};
-                const float uci = us[0] * cx(i) + us[1] * cy(i) + us[2] * cz(i);
-                const float C = -6.f * wgt(i) * r * uci;
-                const float a = 2.f * fs + C;
-                const float F[3] = {a * cx(i), a * cy(i), a * cz(i)};
-                const float Tq[3] = {rb[1] * F[2] - rb[2] * F[1], rb[2] * F[0] - rb[0] * F[2],
-                                     rb[0] * F[1] - rb[1] * F[0]};
-                const int h = tab_slot(tids, p);
-#pragma unroll
-                for (int k = 0; k < 6; k++) {
-                    const unsigned long long q = to_fixed(k < 3 ? F[k] : Tq[k - 3]);
-                    if (h >= 0)
-                        atomicAdd(&tacc[k * TAB + h], q);
-                    else
-                        atomicAdd(&lk.fix[6 * p + k], q);
-                }
-                return fs + C;
-            };
             // store of the post-collision population fs of direction i:
             // streamed to the neighbour, or reflected into slot opp(i) of
-            // this node; a reflection off a particle node takes the moving
-            // bounce-back term C = 6 w_i ρ^c u_surf.(-c_i) (Eq. 4) and gives
-            // the particle (2 f* + C) c_i and r_b x that (Eq. 5), with
-            // u_surf = V + ω x r_b at the link midpoint r_b = x + c_i/2 - X.
+            // this node; a reflection off a particle node goes through
+            // link_term (moving bounce-back, Eq. 4, momentum exchange, Eq. 5)
             auto put = [&](int c, int i, float fs, float r) {
                 const int ci = c * Q + i;
                 if (!(solid & (1u << i))) {
-                    T *q = inner ? dst + ofs.push[ci] : fout + ofs.pop[ci] + nbr(i);
+                    T *q = inner ? dst + ofs.push[ci] : fout + ofs.pop[ci] + wrapped_nbr(L, gx, gy, z, i);
                     S::st(q, fs, L.base[c][i]);
                 } else {
-                    const float v = (part & (1u << i)) ? link(i, c, fs, r) : fs;
+                    float v = fs;
+                    if (part & (1u << i)) {
+                        const int m = inner ? n + (int)(ofs.push[i] - ofs.pop[i]) : wrapped_nbr(L, gx, gy, z, i);
+                        v = link_term(L, lk, i, m, gx, gy, z, fs, r, tids, tacc);
+                    }
                     S::st(dst + ofs.pop[c * Q + opp(i)], v, L.base[c][opp(i)]);
                 }
             };

@@ -30,6 +30,7 @@ struct lbe_ctx {
     int np = 0, cap = 0;
     double *pbuf = nullptr;
     float4 *x32 = nullptr;
+    double *ppart = nullptr;
     Parts P{};
     // graphs keyed by (cur, ocur)
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -108,6 +109,8 @@ void bind_parts(lbe_ctx *c)
     P.fix = reinterpret_cast<unsigned long long *>(at(OFX));
     P.X32 = c->x32;
     P.K32 = c->x32 ? c->x32 + c->cap : nullptr;
+    P.ppart = c->ppart;
+    P.nsplit = c->np > 0 ? pair_splits(c->np) : 1;
 }
 
 void free_all(lbe_ctx *c)
@@ -126,6 +129,7 @@ void free_all(lbe_ctx *c)
     cudaFree(c->mass_out);
     cudaFree(c->pbuf);
     cudaFree(c->x32);
+    cudaFree(c->ppart);
     if (c->L.err) cudaFree(c->L.err);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
@@ -235,6 +239,7 @@ lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_c
     if (d->flags & ~LBE_FLAG_TWO_PASS) return LBE_EINVAL;
     long long N = (long long)d->nx * d->ny * d->nz;
     if (N > 0x7fffffffLL) return LBE_EINVAL;
+    if (d->ny > 65535 || d->nz > 65535) return LBE_EINVAL;  // launch-grid rows and planes
     int dev = d->device;
     if (dev >= 0) {
         if (cudaSetDevice(dev) != cudaSuccess) return LBE_EINVAL;
@@ -395,21 +400,27 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
     if (ncap != cap) {
         double *nb = nullptr;
         float4 *nx32 = nullptr;
+        double *npp = nullptr;
         CK(c, cudaMalloc((void **)&nb, blk.size() * sizeof(double)));
         cudaError_t e = cudaMalloc((void **)&nx32, x32.size() * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&npp, (size_t)PAIR_SPLIT_MAX * 6 * ncap * sizeof(double));
         if (e != cudaSuccess) {
             cudaFree(nb);
+            cudaFree(nx32);
             return cuda_fail(c, e, "add_particles: cudaMalloc");
         }
+        const size_t per_cap = PSTRIDE * sizeof(double) + 3 * sizeof(float4) + PAIR_SPLIT_MAX * 6 * sizeof(double);
         if (c->pbuf) {
             cudaFree(c->pbuf);
             cudaFree(c->x32);
-            c->bytes -= (size_t)cap * (PSTRIDE * sizeof(double) + 3 * sizeof(float4));
+            cudaFree(c->ppart);
+            c->bytes -= (size_t)cap * per_cap;
         }
         c->pbuf = nb;
         c->x32 = nx32;
+        c->ppart = npp;
         c->cap = ncap;
-        c->bytes += (size_t)ncap * (PSTRIDE * sizeof(double) + 3 * sizeof(float4));
+        c->bytes += (size_t)ncap * per_cap;
     }
     CK(c, cudaMemcpy(c->pbuf, blk.data(), blk.size() * sizeof(double), cudaMemcpyHostToDevice));
     CK(c, cudaMemcpy(c->x32, x32.data(), x32.size() * sizeof(float4), cudaMemcpyHostToDevice));

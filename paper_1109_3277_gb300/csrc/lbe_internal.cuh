@@ -104,6 +104,8 @@ struct Parts {
     double *Fpend, *Tpend;          // fill/empty momentum for the next update
     double *F, *T;                  // total of the last update
     unsigned long long *fix;        // [6n] link force and torque in 2^-40 fixed point
+    int nsplit;                     // pair-force splits of the j range
+    double *ppart;                  // [nsplit][6][n] pair-force partial sums
     float4 *X32;                    // FP32 (x, y, z, max radius) for the pair prefilter
     float4 *K32;                    // FP32 velocity [2p] and ω [2p+1] for the fused links
 };
@@ -151,6 +153,8 @@ int fused_zchunk(const Lat &L);
 void launch_links(int storage, const Lat &L, const Parts &P, void *fnew, const float *rho,
                   const uint8_t *type, const uint32_t *owner, cudaStream_t s);
 void launch_pairs(const Lat &L, const Parts &P, const Pair &pp, cudaStream_t s);
+constexpr int PAIR_SPLIT_MAX = 32;
+int pair_splits(int n);
 void launch_integrate(const Lat &L, const Parts &P, int mode, cudaStream_t s);
 void launch_claim(const Lat &L, const Parts &P, int first, uint32_t *owner_new, cudaStream_t s);
 void launch_transition(int storage, const Lat &L, const Parts &P, void *f, uint8_t *type,

@@ -408,6 +408,9 @@ __device__ void pair_term(const Lat &L, const Parts &P, const Pair &pp, int i, i
     }
 }
 
+// The j range is split over gridDim.y CTAs per i tile (enough CTAs to fill
+// the GPU); each split writes its partial sums, which k_integrate adds in
+// split order.
 __global__ void __launch_bounds__(PAIR_T) k_pairs(Lat L, Parts P, Pair pp)
 {
     __shared__ float4 tile[PAIR_T];
@@ -427,9 +430,13 @@ __global__ void __launch_bounds__(PAIR_T) k_pairs(Lat L, Parts P, Pair pp)
     bool per_z = !L.walls;
     float extra = (float)pp.lub_cut + 0.05f;
     double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-    for (int base = 0; base < P.n; base += PAIR_T) {
+    const int tiles = (P.n + PAIR_T - 1) / PAIR_T;
+    const int per = (tiles + gridDim.y - 1) / gridDim.y;
+    const int t0 = blockIdx.y * per, t1 = min(t0 + per, tiles);
+    for (int tt = t0; tt < t1; tt++) {
+        const int base = tt * PAIR_T;
         int j = base + threadIdx.x;
-        tile[threadIdx.x] = j < P.n ? P.X32[j] : make_float4(0.f, 0.f, 0.f, -1e30f);
+        tile[threadIdx.x] = j < P.n ? P.X32[j] : make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
         if (act) {
             int lim = min(PAIR_T, P.n - base);
@@ -448,8 +455,8 @@ __global__ void __launch_bounds__(PAIR_T) k_pairs(Lat L, Parts P, Pair pp)
     }
     if (act)
         for (int k = 0; k < 3; k++) {
-            P.Fpair[3 * i + k] = F[k];
-            P.Tpair[3 * i + k] = T[k];
+            P.ppart[((size_t)blockIdx.y * 6 + k) * P.n + i] = F[k];
+            P.ppart[((size_t)blockIdx.y * 6 + 3 + k) * P.n + i] = T[k];
         }
 }
 
@@ -497,8 +504,15 @@ __global__ void k_integrate(Lat L, Parts P, int mode)
         const double tl = P.Tlink[3 * p + k] + (double)(long long)P.fix[6 * p + 3 + k] * FIXED_UNIT;
         P.fix[6 * p + k] = 0ull;
         P.fix[6 * p + 3 + k] = 0ull;
-        F[k] = fl + P.Fpair[3 * p + k] + P.Fpend[3 * p + k];
-        T[k] = tl + P.Tpair[3 * p + k] + P.Tpend[3 * p + k];
+        double fp = 0.0, tp = 0.0;
+        for (int sp = 0; sp < P.nsplit; sp++) {
+            fp += P.ppart[((size_t)sp * 6 + k) * P.n + p];
+            tp += P.ppart[((size_t)sp * 6 + 3 + k) * P.n + p];
+        }
+        P.Fpair[3 * p + k] = fp;
+        P.Tpair[3 * p + k] = tp;
+        F[k] = fl + fp + P.Fpend[3 * p + k];
+        T[k] = tl + tp + P.Tpend[3 * p + k];
         P.F[3 * p + k] = F[k];
         P.T[3 * p + k] = T[k];
         P.Fpend[3 * p + k] = 0.0;
@@ -812,10 +826,21 @@ void launch_links(int storage, const Lat &L, const Parts &P, void *fnew, const f
     LBE_DISPATCH(storage, (k_links<S><<<P.n, PT, 0, s>>>(L, P, (typename S::T *)fnew, rho, type, owner)));
 }
 
+int pair_splits(int n)
+{
+    // about four CTAs per SM of a 152-SM GPU, at most PAIR_SPLIT_MAX splits
+    int tiles = (n + PAIR_T - 1) / PAIR_T;
+    int sp = (4 * 152 + tiles - 1) / tiles;
+    if (sp > tiles) sp = tiles;
+    if (sp > PAIR_SPLIT_MAX) sp = PAIR_SPLIT_MAX;
+    return sp < 1 ? 1 : sp;
+}
+
 void launch_pairs(const Lat &L, const Parts &P, const Pair &pp, cudaStream_t s)
 {
     if (P.n == 0) return;
-    k_pairs<<<(P.n + PAIR_T - 1) / PAIR_T, PAIR_T, 0, s>>>(L, P, pp);
+    dim3 grid((P.n + PAIR_T - 1) / PAIR_T, P.nsplit);
+    k_pairs<<<grid, PAIR_T, 0, s>>>(L, P, pp);
 }
 
 void launch_integrate(const Lat &L, const Parts &P, int mode, cudaStream_t s)
