@@ -153,6 +153,35 @@ LBE_API int32_t lbe_kernels_per_step(const lbe_ctx *c);
 /* Device bytes held by the context. */
 LBE_API size_t lbe_device_bytes(const lbe_ctx *c);
 
+/* Allocation-free FP64 mass sums.  The paper has no counterpart: this entry
+ * point exists for callers that keep their populations in memory they manage
+ * themselves and cannot call cudaMalloc (a fixed device-memory budget, a
+ * memory pool owned by another framework, or a place in their program where
+ * an allocation's implicit synchronisation is not allowed).  It computes the
+ * same per-component sums as lbe_mass, but on caller-owned buffers, and it
+ * allocates nothing: its per-block partial sums live in a fixed 16 KiB array
+ * (2 x 1024 doubles) that the library keeps on every GPU that loads it until
+ * the process exits.
+ *  f:         device pointer, populations of component c and direction i at
+ *             f + (c*19 + i) * slot_stride (elements of the storage type;
+ *             the 16-bit modes hold f - w_i rho_ref[c]);
+ *  node_type: device pointer, [nodes] bytes, 0 = fluid (summed), others skipped;
+ *  rho_ref:   host pointer to 2 doubles (ignored for LBE_STORE_F32);
+ *  out:       device pointer to 2 doubles, written in stream order;
+ *  device:    CUDA device ordinal, or -1 for the library's current device;
+ *  cuda_stream: the cudaStream_t to enqueue on (NULL = legacy default).
+ * Returns LBE_EINVAL for a null pointer, nodes < 1 or nodes >
+ * LBE_NOALLOC_MAX_NODES, slot_stride < nodes or an unknown storage mode;
+ * LBE_ECUDA if a CUDA call fails.  The first call on a device looks up the
+ * device address of the fixed array (cudaGetSymbolAddress): make that first
+ * call before any stream capture.  All calls share the one array, so calls
+ * that overlap on the GPU (other streams, other threads) race and must be
+ * ordered by the caller. */
+#define LBE_NOALLOC_MAX_NODES 2147483647LL
+LBE_API lbe_status lbe_mass_noalloc(const void *f, int32_t storage, const uint8_t *node_type,
+                                    int64_t nodes, int64_t slot_stride, const double rho_ref[2],
+                                    int32_t device, void *cuda_stream, double *out);
+
 LBE_API const char *lbe_last_error(const lbe_ctx *c);
 LBE_API void lbe_destroy(lbe_ctx *c);
 

@@ -61,6 +61,8 @@ SIGNATURES = {
     "lbe_profile_read": (ctypes.c_int, [_P, _D, ctypes.POINTER(ctypes.c_int64)]),
     "lbe_kernels_per_step": (ctypes.c_int32, [_P]),
     "lbe_device_bytes": (ctypes.c_size_t, [_P]),
+    "lbe_mass_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_int64, _D,
+                                         ctypes.c_int32, _P, _P]),
     "lbe_last_error": (ctypes.c_char_p, [_P]),
     "lbe_destroy": (None, [_P]),
 }
