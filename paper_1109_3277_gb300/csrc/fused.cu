@@ -89,45 +89,25 @@ __device__ __forceinline__ int tab_slot(int *ids, int p)
     return -1;
 }
 
-// Link from fluid node (gx, gy, z) to particle node m = node + c_i (called
-// off the hot path, so that the unrolled collision stays small): the
-// reflected population fs leaving the node along -c_i gains
-// C = 6 w_i ρ^c u_surf.(-c_i), u_surf = V + ω x r_b at the link midpoint
-// r_b = node + c_i/2 - X, and the particle receives (2 fs + C) c_i and
-// r_b x that, added in 2^-40 fixed point.  Returns fs + C.
-__device__ __noinline__ float link_term(const Lat &L, const Links &lk, int i, int m, int gx, int gy, int z,
-                                        float fs, float r, int *tids, unsigned long long *tacc)
+// Per-thread fixed-point sums of the link terms of one node, flushed to the
+// CTA table (or, if it is full, to the per-particle totals) per particle.
+struct LinkAcc {
+    int p;
+    unsigned long long v[6];
+};
+
+__device__ __forceinline__ void acc_flush(LinkAcc &a, const Links &lk, int *tids, unsigned long long *tacc)
 {
-    const float ci[3] = {(float)c_x[i], (float)c_y[i], (float)c_z[i]};
-    const int p = (int)lk.owner[m];
-    const float4 X = lk.X32[p], V = lk.K32[2 * p], W = lk.K32[2 * p + 1];
-    float rb[3] = {(float)gx - X.x, (float)gy - X.y, (float)z - X.z};
-    const float nl[3] = {(float)L.nx, (float)L.ny, (float)L.nz};
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        if (k < 2 || !L.walls) {
-            if (rb[k] > 0.5f * nl[k]) rb[k] -= nl[k];
-            if (rb[k] < -0.5f * nl[k]) rb[k] += nl[k];
-        }
-        rb[k] += 0.5f * ci[k];
-    }
-    const float us[3] = {V.x + W.y * rb[2] - W.z * rb[1], V.y + W.z * rb[0] - W.x * rb[2],
-                         V.z + W.x * rb[1] - W.y * rb[0]};
-    const float uci = us[0] * ci[0] + us[1] * ci[1] + us[2] * ci[2];
-    const float w = i < 7 ? 1.f / 18.f : 1.f / 36.f;
-    const float C = -6.f * w * r * uci;
-    const float a = 2.f * fs + C;
-    const float F[3] = {a * ci[0], a * ci[1], a * ci[2]};
-    const float Tq[3] = {rb[1] * F[2] - rb[2] * F[1], rb[2] * F[0] - rb[0] * F[2], rb[0] * F[1] - rb[1] * F[0]};
-    const int h = tab_slot(tids, p);
+    if (a.p < 0) return;
+    const int h = tab_slot(tids, a.p);
     for (int k = 0; k < 6; k++) {
-        const unsigned long long q = to_fixed(k < 3 ? F[k] : Tq[k - 3]);
         if (h >= 0)
-            atomicAdd(&tacc[k * TAB + h], q);
+            atomicAdd(&tacc[k * TAB + h], a.v[k]);
         else
-            atomicAdd(&lk.fix[6 * p + k], q);
+            atomicAdd(&lk.fix[6 * a.p + k], a.v[k]);
+        a.v[k] = 0ull;
     }
-    return fs + C;
+    a.p = -1;
 }
 
 // Wrapped neighbour index of a node on the lattice boundary (off the hot path).
@@ -138,6 +118,70 @@ __device__ __noinline__ int wrapped_nbr(const Lat &L, int gx, int gy, int z, int
     y = y < 0 ? y + L.ny : (y >= L.ny ? y - L.ny : y);
     zz = zz < 0 ? zz + L.nz : (zz >= L.nz ? zz - L.nz : zz);
     return x + L.nx * (y + L.ny * zz);
+}
+
+// All links of one fluid node (gx, gy, z) into particle nodes, one loop
+// over the set bits of pm (called off the hot path; lanes of a warp run the
+// same loop body, whatever directions their links take).  For direction i
+// the post-collision population f*_i is recomputed from the staged
+// populations and the node's equilibrium velocity; the reflected population
+// leaving along -c_i gains C = 6 w_i ρ^c u_surf.(-c_i) (Eq. 4) with
+// u_surf = V + ω x r_b at the link midpoint r_b = node + c_i/2 - X, and the
+// particle receives (2 f*_i + C) c_i and r_b x that (Eq. 5).
+template <class S>
+__device__ __noinline__ void link_node(const Lat &L, const Links &lk, const typename S::T *fb, typename S::T *dst,
+                                       const long long *pop, uint32_t pm, const float *ue, const float *uu15,
+                                       const float *rho, int n, bool inner, int gx, int gy, int z, int nxy,
+                                       int *tids, unsigned long long *tacc)
+{
+    LinkAcc acc;
+    acc.p = -1;
+    for (int k = 0; k < 6; k++) acc.v[k] = 0ull;
+    const float nl[3] = {(float)L.nx, (float)L.ny, (float)L.nz};
+    while (pm) {
+        const int i = __ffs(pm) - 1;
+        pm &= pm - 1;
+        const int m = inner ? n + c_x[i] + L.nx * c_y[i] + nxy * c_z[i] : wrapped_nbr(L, gx, gy, z, i);
+        const int p = (int)lk.owner[m];
+        if (p != acc.p) {
+            acc_flush(acc, lk, tids, tacc);
+            acc.p = p;
+        }
+        const float ci[3] = {(float)c_x[i], (float)c_y[i], (float)c_z[i]};
+        const float4 X = lk.X32[p], V = lk.K32[2 * p], W = lk.K32[2 * p + 1];
+        float rb[3] = {(float)gx - X.x, (float)gy - X.y, (float)z - X.z};
+        for (int k = 0; k < 3; k++) {
+            if (k < 2 || !L.walls) {
+                if (rb[k] > 0.5f * nl[k]) rb[k] -= nl[k];
+                if (rb[k] < -0.5f * nl[k]) rb[k] += nl[k];
+            }
+            rb[k] += 0.5f * ci[k];
+        }
+        const float us[3] = {V.x + W.y * rb[2] - W.z * rb[1], V.y + W.z * rb[0] - W.x * rb[2],
+                             V.z + W.x * rb[1] - W.y * rb[0]};
+        const float uci = us[0] * ci[0] + us[1] * ci[1] + us[2] * ci[2];
+        const float w = i < 7 ? 1.f / 18.f : 1.f / 36.f;
+        const int io = (i & 1) ? i + 1 : i - 1;
+        float a = 0.f;
+        for (int c = 0; c < 2; c++) {
+            const float r = rho[c];
+            const float cu = ci[0] * ue[3 * c] + ci[1] * ue[3 * c + 1] + ci[2] * ue[3 * c + 2];
+            const float wr = w * r;
+            const float feq = wr * (uu15[c] + 4.5f * cu * cu) + 3.f * wr * cu;
+            const float fi = S::cvt(fb[(c * Q + i) * NT], L.base[c][i]);
+            const float fs = fi - (fi - feq) * L.itau[c];
+            const float C = -6.f * wr * uci;
+            S::st(dst + pop[c * Q + io], fs + C, L.base[c][io]);
+            a += 2.f * fs + C;
+        }
+        const float F[3] = {a * ci[0], a * ci[1], a * ci[2]};
+        const float Tq[3] = {rb[1] * F[2] - rb[2] * F[1], rb[2] * F[0] - rb[0] * F[2], rb[0] * F[1] - rb[1] * F[0]};
+        for (int k = 0; k < 3; k++) {
+            acc.v[k] += to_fixed(F[k]);
+            acc.v[3 + k] += to_fixed(Tq[k]);
+        }
+    }
+    acc_flush(acc, lk, tids, tacc);
 }
 
 // Offsets of the population arrays, per lattice, passed with the launch:
@@ -331,22 +375,18 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
             T *dst = fout + n;
             // store of the post-collision population fs of direction i:
             // streamed to the neighbour, or reflected into slot opp(i) of
-            // this node; a reflection off a particle node goes through
-            // link_term (moving bounce-back, Eq. 4, momentum exchange, Eq. 5)
+            // this node; reflections off particle nodes are left to
+            // link_node after the loop (moving bounce-back, momentum exchange)
             auto put = [&](int c, int i, float fs, float r) {
                 const int ci = c * Q + i;
                 if (!(solid & (1u << i))) {
                     T *q = inner ? dst + ofs.push[ci] : fout + ofs.pop[ci] + wrapped_nbr(L, gx, gy, z, i);
                     S::st(q, fs, L.base[c][i]);
-                } else {
-                    float v = fs;
-                    if (part & (1u << i)) {
-                        const int m = inner ? n + (int)(ofs.push[i] - ofs.pop[i]) : wrapped_nbr(L, gx, gy, z, i);
-                        v = link_term(L, lk, i, m, gx, gy, z, fs, r, tids, tacc);
-                    }
-                    S::st(dst + ofs.pop[c * Q + opp(i)], v, L.base[c][opp(i)]);
+                } else if (!(part & (1u << i))) {
+                    S::st(dst + ofs.pop[c * Q + opp(i)], fs, L.base[c][opp(i)]);
                 }
             };
+            float ue_all[6], uu_all[2];
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 const float r = rho[c];
@@ -356,6 +396,10 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
                 for (int k = 0; k < 3; k++) ue[k] = up[k] + ir * (-L.g * pc[c] * s[c][k] + r * L.body[k]);
                 const float uu15 = 1.f - 1.5f * (ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2]);
                 const float it = L.itau[c];
+                ue_all[3 * c] = ue[0];
+                ue_all[3 * c + 1] = ue[1];
+                ue_all[3 * c + 2] = ue[2];
+                uu_all[c] = uu15;
                 float seq = 0.f;
                 // opposite pairs share the even part of the equilibrium
 #pragma unroll
@@ -374,6 +418,9 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
                 const float f0 = S::cvt(fb[(c * Q) * NT], L.base[c][0]);
                 S::st(dst + ofs.pop[c * Q], f0 - (f0 - (r - seq)) * it, L.base[c][0]);
             }
+            if (part)
+                link_node<S>(L, lk, fb, dst, ofs.pop, part, ue_all, uu_all, rho, n, inner, gx, gy, z, nxy, tids,
+                             tacc);
         }
         __syncthreads();
     }
