@@ -96,29 +96,39 @@ struct LinkAcc {
     unsigned long long v[6];
 };
 
-__device__ __forceinline__ void acc_flush(LinkAcc &a, const Links &lk, int *tids, unsigned long long *tacc)
+__device__ __forceinline__ void acc_flush(LinkAcc &a, unsigned long long *fix, int *tids,
+                                          unsigned long long *tacc)
 {
     if (a.p < 0) return;
     const int h = tab_slot(tids, a.p);
+#pragma unroll
     for (int k = 0; k < 6; k++) {
         if (h >= 0)
             atomicAdd(&tacc[k * TAB + h], a.v[k]);
         else
-            atomicAdd(&lk.fix[6 * a.p + k], a.v[k]);
+            atomicAdd(&fix[6 * a.p + k], a.v[k]);
         a.v[k] = 0ull;
     }
     a.p = -1;
 }
 
-// Wrapped neighbour index of a node on the lattice boundary (off the hot path).
-__device__ __noinline__ int wrapped_nbr(const Lat &L, int gx, int gy, int z, int i)
+// Wrapped neighbour index of a node on the lattice boundary (off the hot
+// path; scalar arguments only, so that nothing is copied to local memory).
+__device__ __noinline__ int wrapped_nbr(int nx, int ny, int nz, int gx, int gy, int z, int i)
 {
     int x = gx + c_x[i], y = gy + c_y[i], zz = z + c_z[i];
-    x = x < 0 ? x + L.nx : (x >= L.nx ? x - L.nx : x);
-    y = y < 0 ? y + L.ny : (y >= L.ny ? y - L.ny : y);
-    zz = zz < 0 ? zz + L.nz : (zz >= L.nz ? zz - L.nz : zz);
-    return x + L.nx * (y + L.ny * zz);
+    x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+    y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+    zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+    return x + nx * (y + ny * zz);
 }
+
+// Per-node values link_node needs, passed by value.
+struct NodeEq {
+    float ue0, ue1, ue2, ue3, ue4, ue5;  // equilibrium velocity of components 0 and 1
+    float uu0, uu1;                      // 1 - 1.5 |ue|^2 per component
+    float r0, r1;                        // densities
+};
 
 // All links of one fluid node (gx, gy, z) into particle nodes, one loop
 // over the set bits of pm (called off the hot path; lanes of a warp run the
@@ -127,61 +137,71 @@ __device__ __noinline__ int wrapped_nbr(const Lat &L, int gx, int gy, int z, int
 // populations and the node's equilibrium velocity; the reflected population
 // leaving along -c_i gains C = 6 w_i ρ^c u_surf.(-c_i) (Eq. 4) with
 // u_surf = V + ω x r_b at the link midpoint r_b = node + c_i/2 - X, and the
-// particle receives (2 f*_i + C) c_i and r_b x that (Eq. 5).
+// particle receives (2 f*_i + C) c_i and r_b x that (Eq. 5).  Only scalars
+// and pointers are passed, so that no argument is copied to local memory.
 template <class S>
-__device__ __noinline__ void link_node(const Lat &L, const Links &lk, const typename S::T *fb, typename S::T *dst,
-                                       const long long *pop, uint32_t pm, const float *ue, const float *uu15,
-                                       const float *rho, int n, bool inner, int gx, int gy, int z, int nxy,
-                                       int *tids, unsigned long long *tacc)
+__device__ __noinline__ void link_node(const typename S::T *fb, typename S::T *dst, long long stride, uint32_t pm,
+                                       NodeEq q, float it0, float it1, float b1r, float b2r, float b1b, float b2b,
+                                       int n, bool inner, int gx, int gy, int z, int nx, int ny, int nz, int walls,
+                                       const uint32_t *owner, const float4 *X32, const float4 *K32,
+                                       unsigned long long *fix, int *tids, unsigned long long *tacc)
 {
     LinkAcc acc;
     acc.p = -1;
+#pragma unroll
     for (int k = 0; k < 6; k++) acc.v[k] = 0ull;
-    const float nl[3] = {(float)L.nx, (float)L.ny, (float)L.nz};
+    const int nxy = nx * ny;
     while (pm) {
         const int i = __ffs(pm) - 1;
         pm &= pm - 1;
-        const int m = inner ? n + c_x[i] + L.nx * c_y[i] + nxy * c_z[i] : wrapped_nbr(L, gx, gy, z, i);
-        const int p = (int)lk.owner[m];
+        const int cxi = c_x[i], cyi = c_y[i], czi = c_z[i];
+        const int m = inner ? n + cxi + nx * cyi + nxy * czi : wrapped_nbr(nx, ny, nz, gx, gy, z, i);
+        const int p = (int)owner[m];
         if (p != acc.p) {
-            acc_flush(acc, lk, tids, tacc);
+            acc_flush(acc, fix, tids, tacc);
             acc.p = p;
         }
-        const float ci[3] = {(float)c_x[i], (float)c_y[i], (float)c_z[i]};
-        const float4 X = lk.X32[p], V = lk.K32[2 * p], W = lk.K32[2 * p + 1];
-        float rb[3] = {(float)gx - X.x, (float)gy - X.y, (float)z - X.z};
-        for (int k = 0; k < 3; k++) {
-            if (k < 2 || !L.walls) {
-                if (rb[k] > 0.5f * nl[k]) rb[k] -= nl[k];
-                if (rb[k] < -0.5f * nl[k]) rb[k] += nl[k];
-            }
-            rb[k] += 0.5f * ci[k];
+        const float4 X = X32[p], V = K32[2 * p], W = K32[2 * p + 1];
+        float rx = (float)gx - X.x, ry = (float)gy - X.y, rz = (float)z - X.z;
+        if (rx > 0.5f * nx) rx -= nx;
+        if (rx < -0.5f * nx) rx += nx;
+        if (ry > 0.5f * ny) ry -= ny;
+        if (ry < -0.5f * ny) ry += ny;
+        if (!walls) {
+            if (rz > 0.5f * nz) rz -= nz;
+            if (rz < -0.5f * nz) rz += nz;
         }
-        const float us[3] = {V.x + W.y * rb[2] - W.z * rb[1], V.y + W.z * rb[0] - W.x * rb[2],
-                             V.z + W.x * rb[1] - W.y * rb[0]};
-        const float uci = us[0] * ci[0] + us[1] * ci[1] + us[2] * ci[2];
-        const float w = i < 7 ? 1.f / 18.f : 1.f / 36.f;
+        rx += 0.5f * cxi;
+        ry += 0.5f * cyi;
+        rz += 0.5f * czi;
+        const float usx = V.x + W.y * rz - W.z * ry, usy = V.y + W.z * rx - W.x * rz, usz = V.z + W.x * ry - W.y * rx;
+        const float uci = usx * cxi + usy * cyi + usz * czi;
+        const bool axis = i < 7;
+        const float w = axis ? 1.f / 18.f : 1.f / 36.f;
         const int io = (i & 1) ? i + 1 : i - 1;
         float a = 0.f;
+#pragma unroll
         for (int c = 0; c < 2; c++) {
-            const float r = rho[c];
-            const float cu = ci[0] * ue[3 * c] + ci[1] * ue[3 * c + 1] + ci[2] * ue[3 * c + 2];
+            const float r = c ? q.r1 : q.r0;
+            const float cu = c ? cxi * q.ue3 + cyi * q.ue4 + czi * q.ue5 : cxi * q.ue0 + cyi * q.ue1 + czi * q.ue2;
             const float wr = w * r;
-            const float feq = wr * (uu15[c] + 4.5f * cu * cu) + 3.f * wr * cu;
-            const float fi = S::cvt(fb[(c * Q + i) * NT], L.base[c][i]);
-            const float fs = fi - (fi - feq) * L.itau[c];
+            const float feq = wr * ((c ? q.uu1 : q.uu0) + 4.5f * cu * cu) + 3.f * wr * cu;
+            const float base = c ? (axis ? b1b : b2b) : (axis ? b1r : b2r);
+            const float fi = S::cvt(fb[(c * Q + i) * NT], base);
+            const float fs = fi - (fi - feq) * (c ? it1 : it0);
             const float C = -6.f * wr * uci;
-            S::st(dst + pop[c * Q + io], fs + C, L.base[c][io]);
+            S::st(dst + (long long)(c * Q + io) * stride, fs + C, base);
             a += 2.f * fs + C;
         }
-        const float F[3] = {a * ci[0], a * ci[1], a * ci[2]};
-        const float Tq[3] = {rb[1] * F[2] - rb[2] * F[1], rb[2] * F[0] - rb[0] * F[2], rb[0] * F[1] - rb[1] * F[0]};
-        for (int k = 0; k < 3; k++) {
-            acc.v[k] += to_fixed(F[k]);
-            acc.v[3 + k] += to_fixed(Tq[k]);
-        }
+        const float Fx = a * cxi, Fy = a * cyi, Fz = a * czi;
+        acc.v[0] += to_fixed(Fx);
+        acc.v[1] += to_fixed(Fy);
+        acc.v[2] += to_fixed(Fz);
+        acc.v[3] += to_fixed(ry * Fz - rz * Fy);
+        acc.v[4] += to_fixed(rz * Fx - rx * Fz);
+        acc.v[5] += to_fixed(rx * Fy - ry * Fx);
     }
-    acc_flush(acc, lk, tids, tacc);
+    acc_flush(acc, fix, tids, tacc);
 }
 
 // Offsets of the population arrays, per lattice, passed with the launch:
@@ -380,13 +400,13 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
             auto put = [&](int c, int i, float fs, float r) {
                 const int ci = c * Q + i;
                 if (!(solid & (1u << i))) {
-                    T *q = inner ? dst + ofs.push[ci] : fout + ofs.pop[ci] + wrapped_nbr(L, gx, gy, z, i);
+                    T *q = inner ? dst + ofs.push[ci] : fout + ofs.pop[ci] + wrapped_nbr(L.nx, L.ny, L.nz, gx, gy, z, i);
                     S::st(q, fs, L.base[c][i]);
                 } else if (!(part & (1u << i))) {
                     S::st(dst + ofs.pop[c * Q + opp(i)], fs, L.base[c][opp(i)]);
                 }
             };
-            float ue_all[6], uu_all[2];
+            NodeEq q;
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 const float r = rho[c];
@@ -396,10 +416,19 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
                 for (int k = 0; k < 3; k++) ue[k] = up[k] + ir * (-L.g * pc[c] * s[c][k] + r * L.body[k]);
                 const float uu15 = 1.f - 1.5f * (ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2]);
                 const float it = L.itau[c];
-                ue_all[3 * c] = ue[0];
-                ue_all[3 * c + 1] = ue[1];
-                ue_all[3 * c + 2] = ue[2];
-                uu_all[c] = uu15;
+                if (c == 0) {
+                    q.ue0 = ue[0];
+                    q.ue1 = ue[1];
+                    q.ue2 = ue[2];
+                    q.uu0 = uu15;
+                    q.r0 = r;
+                } else {
+                    q.ue3 = ue[0];
+                    q.ue4 = ue[1];
+                    q.ue5 = ue[2];
+                    q.uu1 = uu15;
+                    q.r1 = r;
+                }
                 float seq = 0.f;
                 // opposite pairs share the even part of the equilibrium
 #pragma unroll
@@ -419,8 +448,9 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
                 S::st(dst + ofs.pop[c * Q], f0 - (f0 - (r - seq)) * it, L.base[c][0]);
             }
             if (part)
-                link_node<S>(L, lk, fb, dst, ofs.pop, part, ue_all, uu_all, rho, n, inner, gx, gy, z, nxy, tids,
-                             tacc);
+                link_node<S>(fb, dst, L.S, part, q, L.itau[0], L.itau[1], L.base[0][1], L.base[0][7], L.base[1][1],
+                             L.base[1][7], n, inner, gx, gy, z, L.nx, L.ny, L.nz, L.walls, lk.owner, lk.X32,
+                             lk.K32, lk.fix, tids, tacc);
         }
         __syncthreads();
     }
