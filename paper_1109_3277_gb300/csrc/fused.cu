@@ -59,7 +59,8 @@ struct Smem {
     static constexpr size_t smo = sps + 3 * 2 * HN * sizeof(float);             // float [2][5][NT]
     static constexpr size_t tacc = smo + 2 * 5 * NT * sizeof(float);           // int64 [6][TAB]
     static constexpr size_t tid_ = tacc + 6 * TAB * sizeof(long long);          // int [TAB]
-    static constexpr size_t sty = tid_ + TAB * sizeof(int);                     // uint8 [3][HN]
+    static constexpr size_t sow = tid_ + TAB * sizeof(int);                     // int [3][HN] owners
+    static constexpr size_t sty = sow + 3 * HN * sizeof(int);                   // uint8 [3][HN]
     static constexpr size_t bytes = sty + 3 * HN;
 };
 
@@ -142,26 +143,28 @@ struct NodeEq {
 template <class S>
 __device__ __noinline__ void link_node(const typename S::T *fb, typename S::T *dst, long long stride, uint32_t pm,
                                        NodeEq q, float it0, float it1, float b1r, float b2r, float b1b, float b2b,
-                                       int n, bool inner, int gx, int gy, int z, int nx, int ny, int nz, int walls,
-                                       const uint32_t *owner, const float4 *X32, const float4 *K32,
+                                       int ec, const int *ow0, const int *ow1, const int *ow2, int gx, int gy, int z,
+                                       int nx, int ny, int nz, int walls, const float4 *X32, const float4 *K32,
                                        unsigned long long *fix, int *tids, unsigned long long *tacc)
 {
     LinkAcc acc;
     acc.p = -1;
 #pragma unroll
     for (int k = 0; k < 6; k++) acc.v[k] = 0ull;
-    const int nxy = nx * ny;
+    float4 X = make_float4(0.f, 0.f, 0.f, 0.f), V = X, W = X;
     while (pm) {
         const int i = __ffs(pm) - 1;
         pm &= pm - 1;
         const int cxi = c_x[i], cyi = c_y[i], czi = c_z[i];
-        const int m = inner ? n + cxi + nx * cyi + nxy * czi : wrapped_nbr(nx, ny, nz, gx, gy, z, i);
-        const int p = (int)owner[m];
+        const int e = ec + cyi * HX + cxi;
+        const int p = czi < 0 ? ow0[e] : (czi == 0 ? ow1[e] : ow2[e]);
         if (p != acc.p) {
             acc_flush(acc, fix, tids, tacc);
             acc.p = p;
+            X = X32[p];
+            V = K32[2 * p];
+            W = K32[2 * p + 1];
         }
-        const float4 X = X32[p], V = K32[2 * p], W = K32[2 * p + 1];
         float rx = (float)gx - X.x, ry = (float)gy - X.y, rz = (float)z - X.z;
         if (rx > 0.5f * nx) rx -= nx;
         if (rx < -0.5f * nx) rx += nx;
@@ -227,6 +230,7 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
     uint8_t *sty = smem + Smem<S>::sty;                             // [slot][e]
     unsigned long long *tacc = reinterpret_cast<unsigned long long *>(smem + Smem<S>::tacc);  // [k][TAB]
     int *tids = reinterpret_cast<int *>(smem + Smem<S>::tid_);      // [TAB]
+    int *sow = reinterpret_cast<int *>(smem + Smem<S>::sow);        // [slot][e] particle owners
     for (int e = threadIdx.x; e < TAB; e += NT) {
         tids[e] = -1;
 #pragma unroll
@@ -276,6 +280,7 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
         }
         float *ps = sps + slot * 2 * HN;
         uint8_t *ts = sty + slot * HN;
+        int *os = sow + slot * HN;
         {
             float p0 = 0.f, p1 = 0.f;
             uint8_t t = WALL;
@@ -327,6 +332,7 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
                 } else {
                     p0 = psi[n];
                     p1 = psi[(size_t)L.N + n];
+                    if (t == PART) os[ec] = (int)lk.owner[n];
                 }
             }
             ps[ec] = p0;
@@ -352,6 +358,7 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
                 } else {
                     p0 = psi[n];
                     p1 = psi[(size_t)L.N + n];
+                    if (t == PART) os[he] = (int)lk.owner[n];
                 }
             }
             ps[he] = p0;
@@ -449,8 +456,9 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
             }
             if (part)
                 link_node<S>(fb, dst, L.S, part, q, L.itau[0], L.itau[1], L.base[0][1], L.base[0][7], L.base[1][1],
-                             L.base[1][7], n, inner, gx, gy, z, L.nx, L.ny, L.nz, L.walls, lk.owner, lk.X32,
-                             lk.K32, lk.fix, tids, tacc);
+                             L.base[1][7], ec, sow + ((z + 2) % 3) * HN, sow + (z % 3) * HN,
+                             sow + ((z + 1) % 3) * HN, gx, gy, z, L.nx, L.ny, L.nz, L.walls, lk.X32, lk.K32, lk.fix,
+                             tids, tacc);
         }
         __syncthreads();
     }
