@@ -45,7 +45,8 @@ __device__ __forceinline__ int wrapc(int v, int n)
     return v < 0 ? v + n : v;
 }
 
-constexpr int TAB = 128;  // per-CTA particle table (power of two)
+constexpr int TAB = 128;       // per-CTA particle table (power of two)
+constexpr int QCAP = 8 * NT;   // link queue of a CTA (one round of the link pass)
 
 __constant__ int c_x[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
 __constant__ int c_y[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
@@ -60,7 +61,9 @@ struct Smem {
     static constexpr size_t tacc = smo + 2 * 5 * NT * sizeof(float);           // int64 [6][TAB]
     static constexpr size_t tid_ = tacc + 6 * TAB * sizeof(long long);          // int [TAB]
     static constexpr size_t sow = tid_ + TAB * sizeof(int);                     // int [3][HN] owners
-    static constexpr size_t sty = sow + 3 * HN * sizeof(int);                   // uint8 [3][HN]
+    static constexpr size_t lq = sow + 3 * HN * sizeof(int);                    // uint16 [QCAP]
+    static constexpr size_t lqn = lq + QCAP * sizeof(unsigned short);           // int
+    static constexpr size_t sty = lqn + 16;                                      // uint8 [3][HN]
     static constexpr size_t bytes = sty + 3 * HN;
 };
 
@@ -90,29 +93,6 @@ __device__ __forceinline__ int tab_slot(int *ids, int p)
     return -1;
 }
 
-// Per-thread fixed-point sums of the link terms of one node, flushed to the
-// CTA table (or, if it is full, to the per-particle totals) per particle.
-struct LinkAcc {
-    int p;
-    unsigned long long v[6];
-};
-
-__device__ __forceinline__ void acc_flush(LinkAcc &a, unsigned long long *fix, int *tids,
-                                          unsigned long long *tacc)
-{
-    if (a.p < 0) return;
-    const int h = tab_slot(tids, a.p);
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-        if (h >= 0)
-            atomicAdd(&tacc[k * TAB + h], a.v[k]);
-        else
-            atomicAdd(&fix[6 * a.p + k], a.v[k]);
-        a.v[k] = 0ull;
-    }
-    a.p = -1;
-}
-
 // Wrapped neighbour index of a node on the lattice boundary (off the hot
 // path; scalar arguments only, so that nothing is copied to local memory).
 __device__ __noinline__ int wrapped_nbr(int nx, int ny, int nz, int gx, int gy, int z, int i)
@@ -124,87 +104,92 @@ __device__ __noinline__ int wrapped_nbr(int nx, int ny, int nz, int gx, int gy, 
     return x + nx * (y + ny * zz);
 }
 
-// Per-node values link_node needs, passed by value.
-struct NodeEq {
-    float ue0, ue1, ue2, ue3, ue4, ue5;  // equilibrium velocity of components 0 and 1
-    float uu0, uu1;                      // 1 - 1.5 |ue|^2 per component
-    float r0, r1;                        // densities
-};
-
-// All links of one fluid node (gx, gy, z) into particle nodes, one loop
-// over the set bits of pm (called off the hot path; lanes of a warp run the
-// same loop body, whatever directions their links take).  For direction i
-// the post-collision population f*_i is recomputed from the staged
-// populations and the node's equilibrium velocity; the reflected population
-// leaving along -c_i gains C = 6 w_i ρ^c u_surf.(-c_i) (Eq. 4) with
-// u_surf = V + ω x r_b at the link midpoint r_b = node + c_i/2 - X, and the
-// particle receives (2 f*_i + C) c_i and r_b x that (Eq. 5).  Only scalars
-// and pointers are passed, so that no argument is copied to local memory.
+// One link of the link pass: node t of the CTA's tile (plane z) to the
+// particle node along c_i.  The node's moments, the ψ ring and the staged
+// populations are still in shared memory, so the node's equilibrium
+// velocity and f*_i are recomputed here.  The population reflected along
+// -c_i gains C = 6 w_i ρ^c u_surf.(-c_i) (Eq. 4), u_surf = V + ω x r_b at
+// the link midpoint r_b = node + c_i/2 - X, and the particle receives
+// (2 f*_i + C) c_i and r_b x that (Eq. 5), in 2^-40 fixed point.
 template <class S>
-__device__ __noinline__ void link_node(const typename S::T *fb, typename S::T *dst, long long stride, uint32_t pm,
-                                       NodeEq q, float it0, float it1, float b1r, float b2r, float b1b, float b2b,
-                                       int ec, const int *ow0, const int *ow1, const int *ow2, int gx, int gy, int z,
-                                       int nx, int ny, int nz, int walls, const float4 *X32, const float4 *K32,
-                                       unsigned long long *fix, int *tids, unsigned long long *tacc)
+__device__ __forceinline__ void link_pass(const Lat &L, const Links &lk, int t, int i, int z, int x0, int y0,
+                                          const typename S::T *fbuf, const float *smo, const float *sps,
+                                          const int *sow, typename S::T *fout, int *tids, unsigned long long *tacc)
 {
-    LinkAcc acc;
-    acc.p = -1;
+    const int ttx = t % TX, tty = t / TX;
+    const int lx = wrapc(x0 + ttx, L.nx), ly = wrapc(y0 + tty, L.ny);
+    const int nn = lx + L.nx * (ly + L.ny * z);
+    const int ec = (tty + 1) * HX + (ttx + 1);
+    const int sl[3] = {((z + 2) % 3), (z % 3), ((z + 1) % 3)};
+    const int cxi = c_x[i], cyi = c_y[i], czi = c_z[i];
+    const int sli = czi < 0 ? sl[0] : (czi == 0 ? sl[1] : sl[2]);
+    const int p = sow[sli * HN + ec + cyi * HX + cxi];
+    // the node's equilibrium velocity (as in the collision)
+    const int par = z & 1;
+    const float *mo = smo + par * 5 * NT + t;
+    const float rho[2] = {mo[0], mo[NT]};
+    const float up[3] = {mo[2 * NT], mo[3 * NT], mo[4 * NT]};
+    float s0x = 0.f, s0y = 0.f, s0z = 0.f, s1x = 0.f, s1y = 0.f, s1z = 0.f;
 #pragma unroll
-    for (int k = 0; k < 6; k++) acc.v[k] = 0ull;
-    float4 X = make_float4(0.f, 0.f, 0.f, 0.f), V = X, W = X;
-    while (pm) {
-        const int i = __ffs(pm) - 1;
-        pm &= pm - 1;
-        const int cxi = c_x[i], cyi = c_y[i], czi = c_z[i];
-        const int e = ec + cyi * HX + cxi;
-        const int p = czi < 0 ? ow0[e] : (czi == 0 ? ow1[e] : ow2[e]);
-        if (p != acc.p) {
-            acc_flush(acc, fix, tids, tacc);
-            acc.p = p;
-            X = X32[p];
-            V = K32[2 * p];
-            W = K32[2 * p + 1];
-        }
-        float rx = (float)gx - X.x, ry = (float)gy - X.y, rz = (float)z - X.z;
-        if (rx > 0.5f * nx) rx -= nx;
-        if (rx < -0.5f * nx) rx += nx;
-        if (ry > 0.5f * ny) ry -= ny;
-        if (ry < -0.5f * ny) ry += ny;
-        if (!walls) {
-            if (rz > 0.5f * nz) rz -= nz;
-            if (rz < -0.5f * nz) rz += nz;
-        }
-        rx += 0.5f * cxi;
-        ry += 0.5f * cyi;
-        rz += 0.5f * czi;
-        const float usx = V.x + W.y * rz - W.z * ry, usy = V.y + W.z * rx - W.x * rz, usz = V.z + W.x * ry - W.y * rx;
-        const float uci = usx * cxi + usy * cyi + usz * czi;
-        const bool axis = i < 7;
-        const float w = axis ? 1.f / 18.f : 1.f / 36.f;
-        const int io = (i & 1) ? i + 1 : i - 1;
-        float a = 0.f;
-#pragma unroll
-        for (int c = 0; c < 2; c++) {
-            const float r = c ? q.r1 : q.r0;
-            const float cu = c ? cxi * q.ue3 + cyi * q.ue4 + czi * q.ue5 : cxi * q.ue0 + cyi * q.ue1 + czi * q.ue2;
-            const float wr = w * r;
-            const float feq = wr * ((c ? q.uu1 : q.uu0) + 4.5f * cu * cu) + 3.f * wr * cu;
-            const float base = c ? (axis ? b1b : b2b) : (axis ? b1r : b2r);
-            const float fi = S::cvt(fb[(c * Q + i) * NT], base);
-            const float fs = fi - (fi - feq) * (c ? it1 : it0);
-            const float C = -6.f * wr * uci;
-            S::st(dst + (long long)(c * Q + io) * stride, fs + C, base);
-            a += 2.f * fs + C;
-        }
-        const float Fx = a * cxi, Fy = a * cyi, Fz = a * czi;
-        acc.v[0] += to_fixed(Fx);
-        acc.v[1] += to_fixed(Fy);
-        acc.v[2] += to_fixed(Fz);
-        acc.v[3] += to_fixed(ry * Fz - rz * Fy);
-        acc.v[4] += to_fixed(rz * Fx - rx * Fz);
-        acc.v[5] += to_fixed(rx * Fy - ry * Fx);
+    for (int j = 1; j < Q; j++) {
+        const float *pp = sps + sl[cz(j) + 1] * 2 * HN + ec + cy(j) * HX + cx(j);
+        const float p0 = pp[0], p1 = pp[HN];
+        if (cx(j)) { s0x += cx(j) * p1; s1x += cx(j) * p0; }
+        if (cy(j)) { s0y += cy(j) * p1; s1y += cy(j) * p0; }
+        if (cz(j)) { s0z += cz(j) * p1; s1z += cz(j) * p0; }
     }
-    acc_flush(acc, fix, tids, tacc);
+    const float pc0 = sps[sl[1] * 2 * HN + ec], pc1 = sps[sl[1] * 2 * HN + HN + ec];
+    const float4 X = lk.X32[p], V = lk.K32[2 * p], W = lk.K32[2 * p + 1];
+    float rx = (float)lx - X.x, ry = (float)ly - X.y, rz = (float)z - X.z;
+    if (rx > 0.5f * L.nx) rx -= L.nx;
+    if (rx < -0.5f * L.nx) rx += L.nx;
+    if (ry > 0.5f * L.ny) ry -= L.ny;
+    if (ry < -0.5f * L.ny) ry += L.ny;
+    if (!L.walls) {
+        if (rz > 0.5f * L.nz) rz -= L.nz;
+        if (rz < -0.5f * L.nz) rz += L.nz;
+    }
+    rx += 0.5f * cxi;
+    ry += 0.5f * cyi;
+    rz += 0.5f * czi;
+    const float usx = V.x + W.y * rz - W.z * ry, usy = V.y + W.z * rx - W.x * rz, usz = V.z + W.x * ry - W.y * rx;
+    const float uci = usx * cxi + usy * cyi + usz * czi;
+    const bool axis = i < 7;
+    const float w = axis ? 1.f / 18.f : 1.f / 36.f;
+    const int io = (i & 1) ? i + 1 : i - 1;
+    const typename S::T *fbt = fbuf + par * 2 * Q * NT + t;
+    float a = 0.f;
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        const float r = rho[c];
+        const float pcc = c ? pc1 : pc0;
+        const float sx = c ? s1x : s0x, sy = c ? s1y : s0y, sz = c ? s1z : s0z;
+        const float ir = r > 0.f ? L.tau[c] / r : 0.f;
+        const float ux = up[0] + ir * (-L.g * pcc * sx + r * L.body[0]);
+        const float uy = up[1] + ir * (-L.g * pcc * sy + r * L.body[1]);
+        const float uz = up[2] + ir * (-L.g * pcc * sz + r * L.body[2]);
+        const float uu15 = 1.f - 1.5f * (ux * ux + uy * uy + uz * uz);
+        const float cu = cxi * ux + cyi * uy + czi * uz;
+        const float wr = w * r;
+        const float feq = wr * (uu15 + 4.5f * cu * cu) + 3.f * wr * cu;
+        const float base = axis ? L.base[c][1] : L.base[c][7];
+        const float fi = S::cvt(fbt[(c * Q + i) * NT], base);
+        const float fs = fi - (fi - feq) * L.itau[c];
+        const float C = -6.f * wr * uci;
+        S::st(fout + nn + (long long)(c * Q + io) * L.S, fs + C, base);
+        a += 2.f * fs + C;
+    }
+    const float Fx = a * cxi, Fy = a * cyi, Fz = a * czi;
+    const float vv[6] = {Fx, Fy, Fz, ry * Fz - rz * Fy, rz * Fx - rx * Fz, rx * Fy - ry * Fx};
+    const int h = tab_slot(tids, p);
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        const unsigned long long qv = to_fixed(vv[k]);
+        if (h >= 0)
+            atomicAdd(&tacc[k * TAB + h], qv);
+        else
+            atomicAdd(&lk.fix[6 * p + k], qv);
+    }
 }
 
 // Offsets of the population arrays, per lattice, passed with the launch:
@@ -231,6 +216,9 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
     unsigned long long *tacc = reinterpret_cast<unsigned long long *>(smem + Smem<S>::tacc);  // [k][TAB]
     int *tids = reinterpret_cast<int *>(smem + Smem<S>::tid_);      // [TAB]
     int *sow = reinterpret_cast<int *>(smem + Smem<S>::sow);        // [slot][e] particle owners
+    unsigned short *lq = reinterpret_cast<unsigned short *>(smem + Smem<S>::lq);  // link queue
+    int *lqn = reinterpret_cast<int *>(smem + Smem<S>::lqn);        // queue length
+    if (threadIdx.x == 0) *lqn = 0;
     for (int e = threadIdx.x; e < TAB; e += NT) {
         tids[e] = -1;
 #pragma unroll
@@ -371,6 +359,18 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
     load_plane(zb, true);
     const bool xy_inner = gx >= 1 && gx <= L.nx - 2 && gy >= 1 && gy <= L.ny - 2;
     for (int z = zb; z < ze; z++) {
+        uint32_t my_part = 0;  // this node's particle links and their queue position
+        int my_at = 0;
+        auto enqueue = [&](int r0) {
+            uint32_t pm = my_part;
+            int at = my_at;
+            while (pm) {
+                const int i = __ffs(pm) - 1;
+                pm &= pm - 1;
+                if (at >= r0 && at < r0 + QCAP) lq[at - r0] = (unsigned short)(tid | (i << 8));
+                at++;
+            }
+        };
         load_plane(z + 1, z + 1 < ze);
         __syncthreads();
         // ring slots of planes z-1, z, z+1
@@ -402,8 +402,8 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
             T *dst = fout + n;
             // store of the post-collision population fs of direction i:
             // streamed to the neighbour, or reflected into slot opp(i) of
-            // this node; reflections off particle nodes are left to
-            // link_node after the loop (moving bounce-back, momentum exchange)
+            // this node; reflections off particle nodes are queued for the
+            // link pass after the plane (moving bounce-back, momentum exchange)
             auto put = [&](int c, int i, float fs, float r) {
                 const int ci = c * Q + i;
                 if (!(solid & (1u << i))) {
@@ -413,7 +413,6 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
                     S::st(dst + ofs.pop[c * Q + opp(i)], fs, L.base[c][opp(i)]);
                 }
             };
-            NodeEq q;
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 const float r = rho[c];
@@ -423,19 +422,7 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
                 for (int k = 0; k < 3; k++) ue[k] = up[k] + ir * (-L.g * pc[c] * s[c][k] + r * L.body[k]);
                 const float uu15 = 1.f - 1.5f * (ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2]);
                 const float it = L.itau[c];
-                if (c == 0) {
-                    q.ue0 = ue[0];
-                    q.ue1 = ue[1];
-                    q.ue2 = ue[2];
-                    q.uu0 = uu15;
-                    q.r0 = r;
-                } else {
-                    q.ue3 = ue[0];
-                    q.ue4 = ue[1];
-                    q.ue5 = ue[2];
-                    q.uu1 = uu15;
-                    q.r1 = r;
-                }
+
                 float seq = 0.f;
                 // opposite pairs share the even part of the equilibrium
 #pragma unroll
@@ -454,13 +441,29 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
                 const float f0 = S::cvt(fb[(c * Q) * NT], L.base[c][0]);
                 S::st(dst + ofs.pop[c * Q], f0 - (f0 - (r - seq)) * it, L.base[c][0]);
             }
-            if (part)
-                link_node<S>(fb, dst, L.S, part, q, L.itau[0], L.itau[1], L.base[0][1], L.base[0][7], L.base[1][1],
-                             L.base[1][7], ec, sow + ((z + 2) % 3) * HN, sow + (z % 3) * HN,
-                             sow + ((z + 1) % 3) * HN, gx, gy, z, L.nx, L.ny, L.nz, L.walls, lk.X32, lk.K32, lk.fix,
-                             tids, tacc);
+            if (part) {
+                // queue this node's particle links: (node, direction) in 16 bits
+                my_part = part;
+                my_at = atomicAdd(lqn, __popc(part));
+                enqueue(0);
+            }
         }
         __syncthreads();
+        // Link pass: every thread takes queued links (in rounds of QCAP).
+        const int total = *lqn;
+        for (int r0 = 0; r0 < total; r0 += QCAP) {
+            if (r0 > 0) {
+                enqueue(r0);
+                __syncthreads();
+            }
+            const int nq = min(total - r0, QCAP);
+            for (int qi = tid; qi < nq; qi += NT) {
+                const int ent = lq[qi];
+                link_pass<S>(L, lk, ent & 255, ent >> 8, z, x0, y0, fbuf, smo, sps, sow, fout, tids, tacc);
+            }
+            __syncthreads();
+        }
+        if (tid == 0) *lqn = 0;
     }
     // flush the per-particle link sums of this CTA
     for (int e = threadIdx.x; e < TAB; e += NT) {
