@@ -46,7 +46,6 @@ __device__ __forceinline__ int wrapc(int v, int n)
 }
 
 constexpr int TAB = 128;       // per-CTA particle table (power of two)
-constexpr int QCAP = 8 * NT;   // link queue of a CTA (one round of the link pass)
 
 __constant__ int c_x[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
 __constant__ int c_y[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
@@ -61,8 +60,9 @@ struct Smem {
     static constexpr size_t tacc = smo + 2 * 5 * NT * sizeof(float);           // int64 [6][TAB]
     static constexpr size_t tid_ = tacc + 6 * TAB * sizeof(long long);          // int [TAB]
     static constexpr size_t sow = tid_ + TAB * sizeof(int);                     // int [3][HN] owners
-    static constexpr size_t lq = sow + 3 * HN * sizeof(int);                    // uint16 [QCAP]
-    static constexpr size_t lqn = lq + QCAP * sizeof(unsigned short);           // int
+    static constexpr size_t lq = sow + 3 * HN * sizeof(int);                    // uint16 [NT] link nodes
+    static constexpr size_t lpm = lq + NT * sizeof(unsigned short);             // uint32 [NT] link masks
+    static constexpr size_t lqn = lpm + NT * sizeof(uint32_t);                  // int
     static constexpr size_t sty = lqn + 16;                                      // uint8 [3][HN]
     static constexpr size_t bytes = sty + 3 * HN;
 };
@@ -104,92 +104,150 @@ __device__ __noinline__ int wrapped_nbr(int nx, int ny, int nz, int gx, int gy, 
     return x + nx * (y + ny * zz);
 }
 
-// One link of the link pass: node t of the CTA's tile (plane z) to the
-// particle node along c_i.  The node's moments, the ψ ring and the staged
-// populations are still in shared memory, so the node's equilibrium
-// velocity and f*_i are recomputed here.  The population reflected along
-// -c_i gains C = 6 w_i ρ^c u_surf.(-c_i) (Eq. 4), u_surf = V + ω x r_b at
-// the link midpoint r_b = node + c_i/2 - X, and the particle receives
-// (2 f*_i + C) c_i and r_b x that (Eq. 5), in 2^-40 fixed point.
-template <class S>
-__device__ __forceinline__ void link_pass(const Lat &L, const Links &lk, int t, int i, int z, int x0, int y0,
-                                          const typename S::T *fbuf, const float *smo, const float *sps,
-                                          const int *sow, typename S::T *fout, int *tids, unsigned long long *tacc)
+// Add this lane's fixed-point sums v[6] for particle p (or nothing, p < 0)
+// to the CTA table: lanes of the warp with the same particle are combined
+// first (exact integer reductions over 16/16/32-bit limbs), and one lane per
+// particle does the atomics.  Must be called by all 32 lanes.
+__device__ __forceinline__ void warp_add(int p, const unsigned long long v[6], const Links &lk, int *tids,
+                                         unsigned long long *tacc)
 {
-    const int ttx = t % TX, tty = t / TX;
-    const int lx = wrapc(x0 + ttx, L.nx), ly = wrapc(y0 + tty, L.ny);
-    const int nn = lx + L.nx * (ly + L.ny * z);
-    const int ec = (tty + 1) * HX + (ttx + 1);
-    const int sl[3] = {((z + 2) % 3), (z % 3), ((z + 1) % 3)};
-    const int cxi = c_x[i], cyi = c_y[i], czi = c_z[i];
-    const int sli = czi < 0 ? sl[0] : (czi == 0 ? sl[1] : sl[2]);
-    const int p = sow[sli * HN + ec + cyi * HX + cxi];
-    // the node's equilibrium velocity (as in the collision)
-    const int par = z & 1;
-    const float *mo = smo + par * 5 * NT + t;
-    const float rho[2] = {mo[0], mo[NT]};
-    const float up[3] = {mo[2 * NT], mo[3 * NT], mo[4 * NT]};
-    float s0x = 0.f, s0y = 0.f, s0z = 0.f, s1x = 0.f, s1y = 0.f, s1z = 0.f;
+    const unsigned grp = __match_any_sync(0xffffffffu, p);
+    const int lane = threadIdx.x & 31;
+    const bool leader = lane == __ffs(grp) - 1;
+    unsigned long long tot[6];
 #pragma unroll
-    for (int j = 1; j < Q; j++) {
-        const float *pp = sps + sl[cz(j) + 1] * 2 * HN + ec + cy(j) * HX + cx(j);
-        const float p0 = pp[0], p1 = pp[HN];
-        if (cx(j)) { s0x += cx(j) * p1; s1x += cx(j) * p0; }
-        if (cy(j)) { s0y += cy(j) * p1; s1y += cy(j) * p0; }
-        if (cz(j)) { s0z += cz(j) * p1; s1z += cz(j) * p0; }
+    for (int k = 0; k < 6; k++) {
+        const unsigned lo = (unsigned)v[k], hi = (unsigned)(v[k] >> 32);
+        const unsigned s0 = __reduce_add_sync(grp, lo & 0xffffu);
+        const unsigned s1 = __reduce_add_sync(grp, lo >> 16);
+        const unsigned s2 = __reduce_add_sync(grp, hi);
+        tot[k] = ((unsigned long long)s2 << 32) + ((unsigned long long)s1 << 16) + (unsigned long long)s0;
     }
-    const float pc0 = sps[sl[1] * 2 * HN + ec], pc1 = sps[sl[1] * 2 * HN + HN + ec];
-    const float4 X = lk.X32[p], V = lk.K32[2 * p], W = lk.K32[2 * p + 1];
-    float rx = (float)lx - X.x, ry = (float)ly - X.y, rz = (float)z - X.z;
-    if (rx > 0.5f * L.nx) rx -= L.nx;
-    if (rx < -0.5f * L.nx) rx += L.nx;
-    if (ry > 0.5f * L.ny) ry -= L.ny;
-    if (ry < -0.5f * L.ny) ry += L.ny;
-    if (!L.walls) {
-        if (rz > 0.5f * L.nz) rz -= L.nz;
-        if (rz < -0.5f * L.nz) rz += L.nz;
-    }
-    rx += 0.5f * cxi;
-    ry += 0.5f * cyi;
-    rz += 0.5f * czi;
-    const float usx = V.x + W.y * rz - W.z * ry, usy = V.y + W.z * rx - W.x * rz, usz = V.z + W.x * ry - W.y * rx;
-    const float uci = usx * cxi + usy * cyi + usz * czi;
-    const bool axis = i < 7;
-    const float w = axis ? 1.f / 18.f : 1.f / 36.f;
-    const int io = (i & 1) ? i + 1 : i - 1;
-    const typename S::T *fbt = fbuf + par * 2 * Q * NT + t;
-    float a = 0.f;
-#pragma unroll
-    for (int c = 0; c < 2; c++) {
-        const float r = rho[c];
-        const float pcc = c ? pc1 : pc0;
-        const float sx = c ? s1x : s0x, sy = c ? s1y : s0y, sz = c ? s1z : s0z;
-        const float ir = r > 0.f ? L.tau[c] / r : 0.f;
-        const float ux = up[0] + ir * (-L.g * pcc * sx + r * L.body[0]);
-        const float uy = up[1] + ir * (-L.g * pcc * sy + r * L.body[1]);
-        const float uz = up[2] + ir * (-L.g * pcc * sz + r * L.body[2]);
-        const float uu15 = 1.f - 1.5f * (ux * ux + uy * uy + uz * uz);
-        const float cu = cxi * ux + cyi * uy + czi * uz;
-        const float wr = w * r;
-        const float feq = wr * (uu15 + 4.5f * cu * cu) + 3.f * wr * cu;
-        const float base = axis ? L.base[c][1] : L.base[c][7];
-        const float fi = S::cvt(fbt[(c * Q + i) * NT], base);
-        const float fs = fi - (fi - feq) * L.itau[c];
-        const float C = -6.f * wr * uci;
-        S::st(fout + nn + (long long)(c * Q + io) * L.S, fs + C, base);
-        a += 2.f * fs + C;
-    }
-    const float Fx = a * cxi, Fy = a * cyi, Fz = a * czi;
-    const float vv[6] = {Fx, Fy, Fz, ry * Fz - rz * Fy, rz * Fx - rx * Fz, rx * Fy - ry * Fx};
+    if (p < 0 || !leader) return;
     const int h = tab_slot(tids, p);
 #pragma unroll
     for (int k = 0; k < 6; k++) {
-        const unsigned long long qv = to_fixed(vv[k]);
         if (h >= 0)
-            atomicAdd(&tacc[k * TAB + h], qv);
+            atomicAdd(&tacc[k * TAB + h], tot[k]);
         else
-            atomicAdd(&lk.fix[6 * p + k], qv);
+            atomicAdd(&lk.fix[6 * p + k], tot[k]);
     }
+}
+
+// All particle links of node t of the CTA's tile (plane z); t < 0: no node
+// (the lane still takes part in the warp reductions).  The node's moments,
+// the ψ ring and the staged populations are still in shared memory, so its
+// equilibrium velocity and the post-collision populations f*_i are
+// recomputed here.  The population reflected along -c_i gains
+// C = 6 w_i ρ^c u_surf.(-c_i) (Eq. 4), u_surf = V + ω x r_b at the link
+// midpoint r_b = node + c_i/2 - X, and the particle receives (2 f*_i + C) c_i
+// and r_b x that (Eq. 5), summed in 2^-40 fixed point.
+template <class S>
+__device__ __forceinline__ void link_node(const Lat &L, const Links &lk, int t, uint32_t pm, int z, int x0, int y0,
+                                          const typename S::T *fbuf, const float *smo, const float *sps,
+                                          const int *sow, typename S::T *fout, int *tids, unsigned long long *tacc)
+{
+    unsigned long long acc[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+    int pcur = -1;
+    const int tt = t < 0 ? 0 : t;
+    const int ttx = tt % TX, tty = tt / TX;
+    const int lx = wrapc(x0 + ttx, L.nx), ly = wrapc(y0 + tty, L.ny);
+    const int nn = lx + L.nx * (ly + L.ny * z);
+    const int ec = (tty + 1) * HX + (ttx + 1);
+    const int sl0 = (z + 2) % 3, sl1 = z % 3, sl2 = (z + 1) % 3;
+    const int par = z & 1;
+    float ue[2][3], uu[2], rho[2];
+    float4 X = make_float4(0.f, 0.f, 0.f, 0.f), V = X, W = X;
+    if (pm) {
+        // the node's equilibrium velocity, as in the collision
+        const float *mo = smo + par * 5 * NT + tt;
+        rho[0] = mo[0];
+        rho[1] = mo[NT];
+        const float up[3] = {mo[2 * NT], mo[3 * NT], mo[4 * NT]};
+        float s[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+        for (int j = 1; j < Q; j++) {
+            const int slj = cz(j) < 0 ? sl0 : (cz(j) == 0 ? sl1 : sl2);
+            const float *pp = sps + slj * 2 * HN + ec + cy(j) * HX + cx(j);
+            const float p0 = pp[0], p1 = pp[HN];
+            if (cx(j)) { s[0][0] += cx(j) * p1; s[1][0] += cx(j) * p0; }
+            if (cy(j)) { s[0][1] += cy(j) * p1; s[1][1] += cy(j) * p0; }
+            if (cz(j)) { s[0][2] += cz(j) * p1; s[1][2] += cz(j) * p0; }
+        }
+        const float pc[2] = {sps[sl1 * 2 * HN + ec], sps[sl1 * 2 * HN + HN + ec]};
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            const float r = rho[c];
+            const float ir = r > 0.f ? L.tau[c] / r : 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; k++) ue[c][k] = up[k] + ir * (-L.g * pc[c] * s[c][k] + r * L.body[k]);
+            uu[c] = 1.f - 1.5f * (ue[c][0] * ue[c][0] + ue[c][1] * ue[c][1] + ue[c][2] * ue[c][2]);
+        }
+    }
+    const typename S::T *fbt = fbuf + par * 2 * Q * NT + tt;
+    while (pm) {
+        const int i = __ffs(pm) - 1;
+        pm &= pm - 1;
+        const int cxi = c_x[i], cyi = c_y[i], czi = c_z[i];
+        const int sli = czi < 0 ? sl0 : (czi == 0 ? sl1 : sl2);
+        const int p = sow[sli * HN + ec + cyi * HX + cxi];
+        if (p != pcur) {
+            if (pcur >= 0) {  // a second particle at this node: add the first directly
+                const int h = tab_slot(tids, pcur);
+#pragma unroll
+                for (int k = 0; k < 6; k++) {
+                    if (h >= 0)
+                        atomicAdd(&tacc[k * TAB + h], acc[k]);
+                    else
+                        atomicAdd(&lk.fix[6 * pcur + k], acc[k]);
+                    acc[k] = 0ull;
+                }
+            }
+            pcur = p;
+            X = lk.X32[p];
+            V = lk.K32[2 * p];
+            W = lk.K32[2 * p + 1];
+        }
+        float rx = (float)lx - X.x, ry = (float)ly - X.y, rz = (float)z - X.z;
+        if (rx > 0.5f * L.nx) rx -= L.nx;
+        if (rx < -0.5f * L.nx) rx += L.nx;
+        if (ry > 0.5f * L.ny) ry -= L.ny;
+        if (ry < -0.5f * L.ny) ry += L.ny;
+        if (!L.walls) {
+            if (rz > 0.5f * L.nz) rz -= L.nz;
+            if (rz < -0.5f * L.nz) rz += L.nz;
+        }
+        rx += 0.5f * cxi;
+        ry += 0.5f * cyi;
+        rz += 0.5f * czi;
+        const float usx = V.x + W.y * rz - W.z * ry, usy = V.y + W.z * rx - W.x * rz, usz = V.z + W.x * ry - W.y * rx;
+        const float uci = usx * cxi + usy * cyi + usz * czi;
+        const bool axis = i < 7;
+        const float w = axis ? 1.f / 18.f : 1.f / 36.f;
+        const int io = (i & 1) ? i + 1 : i - 1;
+        float a = 0.f;
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            const float r = rho[c];
+            const float cu = cxi * ue[c][0] + cyi * ue[c][1] + czi * ue[c][2];
+            const float wr = w * r;
+            const float feq = wr * (uu[c] + 4.5f * cu * cu) + 3.f * wr * cu;
+            const float base = axis ? L.base[c][1] : L.base[c][7];
+            const float fi = S::cvt(fbt[(c * Q + i) * NT], base);
+            const float fs = fi - (fi - feq) * L.itau[c];
+            const float C = -6.f * wr * uci;
+            S::st(fout + nn + (long long)(c * Q + io) * L.S, fs + C, base);
+            a += 2.f * fs + C;
+        }
+        const float Fx = a * cxi, Fy = a * cyi, Fz = a * czi;
+        acc[0] += to_fixed(Fx);
+        acc[1] += to_fixed(Fy);
+        acc[2] += to_fixed(Fz);
+        acc[3] += to_fixed(ry * Fz - rz * Fy);
+        acc[4] += to_fixed(rz * Fx - rx * Fz);
+        acc[5] += to_fixed(rx * Fy - ry * Fx);
+    }
+    warp_add(pcur, acc, lk, tids, tacc);
 }
 
 // Offsets of the population arrays, per lattice, passed with the launch:
@@ -217,6 +275,7 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
     int *tids = reinterpret_cast<int *>(smem + Smem<S>::tid_);      // [TAB]
     int *sow = reinterpret_cast<int *>(smem + Smem<S>::sow);        // [slot][e] particle owners
     unsigned short *lq = reinterpret_cast<unsigned short *>(smem + Smem<S>::lq);  // link queue
+    uint32_t *lpm = reinterpret_cast<uint32_t *>(smem + Smem<S>::lpm);  // link mask per node
     int *lqn = reinterpret_cast<int *>(smem + Smem<S>::lqn);        // queue length
     if (threadIdx.x == 0) *lqn = 0;
     for (int e = threadIdx.x; e < TAB; e += NT) {
@@ -359,18 +418,6 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
     load_plane(zb, true);
     const bool xy_inner = gx >= 1 && gx <= L.nx - 2 && gy >= 1 && gy <= L.ny - 2;
     for (int z = zb; z < ze; z++) {
-        uint32_t my_part = 0;  // this node's particle links and their queue position
-        int my_at = 0;
-        auto enqueue = [&](int r0) {
-            uint32_t pm = my_part;
-            int at = my_at;
-            while (pm) {
-                const int i = __ffs(pm) - 1;
-                pm &= pm - 1;
-                if (at >= r0 && at < r0 + QCAP) lq[at - r0] = (unsigned short)(tid | (i << 8));
-                at++;
-            }
-        };
         load_plane(z + 1, z + 1 < ze);
         __syncthreads();
         // ring slots of planes z-1, z, z+1
@@ -402,8 +449,8 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
             T *dst = fout + n;
             // store of the post-collision population fs of direction i:
             // streamed to the neighbour, or reflected into slot opp(i) of
-            // this node; reflections off particle nodes are queued for the
-            // link pass after the plane (moving bounce-back, momentum exchange)
+            // this node; reflections off particle nodes are left to the link
+            // pass after the plane (moving bounce-back, momentum exchange)
             auto put = [&](int c, int i, float fs, float r) {
                 const int ci = c * Q + i;
                 if (!(solid & (1u << i))) {
@@ -442,27 +489,20 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
                 S::st(dst + ofs.pop[c * Q], f0 - (f0 - (r - seq)) * it, L.base[c][0]);
             }
             if (part) {
-                // queue this node's particle links: (node, direction) in 16 bits
-                my_part = part;
-                my_at = atomicAdd(lqn, __popc(part));
-                enqueue(0);
+                // queue this node for the link pass
+                lpm[tid] = part;
+                lq[atomicAdd(lqn, 1)] = (unsigned short)tid;
             }
         }
         __syncthreads();
-        // Link pass: every thread takes queued links (in rounds of QCAP).
-        const int total = *lqn;
-        for (int r0 = 0; r0 < total; r0 += QCAP) {
-            if (r0 > 0) {
-                enqueue(r0);
-                __syncthreads();
-            }
-            const int nq = min(total - r0, QCAP);
-            for (int qi = tid; qi < nq; qi += NT) {
-                const int ent = lq[qi];
-                link_pass<S>(L, lk, ent & 255, ent >> 8, z, x0, y0, fbuf, smo, sps, sow, fout, tids, tacc);
-            }
-            __syncthreads();
+        // Link pass: every thread takes one queued node and all its links.
+        const int nq = *lqn;
+        for (int q0 = 0; q0 < nq; q0 += NT) {
+            const int qi = q0 + tid;
+            const int t = qi < nq ? lq[qi] : -1;
+            link_node<S>(L, lk, t, t >= 0 ? lpm[t] : 0u, z, x0, y0, fbuf, smo, sps, sow, fout, tids, tacc);
         }
+        __syncthreads();
         if (tid == 0) *lqn = 0;
     }
     // flush the per-particle link sums of this CTA
