@@ -495,14 +495,16 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
             }
         }
         __syncthreads();
-        // Link pass: every thread takes one queued node and all its links.
+        // Link pass: every thread takes one queued node and all its links;
+        // consecutive queue entries go to different warps, so that the
+        // work spreads over the whole CTA.
         const int nq = *lqn;
-        for (int q0 = 0; q0 < nq; q0 += NT) {
-            const int qi = q0 + tid;
+        if (nq > 0) {
+            const int qi = (tid & 31) * (NT / 32) + (tid >> 5);
             const int t = qi < nq ? lq[qi] : -1;
             link_node<S>(L, lk, t, t >= 0 ? lpm[t] : 0u, z, x0, y0, fbuf, smo, sps, sow, fout, tids, tacc);
+            __syncthreads();
         }
-        __syncthreads();
         if (tid == 0) *lqn = 0;
     }
     // flush the per-particle link sums of this CTA
