@@ -1,0 +1,108 @@
+"""Parity at the full benchmark size, in the launch configuration bench.py
+times: the 512^3 Pickering emulsion (25,033 prolate ellipsoids), one step.
+
+The oracle cannot run 512^3, so it checks sampled outputs: for a few
+particles it runs a 71^3 periodic window of the same seeded input centred on
+the particle, holding every particle whose centre lies in the window.  After
+one step a node depends only on nodes within two lattice spacings; a particle
+that reaches the window's core (within 10 nodes of the centre) has its centre
+within 18 of it, and all its pair partners (reach 2 r_par + Δc < 17) lie
+within 35, inside the window; a particle cut by the window edge reaches at
+most r_par = 8 into it.  So the central particle's force and torque and the
+node types and densities of the core are exact samples of the full-size
+step."""
+import numpy as np
+import pytest
+
+from oracle import lbref
+from paper_1109_3277_gb300 import lbe
+from paper_1109_3277_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+WIN = 71
+CORE = 10
+
+
+@pytest.fixture(scope="module")
+def pickering():
+    return W.pickering(n=512)
+
+
+def _window(w, centre):
+    """Window origin, densities and the particles (global order) whose centre
+    lies inside the window, in window coordinates."""
+    n = w.shape[0]
+    o = np.floor(centre).astype(int) - WIN // 2
+    idx = [(o[k] + np.arange(WIN)) % n for k in range(3)]
+    rho = w.rho0[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]]
+    rel = (w.particles["pos"] - o) % n
+    inside = np.all(rel < WIN, axis=1)
+    sel = np.nonzero(inside)[0]
+    return o, rho, sel, rel[sel]
+
+
+def _run(pickering, storage):
+    w = pickering
+    g = lbe.Lattice(w.shape, w.rho0, storage=storage, **w.params)
+    p = w.particles
+    g.add_particles(p["pos"], p["quat"], p["r_par"], p["r_perp"], p["delta_rho"])
+    g.step(1)
+    rho, _, typ = g.read_fields(vel=False)
+    part = g.read_particles()
+    g.close()
+    return rho, typ, part
+
+
+@pytest.mark.parametrize("storage,tol_rho,tol_f", [("f32", 1e-5, 1e-5), ("f16", 2e-4, 5e-3)])
+def test_fullsize_one_step_sampled(pickering, storage, tol_rho, tol_f):
+    w = pickering
+    rho_g, typ_g, part_g = _run(w, storage)
+    n = w.shape[0]
+    rng = np.random.default_rng(5)
+    samples = rng.choice(len(w.particles["pos"]), size=3, replace=False)
+    for s in samples:
+        centre = w.particles["pos"][s]
+        o, rho0, sel, rel = _window(w, centre)
+        r = lbref.Lattice((WIN, WIN, WIN), rho0, **w.params)
+        p = w.particles
+        r.add_particles(rel, p["quat"][sel], p["r_par"][sel], p["r_perp"][sel], p["delta_rho"][sel])
+        r.step(1)
+        rho_r, _, typ_r = r.read_fields()
+        pr = r.read_particles()
+        k = int(np.nonzero(sel == s)[0][0])
+        # the sampled particle: force and torque of the first update
+        scale = max(1.0, np.abs(pr["force"][k]).max())
+        assert np.max(np.abs(part_g["force"][s] - pr["force"][k])) < tol_f * scale
+        tscale = max(1.0, np.abs(pr["torque"][k]).max())
+        assert np.max(np.abs(part_g["torque"][s] - pr["torque"][k])) < tol_f * tscale
+        assert np.max(np.abs(part_g["pos"][s] - ((pr["pos"][k] + o) % n))) < 1e-6
+        # densities and node types of the core
+        c0 = WIN // 2 - CORE
+        sl = slice(c0, c0 + 2 * CORE + 1)
+        idx = [(o[kk] + np.arange(WIN))[sl] % n for kk in range(3)]
+        core_g = rho_g[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]]
+        core_t = typ_g[idx[2]][:, idx[1]][:, :, idx[0]]
+        assert np.array_equal(core_t, typ_r[sl, sl, sl])
+        both = (core_t == 0) & (typ_r[sl, sl, sl] == 0)
+        assert np.max(np.abs(core_g - rho_r[:, sl, sl, sl])[:, both]) < tol_rho
+
+
+def test_fullsize_mass_and_types(pickering):
+    """Properties at any size: all 25,033 particles are placed (their node
+    count is that of the oracle's coverage rule, checked on a window above),
+    and the fluid mass changes only by what the moving boundaries create or
+    remove, a few parts in 10^6 over a few steps."""
+    w = pickering
+    g = lbe.Lattice(w.shape, w.rho0, storage="f32", **w.params)
+    p = w.particles
+    g.add_particles(p["pos"], p["quat"], p["r_par"], p["r_perp"], p["delta_rho"])
+    _, _, typ = g.read_fields(rho=False, vel=False)
+    solid = int((typ == 2).sum())
+    vol = 4 / 3 * np.pi * 8 * 4 * 4 * len(p["pos"])
+    assert abs(solid - vol) < 0.05 * vol
+    m0 = g.mass()
+    g.step(4)
+    m1 = g.mass()
+    assert np.all(np.abs(m1 - m0) / m0 < 1e-5)
+    g.close()
