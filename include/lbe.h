@@ -182,6 +182,34 @@ LBE_API lbe_status lbe_mass_noalloc(const void *f, int32_t storage, const uint8_
                                     int64_t nodes, int64_t slot_stride, const double rho_ref[2],
                                     int32_t device, void *cuda_stream, double *out);
 
+/* Pick the fused kernel's z-chunk length for this lattice by timing the
+ * candidates with CUDA events on the current state (which is not changed);
+ * later steps use the fastest.  *chosen_zc (may be NULL) receives it. */
+LBE_API lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc);
+
+/* Batches: several lattices stepped together, every kernel of the step
+ * covering all of them in one launch (the fused fluid kernel as a persistent
+ * kernel taking tiles of all boxes from one queue), replayed as a captured
+ * CUDA graph on a stream of the batch's own, ordered by events after the
+ * members' earlier work and before their later work.  Members must share
+ * device and storage mode, must not
+ * use LBE_FLAG_TWO_PASS, and must not change (add particles) while the
+ * batch exists; the batch does not own them.  After lbe_batch_step the
+ * members are read with the usual calls.  Every member's populations and
+ * particles are bit-identical to those of stepping it alone with lbe_step,
+ * whatever else is in the batch.  The pair forces run one thread per
+ * particle over the member's particles, so members are limited to
+ * LBE_BATCH_MAX_PARTICLES particles each (LBE_EINVAL beyond). */
+#define LBE_BATCH_MAX_PARTICLES 4096
+typedef struct lbe_batch lbe_batch;
+LBE_API lbe_status lbe_batch_create(lbe_ctx *const *members, int32_t n, lbe_batch **out);
+LBE_API lbe_status lbe_batch_step(lbe_batch *b, int32_t nsteps);
+/* Pick the persistent CTAs per SM of the batched fused kernel by timing. */
+LBE_API lbe_status lbe_batch_autotune(lbe_batch *b, int32_t *chosen_ctas_per_sm);
+/* Kernels of this library one batched step launches (0 if b is NULL). */
+LBE_API int32_t lbe_batch_kernels_per_step(const lbe_batch *b);
+LBE_API void lbe_batch_destroy(lbe_batch *b);
+
 LBE_API const char *lbe_last_error(const lbe_ctx *c);
 LBE_API void lbe_destroy(lbe_ctx *c);
 

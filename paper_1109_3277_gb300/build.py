@@ -18,6 +18,12 @@ SOURCES = ["lbe_api.cu", "fluid.cu", "fused.cu", "particles.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]
+# The particle kernels compile without multiply-add contraction: the bodies
+# they share between single-lattice and batched kernels (Newton-Euler update,
+# coverage, fill and empty, pair terms) then round every operation the same
+# way wherever they are inlined.  Where a fused multiply-add is wanted there
+# (the pair prefilter), it is written as an intrinsic.
+FILE_FLAGS = {"particles.cu": ["--fmad=false"]}
 
 
 def nvcc():
@@ -55,7 +61,7 @@ def build(force=False, verbose=False, extra=(), check=False):
 
     def compile_one(src):
         obj = os.path.join(bdir, src.replace(".cu", ".o"))
-        cmd = [nv, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nv, *ARCH, *FLAGS, *FILE_FLAGS.get(src, []), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

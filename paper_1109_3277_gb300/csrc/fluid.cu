@@ -138,11 +138,11 @@ __device__ __forceinline__ int site_nb(const Lat &L, const Site &s, int i)
 }
 
 template <class S>
-__global__ void __launch_bounds__(128) k_bnd_rho(Lat L, const typename S::T *__restrict__ f,
-                                                 const uint8_t *__restrict__ type, float *__restrict__ rho)
+__device__ __forceinline__ void bnd_rho_node(const Lat &L, const typename S::T *__restrict__ f,
+                                             const uint8_t *__restrict__ type, float *__restrict__ rho,
+                                             const Site &s)
 {
-    Site s;
-    if (!site_of(L, s) || type[s.n] != FLUID) return;
+    if (type[s.n] != FLUID) return;
     bool bnd = false;
 #pragma unroll
     for (int i = 1; i < Q; i++) {
@@ -159,19 +159,50 @@ __global__ void __launch_bounds__(128) k_bnd_rho(Lat L, const typename S::T *__r
     }
 }
 
+template <class S>
+__global__ void __launch_bounds__(128) k_bnd_rho(Lat L, const typename S::T *__restrict__ f,
+                                                 const uint8_t *__restrict__ type, float *__restrict__ rho)
+{
+    Site s;
+    if (!site_of(L, s)) return;
+    bnd_rho_node<S>(L, f, type, rho, s);
+}
+
+// Node g of a batch (all boxes' nodes in box order) as a site of its box.
+__device__ __forceinline__ const BoxDev &batch_site(const BatchIndex &B, int g, Site &s)
+{
+    const int b = find_box(B.node0, B.nbox, g);
+    const BoxDev &bx = B.box[b];
+    const int n = g - B.node0[b];
+    s.n = n;
+    s.x = n % bx.L.nx;
+    const int t = n / bx.L.nx;
+    s.y = t % bx.L.ny;
+    s.z = t / bx.L.ny;
+    s.inner = s.x >= 1 && s.x <= bx.L.nx - 2 && s.y >= 1 && s.y <= bx.L.ny - 2 && s.z >= 1 && s.z <= bx.L.nz - 2;
+    return bx;
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_bnd_rho_batch(BatchIndex B, int total)
+{
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+        Site s;
+        const BoxDev &bx = batch_site(B, g, s);
+        const int b = find_box(B.node0, B.nbox, g);
+        bnd_rho_node<S>(bx.L, (const typename S::T *)bx.f[B.par[2 * b]], bx.type, bx.rho, s);
+    }
+}
+
 // ---------------------------------------------------------- shell fill
 // Solid nodes with at least one fluid neighbour take the mean ρ^c of those
 // neighbours (Eq. 10); the colour Δρ of the owning particle is added to red
 // if positive, else |Δρ| to blue.  Walls take Δρ = 0.
 
-__global__ void __launch_bounds__(128) k_shell(Lat L, const float *__restrict__ rho,
-                                               float *__restrict__ psi,
-                                               const uint8_t *__restrict__ type,
-                                               const uint32_t *__restrict__ owner,
-                                               const double *__restrict__ drho)
+__device__ __forceinline__ void shell_node(const Lat &L, const float *__restrict__ rho, float *__restrict__ psi,
+                                           const uint8_t *__restrict__ type, const uint32_t *__restrict__ owner,
+                                           const double *__restrict__ drho, const Site &s)
 {
-    Site s;
-    if (!site_of(L, s)) return;
     const int n = s.n;
     uint8_t t = type[n];
     if (t == FLUID) return;
@@ -198,6 +229,27 @@ __global__ void __launch_bounds__(128) k_shell(Lat L, const float *__restrict__ 
         r1 += fabsf(dr);
     psi[n] = 1.f - expf(-r0);
     psi[(size_t)L.N + n] = 1.f - expf(-r1);
+}
+
+__global__ void __launch_bounds__(128) k_shell(Lat L, const float *__restrict__ rho,
+                                               float *__restrict__ psi,
+                                               const uint8_t *__restrict__ type,
+                                               const uint32_t *__restrict__ owner,
+                                               const double *__restrict__ drho)
+{
+    Site s;
+    if (!site_of(L, s)) return;
+    shell_node(L, rho, psi, type, owner, drho, s);
+}
+
+__global__ void __launch_bounds__(256) k_shell_batch(BatchIndex B, int total)
+{
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+        Site s;
+        const BoxDev &bx = batch_site(B, g, s);
+        const int b = find_box(B.node0, B.nbox, g);
+        shell_node(bx.L, bx.rho, bx.psi, bx.type, bx.owner[B.par[2 * b + 1]], bx.P.drho, s);
+    }
 }
 
 // ------------------------------------------------------ collide + stream
@@ -466,6 +518,22 @@ void launch_bnd_rho(int storage, const Lat &L, const void *f, const uint8_t *typ
 {
     dim3 grid((L.nx + 127) / 128, L.ny, L.nz);
     LBE_DISPATCH(storage, (k_bnd_rho<S><<<grid, 128, 0, s>>>(L, (const typename S::T *)f, type, rho)));
+}
+
+static unsigned batch_grid(int total)
+{
+    unsigned g = (unsigned)((total + 255) / 256);
+    return g > 8 * 152 ? 8 * 152 : (g ? g : 1);
+}
+
+void launch_bnd_rho_batch(int storage, const BatchIndex &B, int total_nodes, cudaStream_t s)
+{
+    LBE_DISPATCH(storage, (k_bnd_rho_batch<S><<<batch_grid(total_nodes), 256, 0, s>>>(B, total_nodes)));
+}
+
+void launch_shell_batch(const BatchIndex &B, int total_nodes, cudaStream_t s)
+{
+    k_shell_batch<<<batch_grid(total_nodes), 256, 0, s>>>(B, total_nodes);
 }
 
 void launch_shell(const Lat &L, const float *rho, float *psi, const uint8_t *type,

@@ -67,6 +67,37 @@ struct Smem {
     static constexpr size_t bytes = sty + 3 * HN;
 };
 
+// ---- node arithmetic shared by the collision and the link pass ----------
+// Every product or sum that rounds is written with a round-to-nearest
+// intrinsic (which the compiler never contracts), so that each kernel that
+// inlines these computes the same bits: the single-lattice and the batched
+// fused kernels agree exactly.  Products with the lattice velocities c_i
+// (components 0 or ±1) are exact and stay plain.
+
+// Equilibrium velocity of component c, u' + (τ_c/ρ_c) F^c with the
+// Shan–Chen force F^c = -g ψ^c s^c + ρ^c g_body (Eq. 3), and 1 - 1.5 u·u.
+__device__ __forceinline__ void eq_velocity(const Lat &L, int c, float r, float pc, const float s[3],
+                                            const float up[3], float ue[3], float &uu15)
+{
+    const float ir = r > 0.f ? __fdiv_rn(L.tau[c], r) : 0.f;
+    const float gp = __fmul_rn(-L.g, pc);
+#pragma unroll
+    for (int k = 0; k < 3; k++) ue[k] = __fmaf_rn(ir, __fmaf_rn(gp, s[k], __fmul_rn(r, L.body[k])), up[k]);
+    const float uu = __fmaf_rn(ue[0], ue[0], __fmaf_rn(ue[1], ue[1], __fmul_rn(ue[2], ue[2])));
+    uu15 = __fmaf_rn(-1.5f, uu, 1.f);
+}
+
+// Even and odd parts of f^eq_i = w_i ρ (1 + 3 c·u + 4.5 (c·u)^2 - 1.5 u·u).
+__device__ __forceinline__ void feq_parts(float w, float r, float cu, float uu15, float &even, float &odd)
+{
+    const float wr = __fmul_rn(w, r);
+    even = __fmul_rn(wr, __fmaf_rn(__fmul_rn(4.5f, cu), cu, uu15));
+    odd = __fmul_rn(__fmul_rn(3.f, wr), cu);
+}
+
+// BGK relaxation f + (f^eq - f)/τ.
+__device__ __forceinline__ float relax(float f, float feq, float it) { return __fmaf_rn(__fsub_rn(feq, f), it, f); }
+
 // FP32 value to 64-bit fixed point in units of 2^-40 (two's complement in an
 // unsigned word, so that wrap-around addition is exact); |v| is clamped to
 // 2^22, far beyond any link term.
@@ -176,13 +207,7 @@ __device__ __forceinline__ void link_node(const Lat &L, const Links &lk, int t, 
         }
         const float pc[2] = {sps[sl1 * 2 * HN + ec], sps[sl1 * 2 * HN + HN + ec]};
 #pragma unroll
-        for (int c = 0; c < 2; c++) {
-            const float r = rho[c];
-            const float ir = r > 0.f ? L.tau[c] / r : 0.f;
-#pragma unroll
-            for (int k = 0; k < 3; k++) ue[c][k] = up[k] + ir * (-L.g * pc[c] * s[c][k] + r * L.body[k]);
-            uu[c] = 1.f - 1.5f * (ue[c][0] * ue[c][0] + ue[c][1] * ue[c][1] + ue[c][2] * ue[c][2]);
-        }
+        for (int c = 0; c < 2; c++) eq_velocity(L, c, rho[c], pc[c], s[c], up, ue[c], uu[c]);
     }
     const typename S::T *fbt = fbuf + par * 2 * Q * NT + tt;
     while (pm) {
@@ -220,7 +245,10 @@ __device__ __forceinline__ void link_node(const Lat &L, const Links &lk, int t, 
         rx += 0.5f * cxi;
         ry += 0.5f * cyi;
         rz += 0.5f * czi;
-        const float usx = V.x + W.y * rz - W.z * ry, usy = V.y + W.z * rx - W.x * rz, usz = V.z + W.x * ry - W.y * rx;
+        // surface velocity V + ω × r_b at the link midpoint
+        const float usx = __fsub_rn(__fmaf_rn(W.y, rz, V.x), __fmul_rn(W.z, ry));
+        const float usy = __fsub_rn(__fmaf_rn(W.z, rx, V.y), __fmul_rn(W.x, rz));
+        const float usz = __fsub_rn(__fmaf_rn(W.x, ry, V.z), __fmul_rn(W.y, rx));
         const float uci = usx * cxi + usy * cyi + usz * czi;
         const bool axis = i < 7;
         const float w = axis ? 1.f / 18.f : 1.f / 36.f;
@@ -230,43 +258,34 @@ __device__ __forceinline__ void link_node(const Lat &L, const Links &lk, int t, 
         for (int c = 0; c < 2; c++) {
             const float r = rho[c];
             const float cu = cxi * ue[c][0] + cyi * ue[c][1] + czi * ue[c][2];
-            const float wr = w * r;
-            const float feq = wr * (uu[c] + 4.5f * cu * cu) + 3.f * wr * cu;
+            float even, odd;
+            feq_parts(w, r, cu, uu[c], even, odd);
             const float base = axis ? L.base[c][1] : L.base[c][7];
             const float fi = S::cvt(fbt[(c * Q + i) * NT], base);
-            const float fs = fi - (fi - feq) * L.itau[c];
-            const float C = -6.f * wr * uci;
-            S::st(fout + nn + (long long)(c * Q + io) * L.S, fs + C, base);
-            a += 2.f * fs + C;
+            const float fs = relax(fi, __fadd_rn(even, odd), L.itau[c]);
+            const float C = __fmul_rn(__fmul_rn(-6.f * w, r), uci);
+            S::st(fout + nn + (long long)(c * Q + io) * L.S, __fadd_rn(fs, C), base);
+            a = __fadd_rn(a, __fmaf_rn(2.f, fs, C));
         }
         const float Fx = a * cxi, Fy = a * cyi, Fz = a * czi;
         acc[0] += to_fixed(Fx);
         acc[1] += to_fixed(Fy);
         acc[2] += to_fixed(Fz);
-        acc[3] += to_fixed(ry * Fz - rz * Fy);
-        acc[4] += to_fixed(rz * Fx - rx * Fz);
-        acc[5] += to_fixed(rx * Fy - ry * Fx);
+        acc[3] += to_fixed(__fsub_rn(__fmul_rn(ry, Fz), __fmul_rn(rz, Fy)));
+        acc[4] += to_fixed(__fsub_rn(__fmul_rn(rz, Fx), __fmul_rn(rx, Fz)));
+        acc[5] += to_fixed(__fsub_rn(__fmul_rn(rx, Fy), __fmul_rn(ry, Fx)));
     }
     warp_add(pcur, acc, lk, tids, tacc);
 }
 
-// Offsets of the population arrays, per lattice, passed with the launch:
-// pop[c*Q+i] = (c*Q+i)*S and push[c*Q+i] = pop[c*Q+i] + (cx + cy*nx + cz*nx*ny),
-// so the address of a load or of an interior push is one add.
-struct FusedOfs {
-    long long pop[2 * Q];
-    long long push[2 * Q];
-};
-
+// One tile (column bx, by, z chunk bz) of one lattice.
 template <class S>
-__global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__restrict__ fin,
-                                              typename S::T *__restrict__ fout,
-                                              const float *__restrict__ psi,
-                                              const uint8_t *__restrict__ type, int zc, Links lk,
-                                              FusedOfs ofs)
+__device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__restrict__ fin,
+                                           typename S::T *__restrict__ fout, const float *__restrict__ psi,
+                                           const uint8_t *__restrict__ type, int zc, const Links &lk,
+                                           const FusedOfs &ofs, int bx, int by, int bz, unsigned char *smem)
 {
     using T = typename S::T;
-    extern __shared__ __align__(16) unsigned char smem[];
     T *fbuf = reinterpret_cast<T *>(smem + Smem<S>::fbuf);          // [parity][c*Q+i][tid]
     float *sps = reinterpret_cast<float *>(smem + Smem<S>::sps);    // [slot][c][e]
     float *smo = reinterpret_cast<float *>(smem + Smem<S>::smo);    // [parity][k][tid]
@@ -284,8 +303,8 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
         for (int k = 0; k < 6; k++) tacc[k * TAB + e] = 0ull;
     }
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int zb = blockIdx.z * zc, ze = min(zb + zc, L.nz);
+    const int x0 = bx * TX, y0 = by * TY;
+    const int zb = bz * zc, ze = min(zb + zc, L.nz);
     const int gx = wrapc(x0 + tx, L.nx), gy = wrapc(y0 + ty, L.ny);
     const bool active = (x0 + tx < L.nx) && (y0 + ty < L.ny);
     const int nxy = L.nx * L.ny;
@@ -369,12 +388,14 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
                     p1 = 1.f - expf(-r[1]);
                     if (own_pops) {
                         float *mo = smo + par * 5 * NT + tid;
-                        const float den = r[0] * L.itau[0] + r[1] * L.itau[1];
+                        // shifted velocity u' = Σ_c j^c/τ_c / Σ_c ρ^c/τ_c
+                        const float den = __fmaf_rn(r[1], L.itau[1], __fmul_rn(r[0], L.itau[0]));
                         const float iden = den > 0.f ? 1.f / den : 0.f;
                         mo[0] = r[0];
                         mo[NT] = r[1];
 #pragma unroll
-                        for (int k = 0; k < 3; k++) mo[(2 + k) * NT] = (j[0][k] * L.itau[0] + j[1][k] * L.itau[1]) * iden;
+                        for (int k = 0; k < 3; k++)
+                            mo[(2 + k) * NT] = __fmul_rn(__fmaf_rn(j[1][k], L.itau[1], __fmul_rn(j[0][k], L.itau[0])), iden);
                     }
                 } else {
                     p0 = psi[n];
@@ -463,11 +484,8 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 const float r = rho[c];
-                float ue[3];
-                const float ir = r > 0.f ? L.tau[c] / r : 0.f;
-#pragma unroll
-                for (int k = 0; k < 3; k++) ue[k] = up[k] + ir * (-L.g * pc[c] * s[c][k] + r * L.body[k]);
-                const float uu15 = 1.f - 1.5f * (ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2]);
+                float ue[3], uu15;
+                eq_velocity(L, c, r, pc[c], s[c], up, ue, uu15);
                 const float it = L.itau[c];
 
                 float seq = 0.f;
@@ -475,18 +493,17 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
 #pragma unroll
                 for (int i = 1; i < Q; i += 2) {
                     const float cu = cx(i) * ue[0] + cy(i) * ue[1] + cz(i) * ue[2];
-                    const float wr = wgt(i) * r;
-                    const float even = wr * (uu15 + 4.5f * cu * cu);
-                    const float odd = 3.f * wr * cu;
+                    float even, odd;
+                    feq_parts(wgt(i), r, cu, uu15, even, odd);
                     const float fa = S::cvt(fb[(c * Q + i) * NT], L.base[c][i]);
                     const float fbv = S::cvt(fb[(c * Q + i + 1) * NT], L.base[c][i + 1]);
-                    seq += 2.f * even;
-                    put(c, i, fa - (fa - (even + odd)) * it, r);
-                    put(c, i + 1, fbv - (fbv - (even - odd)) * it, r);
+                    seq = __fadd_rn(seq, 2.f * even);
+                    put(c, i, relax(fa, __fadd_rn(even, odd), it), r);
+                    put(c, i + 1, relax(fbv, __fsub_rn(even, odd), it), r);
                 }
                 // rest population: equilibrium ρ - Σ_{i>0} f^eq_i (exact mass)
                 const float f0 = S::cvt(fb[(c * Q) * NT], L.base[c][0]);
-                S::st(dst + ofs.pop[c * Q], f0 - (f0 - (r - seq)) * it, L.base[c][0]);
+                S::st(dst + ofs.pop[c * Q], relax(f0, __fsub_rn(r, seq), it), L.base[c][0]);
             }
             if (part) {
                 // queue this node for the link pass
@@ -519,6 +536,48 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
     }
 }
 
+template <class S>
+__global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__restrict__ fin,
+                                              typename S::T *__restrict__ fout,
+                                              const float *__restrict__ psi,
+                                              const uint8_t *__restrict__ type, int zc, Links lk,
+                                              FusedOfs ofs)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    fused_tile<S>(L, fin, fout, psi, type, zc, lk, ofs, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+}
+
+// Persistent multi-lattice variant: CTAs take tiles of all boxes of a batch
+// from one queue (largest boxes first in the queue order set by the host).
+template <class S>
+__global__ void __launch_bounds__(NT, 3) k_fused_batch(BatchIndex B, int total)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_tile, s_box;
+    __shared__ __align__(16) BoxDev sb;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_tile = atomicAdd(B.counter, 1);
+            s_box = s_tile < total ? find_box(B.tile0, B.nbox, s_tile) : 0;
+        }
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= total) break;
+        // the box descriptor into shared memory (word copy)
+        const int *src = reinterpret_cast<const int *>(B.box + s_box);
+        int *dstw = reinterpret_cast<int *>(&sb);
+        for (int k = threadIdx.x; k < (int)(sizeof(BoxDev) / 4); k += NT) dstw[k] = src[k];
+        __syncthreads();
+        const int lt = t - B.tile0[s_box];
+        const int bx = lt % sb.ntx, by = (lt / sb.ntx) % sb.nty, bz = lt / (sb.ntx * sb.nty);
+        const int cur = B.par[2 * s_box], ocur = B.par[2 * s_box + 1];
+        Links lk{sb.owner[ocur], sb.P.X32, sb.P.K32, sb.P.fix};
+        fused_tile<S>(sb.L, (const typename S::T *)sb.f[cur], (typename S::T *)sb.f[1 - cur], sb.psi, sb.type, sb.zc,
+                      lk, sb.ofs, bx, by, bz, smem);
+    }
+}
+
 }  // namespace
 
 #define LBE_DISPATCH(storage, CALL)                                   \
@@ -540,17 +599,8 @@ int fused_zchunk(const Lat &L)
     return zc;
 }
 
-template <class S>
-static void launch_fused_t(const Lat &L, const void *fin, void *fout, const float *psi, const uint8_t *type,
-                           const Links &lk, cudaStream_t s)
+FusedOfs fused_offsets(const Lat &L)
 {
-    static bool configured = false;  // the attribute is per function, set once per process
-    if (!configured) {
-        cudaFuncSetAttribute(k_fused<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem<S>::bytes);
-        configured = true;
-    }
-    const int zc = fused_zchunk(L);
-    dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
     FusedOfs ofs;
     for (int c = 0; c < 2; c++)
         for (int i = 0; i < Q; i++) {
@@ -558,14 +608,52 @@ static void launch_fused_t(const Lat &L, const void *fin, void *fout, const floa
             ofs.pop[c * Q + i] = o;
             ofs.push[c * Q + i] = o + cx(i) + (long long)cy(i) * L.nx + (long long)cz(i) * L.nx * L.ny;
         }
+    return ofs;
+}
+
+template <class S>
+static void launch_fused_t(const Lat &L, const void *fin, void *fout, const float *psi, const uint8_t *type,
+                           const Links &lk, cudaStream_t s, int zc_override)
+{
+    static bool configured = false;  // the attribute is per function and process
+    if (!configured) {
+        cudaFuncSetAttribute(k_fused<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem<S>::bytes);
+        configured = true;
+    }
+    const int zc = zc_override > 0 ? zc_override : fused_zchunk(L);
+    dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
+    FusedOfs ofs = fused_offsets(L);
     k_fused<S><<<grid, NT, Smem<S>::bytes, s>>>(L, (const typename S::T *)fin, (typename S::T *)fout, psi, type,
                                                  zc, lk, ofs);
 }
 
 void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
-                  const uint8_t *type, const Links &lk, cudaStream_t s)
+                  const uint8_t *type, const Links &lk, cudaStream_t s, int zc_override)
 {
-    LBE_DISPATCH(storage, (launch_fused_t<S>(L, fin, fout, psi, type, lk, s)));
+    LBE_DISPATCH(storage, (launch_fused_t<S>(L, fin, fout, psi, type, lk, s, zc_override)));
+}
+
+template <class S>
+static void launch_fused_batch_t(const BatchIndex &B, int total, int ctas, cudaStream_t s)
+{
+    static bool configured = false;
+    if (!configured) {
+        cudaFuncSetAttribute(k_fused_batch<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem<S>::bytes);
+        configured = true;
+    }
+    k_fused_batch<S><<<ctas, NT, Smem<S>::bytes, s>>>(B, total);
+}
+
+void launch_fused_batch(int storage, const BatchIndex &B, int total_tiles, int ctas, cudaStream_t s)
+{
+    LBE_DISPATCH(storage, (launch_fused_batch_t<S>(B, total_tiles, ctas, s)));
+}
+
+int fused_batch_ctas_per_sm(int storage)
+{
+    int n = 0;
+    LBE_DISPATCH(storage, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused_batch<S>, NT, Smem<S>::bytes)));
+    return n > 0 ? n : 1;
 }
 
 }  // namespace lbe

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "lbe_internal.cuh"
@@ -34,6 +35,7 @@ struct lbe_ctx {
     Parts P{};
     // graphs keyed by (cur, ocur)
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    int zc_tuned = 0;  // fused-kernel z chunk chosen by lbe_autotune (0: heuristic)
     // profiling
     bool profiling = false;
     std::vector<cudaEvent_t> ev;
@@ -177,7 +179,7 @@ void enqueue_step(lbe_ctx *c)
         launch_collide_stream(st, L, fin, fout, c->psi, c->type, s);
     } else {
         Links lk{c->owner[c->ocur], c->P.X32, c->P.K32, c->P.fix};
-        launch_fused(st, L, fin, fout, c->psi, c->type, lk, s);
+        launch_fused(st, L, fin, fout, c->psi, c->type, lk, s, c->zc_tuned);
     }
     if (c->profiling) {
         cudaEventRecord(c->ev[c->ev_used + 1], s);
@@ -604,6 +606,298 @@ void lbe_destroy(lbe_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_all(c);
     delete c;
+}
+
+lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc)
+{
+    if (!c) return LBE_EINVAL;
+    cudaSetDevice(c->device);
+    lbe_status st = sync(c, "autotune");
+    if (st != LBE_OK) return st;
+    if (c->d.flags & LBE_FLAG_TWO_PASS) {
+        if (chosen_zc) *chosen_zc = 0;
+        return LBE_OK;
+    }
+    // Candidates for the z chunk of the fused kernel.  Each runs from the
+    // current populations into the spare buffer, which the next step
+    // overwrites anyway, so the state is not changed (the link sums it
+    // accumulates are cleared afterwards).
+    const Lat &L = c->L;
+    std::vector<int> cand;
+    for (int zc = 4; zc < L.nz; zc *= 2) cand.push_back(zc);
+    cand.push_back(L.nz);
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    void *fin = c->f[c->cur], *fout = c->f[1 - c->cur];
+    Links lk{c->owner[c->ocur], c->P.X32, c->P.K32, c->P.fix};
+    launch_bnd_rho(c->d.storage, L, fin, c->type, c->rho, c->stream);
+    launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, c->stream);
+    float best = 1e30f;
+    int best_zc = fused_zchunk(L);
+    for (int zc : cand) {
+        launch_fused(c->d.storage, L, fin, fout, c->psi, c->type, lk, c->stream, zc);  // warm-up
+        cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 3; r++) launch_fused(c->d.storage, L, fin, fout, c->psi, c->type, lk, c->stream, zc);
+        cudaEventRecord(e1, c->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_zc = zc;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (c->np > 0) CK(c, cudaMemsetAsync(c->P.fix, 0, (size_t)6 * c->np * sizeof(unsigned long long), c->stream));
+    c->zc_tuned = best_zc;
+    drop_graphs(c);
+    if (chosen_zc) *chosen_zc = best_zc;
+    return sync(c, "autotune");
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------- batches
+
+struct lbe_batch {
+    std::vector<lbe_ctx *> members;   // in table order (largest box first)
+    int device = 0, storage = 0;
+    cudaStream_t stream = nullptr;    // the batch's own stream
+    cudaEvent_t done = nullptr;       // end of the last batched launch
+    std::vector<cudaEvent_t> mev;     // per member: its stream's last work
+    BoxDev *d_box = nullptr;
+    int *d_idx = nullptr;             // tile0 | node0 | part0 | par | counter
+    BatchIndex idx{};
+    int total_tiles = 0, total_nodes = 0, total_parts = 0;
+    int ctas_per_sm = 0;
+    cudaGraphExec_t graph = nullptr;
+    std::string err;
+};
+
+namespace {
+
+void batch_enqueue_step(lbe_batch *b)
+{
+    cudaStream_t s = b->stream;
+    launch_bnd_rho_batch(b->storage, b->idx, b->total_nodes, s);
+    launch_shell_batch(b->idx, b->total_nodes, s);
+    cudaMemsetAsync(b->idx.counter, 0, sizeof(int), s);
+    launch_fused_batch(b->storage, b->idx, b->total_tiles, 152 * b->ctas_per_sm, s);
+    if (b->total_parts > 0) {
+        launch_pairs_batch(b->idx, b->total_parts, s);
+        launch_integrate_batch(b->idx, b->total_parts, s);
+        launch_claim_batch(b->idx, b->total_parts, s);
+        launch_transition_batch(b->storage, b->idx, b->total_parts, s);
+        launch_reset_batch(b->idx, b->total_parts, s);
+    }
+    launch_flip_batch(b->idx, s);
+}
+
+void batch_free(lbe_batch *b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaEvent_t e : b->mev) cudaEventDestroy(e);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    cudaFree(b->d_box);
+    cudaFree(b->d_idx);
+}
+
+}  // namespace
+
+extern "C" {
+
+lbe_status lbe_batch_create(lbe_ctx *const *members, int32_t n, lbe_batch **out)
+{
+    if (!members || n < 1 || !out) return LBE_EINVAL;
+    *out = nullptr;
+    lbe_ctx *m0 = members[0];
+    if (!m0) return LBE_EINVAL;
+    for (int k = 0; k < n; k++) {
+        lbe_ctx *c = members[k];
+        if (!c || c->device != m0->device || c->d.storage != m0->d.storage) return LBE_EINVAL;
+        if (c->d.flags & LBE_FLAG_TWO_PASS) return LBE_EINVAL;
+        if (c->np > LBE_BATCH_MAX_PARTICLES) return LBE_EINVAL;
+        for (int j = 0; j < k; j++)
+            if (members[j] == c) return LBE_EINVAL;
+    }
+    lbe_batch *b = new (std::nothrow) lbe_batch();
+    if (!b) return LBE_ENOMEM;
+    b->device = m0->device;
+    b->storage = m0->d.storage;
+    cudaSetDevice(b->device);
+    for (int k = 0; k < n; k++) {
+        if (cudaStreamSynchronize(members[k]->stream) != cudaSuccess) {
+            delete b;
+            return LBE_ECUDA;
+        }
+        b->members.push_back(members[k]);
+    }
+    {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+        for (int k = 0; e == cudaSuccess && k < n; k++) {
+            cudaEvent_t ev;
+            e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) b->mev.push_back(ev);
+        }
+        if (e != cudaSuccess) {
+            batch_free(b);
+            delete b;
+            return LBE_ECUDA;
+        }
+    }
+    // largest boxes first, so that the persistent fused kernel starts on them
+    std::stable_sort(b->members.begin(), b->members.end(),
+                     [](const lbe_ctx *x, const lbe_ctx *y) { return x->L.N > y->L.N; });
+    std::vector<BoxDev> box(n);
+    std::vector<int> idx(3 * (n + 1) + 2 * n + 1, 0);
+    int *tile0 = idx.data(), *node0 = tile0 + (n + 1), *part0 = node0 + (n + 1), *par = part0 + (n + 1);
+    for (int k = 0; k < n; k++) {
+        lbe_ctx *c = b->members[k];
+        BoxDev &d = box[k];
+        d.L = c->L;
+        d.ofs = fused_offsets(c->L);
+        d.f[0] = c->f[0];
+        d.f[1] = c->f[1];
+        d.rho = c->rho;
+        d.psi = c->psi;
+        d.type = c->type;
+        d.owner[0] = c->owner[0];
+        d.owner[1] = c->owner[1];
+        d.P = c->P;
+        d.P.n = c->np;
+        d.pair = c->pair;
+        d.mode = c->d.particle_mode;
+        d.zc = c->zc_tuned > 0 ? c->zc_tuned : fused_zchunk(c->L);
+        d.ntx = (c->L.nx + FUSED_TX - 1) / FUSED_TX;
+        d.nty = (c->L.ny + FUSED_TY - 1) / FUSED_TY;
+        d.nzc = (c->L.nz + d.zc - 1) / d.zc;
+        tile0[k + 1] = tile0[k] + d.ntx * d.nty * d.nzc;
+        node0[k + 1] = node0[k] + c->L.N;
+        part0[k + 1] = part0[k] + c->np;
+        par[2 * k] = c->cur;
+        par[2 * k + 1] = c->ocur;
+    }
+    b->total_tiles = tile0[n];
+    b->total_nodes = node0[n];
+    b->total_parts = part0[n];
+    cudaError_t e = cudaMalloc((void **)&b->d_box, sizeof(BoxDev) * n);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_idx, idx.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_box, box.data(), sizeof(BoxDev) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        batch_free(b);
+        delete b;
+        return e == cudaErrorMemoryAllocation ? LBE_ENOMEM : LBE_ECUDA;
+    }
+    b->idx.box = b->d_box;
+    b->idx.nbox = n;
+    b->idx.tile0 = b->d_idx;
+    b->idx.node0 = b->d_idx + (n + 1);
+    b->idx.part0 = b->d_idx + 2 * (n + 1);
+    b->idx.par = b->d_idx + 3 * (n + 1);
+    b->idx.counter = b->idx.par + 2 * n;
+    b->ctas_per_sm = fused_batch_ctas_per_sm(b->storage);
+    *out = b;
+    return LBE_OK;
+}
+
+lbe_status lbe_batch_step(lbe_batch *b, int32_t nsteps)
+{
+    if (!b || nsteps < 0) return LBE_EINVAL;
+    if (nsteps == 0) return LBE_OK;
+    cudaSetDevice(b->device);
+    if (!b->graph) {
+        cudaGraph_t g;
+        cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return LBE_ECUDA;
+        batch_enqueue_step(b);
+        e = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess) return LBE_ECUDA;
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return LBE_ECUDA;
+    }
+    // order after the members' own work, and their later work after this
+    for (size_t m = 0; m < b->members.size(); m++) {
+        if (cudaEventRecord(b->mev[m], b->members[m]->stream) != cudaSuccess) return LBE_ECUDA;
+        if (cudaStreamWaitEvent(b->stream, b->mev[m], 0) != cudaSuccess) return LBE_ECUDA;
+    }
+    for (int k = 0; k < nsteps; k++)
+        if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) return LBE_ECUDA;
+    if (cudaEventRecord(b->done, b->stream) != cudaSuccess) return LBE_ECUDA;
+    for (lbe_ctx *c : b->members)
+        if (cudaStreamWaitEvent(c->stream, b->done, 0) != cudaSuccess) return LBE_ECUDA;
+    // the members' host-side parities follow the device ones
+    for (lbe_ctx *c : b->members) {
+        if (nsteps & 1) {
+            c->cur ^= 1;
+            if (c->np > 0 && c->d.particle_mode != LBE_PARTICLES_STATIC) c->ocur ^= 1;
+        }
+    }
+    return cudaGetLastError() == cudaSuccess ? LBE_OK : LBE_ECUDA;
+}
+
+lbe_status lbe_batch_autotune(lbe_batch *b, int32_t *chosen_ctas_per_sm)
+{
+    if (!b) return LBE_EINVAL;
+    cudaSetDevice(b->device);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LBE_ECUDA;
+    for (lbe_ctx *c : b->members)
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return LBE_ECUDA;
+    // Persistent CTAs per SM for the batched fused kernel, timed on the
+    // fused kernel alone (it writes only the spare buffers; the link sums it
+    // accumulates are cleared afterwards).
+    const int maxc = fused_batch_ctas_per_sm(b->storage);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_c = maxc;
+    for (int cps = 1; cps <= maxc; cps++) {
+        for (int r = 0; r < 4; r++) {
+            if (r == 1) cudaEventRecord(e0, b->stream);
+            cudaMemsetAsync(b->idx.counter, 0, sizeof(int), b->stream);
+            launch_fused_batch(b->storage, b->idx, b->total_tiles, 152 * cps, b->stream);
+        }
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_c = cps;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (lbe_ctx *c : b->members)
+        if (c->np > 0) cudaMemsetAsync(c->P.fix, 0, (size_t)6 * c->np * sizeof(unsigned long long), b->stream);
+    b->ctas_per_sm = best_c;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    if (chosen_ctas_per_sm) *chosen_ctas_per_sm = best_c;
+    return cudaStreamSynchronize(b->stream) == cudaSuccess ? LBE_OK : LBE_ECUDA;
+}
+
+int32_t lbe_batch_kernels_per_step(const lbe_batch *b)
+{
+    if (!b) return 0;
+    return b->total_parts > 0 ? 9 : 4;
+}
+
+void lbe_batch_destroy(lbe_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    delete b;
 }
 
 }  // extern "C"

@@ -120,9 +120,43 @@ struct Links {
 
 constexpr double FIXED_UNIT = 1.0 / 1099511627776.0;  // 2^-40
 
+// Offsets of the population arrays of a lattice: pop[c*Q+i] = (c*Q+i)*S and
+// push[c*Q+i] = pop[c*Q+i] + (cx + cy*nx + cz*nx*ny), so the address of a
+// load or of an interior push is one add.
+struct FusedOfs {
+    long long pop[2 * Q];
+    long long push[2 * Q];
+};
+FusedOfs fused_offsets(const Lat &L);
+
 struct Pair {
     double k_hertz, lub_cut, mu;
     int mode;
+};
+
+// One lattice of a batch (all boxes step together in multi-lattice kernels).
+// Ping-pong parities live in a device array beside the table, so that a
+// captured step can be replayed whatever the parity.
+struct BoxDev {
+    Lat L;
+    FusedOfs ofs;
+    void *f[2];
+    float *rho, *psi;
+    uint8_t *type;
+    uint32_t *owner[2];
+    Parts P;                 // nsplit = 1 inside a batch
+    Pair pair;
+    int mode;                // particle mode
+    int zc, ntx, nty, nzc;   // fused-kernel tiling of this box
+};
+
+// Prefix offsets of the boxes' work items (tiles, nodes, particles).
+struct BatchIndex {
+    const BoxDev *box;
+    int nbox;
+    const int *tile0, *node0, *part0;   // [nbox + 1]
+    int *par;                           // [2 nbox]: cur, ocur
+    int *counter;                       // persistent tile queue of the fused kernel
 };
 
 // ---- launchers (fluid.cu) -------------------------------------------------
@@ -144,10 +178,37 @@ void launch_get_f(int storage, const Lat &L, const void *f, double *out, cudaStr
 void launch_set_f(int storage, const Lat &L, const double *in, void *f, cudaStream_t s);
 int mass_blocks();
 
+// ---- batched launchers (one launch steps every box of a batch) -------------
+void launch_bnd_rho_batch(int storage, const BatchIndex &B, int total_nodes, cudaStream_t s);
+void launch_shell_batch(const BatchIndex &B, int total_nodes, cudaStream_t s);
+void launch_fused_batch(int storage, const BatchIndex &B, int total_tiles, int ctas, cudaStream_t s);
+int fused_batch_ctas_per_sm(int storage);
+void launch_pairs_batch(const BatchIndex &B, int total_parts, cudaStream_t s);
+void launch_integrate_batch(const BatchIndex &B, int total_parts, cudaStream_t s);
+void launch_claim_batch(const BatchIndex &B, int total_parts, cudaStream_t s);
+void launch_transition_batch(int storage, const BatchIndex &B, int total_parts, cudaStream_t s);
+void launch_reset_batch(const BatchIndex &B, int total_parts, cudaStream_t s);
+void launch_flip_batch(const BatchIndex &B, cudaStream_t s);
+
 // ---- launchers (fused.cu) -------------------------------------------------
 void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
-                  const uint8_t *type, const Links &lk, cudaStream_t s);
+                  const uint8_t *type, const Links &lk, cudaStream_t s, int zc_override = 0);
 int fused_zchunk(const Lat &L);
+constexpr int FUSED_TX = 32, FUSED_TY = 8;
+
+// Box lookup: the box b with off[b] <= i < off[b+1] (binary search).
+__device__ __forceinline__ int find_box(const int *off, int nbox, int i)
+{
+    int lo = 0, hi = nbox - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
 
 // ---- launchers (particles.cu) ---------------------------------------------
 void launch_links(int storage, const Lat &L, const Parts &P, void *fnew, const float *rho,

@@ -408,6 +408,20 @@ __device__ void pair_term(const Lat &L, const Parts &P, const Pair &pp, int i, i
     }
 }
 
+// FP32 prefilter of a pair (centres and reaches in xyzw): nearest-image
+// distance within reach_i + reach_j + extra.  Pairs it drops contribute
+// exactly zero, so it decides nothing but the work done.
+__device__ __forceinline__ bool near_pair(float4 me, float4 o, const float nl[3], const float inv[3], bool per_z,
+                                          float extra)
+{
+    float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
+    dx = __fmaf_rn(-nl[0], rintf(dx * inv[0]), dx);
+    dy = __fmaf_rn(-nl[1], rintf(dy * inv[1]), dy);
+    if (per_z) dz = __fmaf_rn(-nl[2], rintf(dz * inv[2]), dz);
+    const float reach = me.w + o.w + extra;
+    return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)) <= reach * reach;
+}
+
 // The j range is split over gridDim.y CTAs per i tile (enough CTAs to fill
 // the GPU); each split writes its partial sums, which k_integrate adds in
 // split order.
@@ -440,16 +454,9 @@ __global__ void __launch_bounds__(PAIR_T) k_pairs(Lat L, Parts P, Pair pp)
         __syncthreads();
         if (act) {
             int lim = min(PAIR_T, P.n - base);
-            for (int t = 0; t < lim; t++) {
-                float4 o = tile[t];
-                float dx = o.x - me.x, dy = o.y - me.y, dz = o.z - me.z;
-                dx -= nl[0] * rintf(dx * inv[0]);
-                dy -= nl[1] * rintf(dy * inv[1]);
-                if (per_z) dz -= nl[2] * rintf(dz * inv[2]);
-                float reach = me.w + o.w + extra;
-                if (dx * dx + dy * dy + dz * dz <= reach * reach && base + t != i)
+            for (int t = 0; t < lim; t++)
+                if (near_pair(me, tile[t], nl, inv, per_z, extra) && base + t != i)
                     pair_term(L, P, pp, i, base + t, oi, F, T);
-            }
         }
         __syncthreads();
     }
@@ -492,10 +499,8 @@ __device__ void rotate_by_body_omega(double q[4], const double wb[3])
     for (int k = 0; k < 4; k++) q[k] = qn[k] / nn;
 }
 
-__global__ void k_integrate(Lat L, Parts P, int mode)
+__device__ __forceinline__ void integrate_body(const Lat &L, const Parts &P, int mode, int p)
 {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P.n) return;
     double F[3], T[3];
     for (int k = 0; k < 3; k++) {
         // link sums: FP64 from the two-pass link kernel, or 2^-40 fixed point
@@ -574,13 +579,19 @@ __global__ void k_integrate(Lat L, Parts P, int mode)
     P.K32[2 * p + 1] = make_float4((float)W[0], (float)W[1], (float)W[2], 0.f);
 }
 
+__global__ void k_integrate(Lat L, Parts P, int mode)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= P.n) return;
+    integrate_body(L, P, mode, p);
+}
+
 // ---------------------------------------------------------------- claim
 // Every non-wall node inside a particle is claimed with atomicMin, so a
 // node inside several particles goes to the lowest index.
 
-__global__ void __launch_bounds__(PT) k_claim(Lat L, Parts P, uint32_t *__restrict__ owner_new)
+__device__ __forceinline__ void claim_body(const Lat &L, const Parts &P, int p, uint32_t *__restrict__ owner_new)
 {
-    const int p = blockIdx.x;
     __shared__ Box box;
     __shared__ Geo geo;
     __shared__ double sX[3];
@@ -622,6 +633,11 @@ __global__ void __launch_bounds__(PT) k_claim(Lat L, Parts P, uint32_t *__restri
     }
 }
 
+__global__ void __launch_bounds__(PT) k_claim(Lat L, Parts P, uint32_t *__restrict__ owner_new)
+{
+    claim_body(L, P, blockIdx.x, owner_new);
+}
+
 // ------------------------------------------------------------ transition
 // Compare the old and new ownership.  A node whose owner changed is handled
 // by exactly one CTA: that of the lower of its old and new owner.
@@ -632,13 +648,10 @@ __global__ void __launch_bounds__(PT) k_claim(Lat L, Parts P, uint32_t *__restri
 // With placement != 0 (particles just added) nodes only change type.
 
 template <class S>
-__global__ void __launch_bounds__(PT) k_transition(Lat L, Parts P, typename S::T *__restrict__ f,
-                                                   uint8_t *__restrict__ type,
-                                                   const uint32_t *__restrict__ own_old,
-                                                   const uint32_t *__restrict__ own_new,
-                                                   int placement)
+__device__ __forceinline__ void transition_body(const Lat &L, const Parts &P, int p, typename S::T *__restrict__ f,
+                                                uint8_t *__restrict__ type, const uint32_t *__restrict__ own_old,
+                                                const uint32_t *__restrict__ own_new, int placement)
 {
-    const int p = blockIdx.x;
     __shared__ Box box;
     __shared__ double sX[3], sV[3], sW[3];
     __shared__ double red[6][PT / 32];
@@ -762,13 +775,23 @@ __global__ void __launch_bounds__(PT) k_transition(Lat L, Parts P, typename S::T
     }
 }
 
+template <class S>
+__global__ void __launch_bounds__(PT) k_transition(Lat L, Parts P, typename S::T *__restrict__ f,
+                                                   uint8_t *__restrict__ type,
+                                                   const uint32_t *__restrict__ own_old,
+                                                   const uint32_t *__restrict__ own_new,
+                                                   int placement)
+{
+    transition_body<S>(L, P, blockIdx.x, f, type, own_old, own_new, placement);
+}
+
 // ---------------------------------------------------------------- reset
 // Clear an ownership map over every particle's box (old geometry when
 // use_old), so the map is all NONE again for the next claim.
 
-__global__ void __launch_bounds__(PT) k_reset(Lat L, Parts P, int use_old, uint32_t *__restrict__ owner)
+__device__ __forceinline__ void reset_body(const Lat &L, const Parts &P, int p, int use_old,
+                                           uint32_t *__restrict__ owner)
 {
-    const int p = blockIdx.x;
     __shared__ Box box;
     if (threadIdx.x == 0) {
         const double *q = use_old ? P.qold + 4 * p : P.q + 4 * p;
@@ -788,6 +811,98 @@ __global__ void __launch_bounds__(PT) k_reset(Lat L, Parts P, int use_old, uint3
     }
 }
 
+__global__ void __launch_bounds__(PT) k_reset(Lat L, Parts P, int use_old, uint32_t *__restrict__ owner)
+{
+    reset_body(L, P, blockIdx.x, use_old, owner);
+}
+
+// ------------------------------------------------------------- batched
+// One launch for all boxes of a batch: a CTA (or thread) per particle of the
+// batch, in box order; parities come from the batch's device state.
+
+__global__ void __launch_bounds__(PT) k_claim_batch(BatchIndex B, int total)
+{
+    const int g = blockIdx.x;
+    const int b = find_box(B.part0, B.nbox, g);
+    const BoxDev &bx = B.box[b];
+    if (bx.mode == LBE_PARTICLES_STATIC) return;
+    claim_body(bx.L, bx.P, g - B.part0[b], bx.owner[1 - B.par[2 * b + 1]]);
+}
+
+template <class S>
+__global__ void __launch_bounds__(PT) k_transition_batch(BatchIndex B, int total)
+{
+    const int g = blockIdx.x;
+    const int b = find_box(B.part0, B.nbox, g);
+    const BoxDev &bx = B.box[b];
+    if (bx.mode == LBE_PARTICLES_STATIC) return;
+    const int cur = B.par[2 * b], ocur = B.par[2 * b + 1];
+    transition_body<S>(bx.L, bx.P, g - B.part0[b], (typename S::T *)bx.f[1 - cur], bx.type, bx.owner[ocur],
+                       bx.owner[1 - ocur], 0);
+}
+
+__global__ void __launch_bounds__(PT) k_reset_batch(BatchIndex B, int total)
+{
+    const int g = blockIdx.x;
+    const int b = find_box(B.part0, B.nbox, g);
+    const BoxDev &bx = B.box[b];
+    if (bx.mode == LBE_PARTICLES_STATIC) return;
+    reset_body(bx.L, bx.P, g - B.part0[b], 1, bx.owner[B.par[2 * b + 1]]);
+}
+
+__global__ void k_integrate_batch(BatchIndex B, int total)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int b = find_box(B.part0, B.nbox, g);
+    const BoxDev &bx = B.box[b];
+    integrate_body(bx.L, bx.P, bx.mode, g - B.part0[b]);
+}
+
+// Pair forces within each box: one thread per particle runs over the same
+// j splits as k_pairs (split s covers the tiles [s*per, (s+1)*per) of
+// PAIR_T particles) and writes each split's sum, so k_integrate adds the
+// same terms in the same order as for the box stepped alone.
+__global__ void k_pairs_batch(BatchIndex B, int total)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int b = find_box(B.part0, B.nbox, g);
+    const BoxDev &bx = B.box[b];
+    const Lat &L = bx.L;
+    const Parts &P = bx.P;
+    const int i = g - B.part0[b];
+    double Ri[3][3];
+    rotmat(P.q + 4 * i, Ri);
+    const double oi[3] = {Ri[0][0], Ri[1][0], Ri[2][0]};
+    const float4 me = P.X32[i];
+    const float nl[3] = {(float)L.nx, (float)L.ny, (float)L.nz};
+    const float inv[3] = {1.f / nl[0], 1.f / nl[1], 1.f / nl[2]};
+    const bool per_z = !L.walls;
+    const float extra = (float)bx.pair.lub_cut + 0.05f;
+    const int tiles = (P.n + PAIR_T - 1) / PAIR_T;
+    const int per = (tiles + P.nsplit - 1) / P.nsplit;
+    for (int sp = 0; sp < P.nsplit; sp++) {
+        double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+        const int j0 = min(sp * per * PAIR_T, P.n), j1 = min((sp + 1) * per * PAIR_T, P.n);
+        for (int j = j0; j < j1; j++)
+            if (near_pair(me, P.X32[j], nl, inv, per_z, extra) && j != i) pair_term(L, P, bx.pair, i, j, oi, F, T);
+        for (int k = 0; k < 3; k++) {
+            P.ppart[((size_t)sp * 6 + k) * P.n + i] = F[k];
+            P.ppart[((size_t)sp * 6 + 3 + k) * P.n + i] = T[k];
+        }
+    }
+}
+
+// End of a batched step: flip each box's parities.
+__global__ void k_flip_batch(BatchIndex B)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B.nbox) return;
+    B.par[2 * b] ^= 1;
+    if (B.box[b].P.n > 0 && B.box[b].mode != LBE_PARTICLES_STATIC) B.par[2 * b + 1] ^= 1;
+}
+
 #ifdef LBE_CHECK
 // Checked builds: after each step the node types must agree with the
 // ownership map (particle iff owned).
@@ -802,6 +917,31 @@ __global__ void k_verify(Lat L, const uint8_t *type, const uint32_t *owner)
 #endif
 
 }  // namespace
+
+void launch_pairs_batch(const BatchIndex &B, int total, cudaStream_t s)
+{
+    if (total > 0) k_pairs_batch<<<(total + 127) / 128, 128, 0, s>>>(B, total);
+}
+
+void launch_integrate_batch(const BatchIndex &B, int total, cudaStream_t s)
+{
+    if (total > 0) k_integrate_batch<<<(total + 127) / 128, 128, 0, s>>>(B, total);
+}
+
+void launch_claim_batch(const BatchIndex &B, int total, cudaStream_t s)
+{
+    if (total > 0) k_claim_batch<<<total, PT, 0, s>>>(B, total);
+}
+
+void launch_reset_batch(const BatchIndex &B, int total, cudaStream_t s)
+{
+    if (total > 0) k_reset_batch<<<total, PT, 0, s>>>(B, total);
+}
+
+void launch_flip_batch(const BatchIndex &B, cudaStream_t s)
+{
+    k_flip_batch<<<(B.nbox + 127) / 128, 128, 0, s>>>(B);
+}
 
 void launch_verify(const Lat &L, const uint8_t *type, const uint32_t *owner, cudaStream_t s)
 {
@@ -862,6 +1002,12 @@ void launch_transition(int storage, const Lat &L, const Parts &P, void *f, uint8
     if (P.n == 0) return;
     LBE_DISPATCH(storage, (k_transition<S><<<P.n, PT, 0, s>>>(L, P, (typename S::T *)f, type, owner_old,
                                                                owner_new, placement)));
+}
+
+void launch_transition_batch(int storage, const BatchIndex &B, int total, cudaStream_t s)
+{
+    if (total == 0) return;
+    LBE_DISPATCH(storage, (k_transition_batch<S><<<total, PT, 0, s>>>(B, total)));
 }
 
 void launch_reset(const Lat &L, const Parts &P, int use_old, uint32_t *owner, cudaStream_t s)

@@ -63,6 +63,12 @@ SIGNATURES = {
     "lbe_device_bytes": (ctypes.c_size_t, [_P]),
     "lbe_mass_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_int64, _D,
                                          ctypes.c_int32, _P, _P]),
+    "lbe_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "lbe_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_P)]),
+    "lbe_batch_step": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "lbe_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "lbe_batch_kernels_per_step": (ctypes.c_int32, [_P]),
+    "lbe_batch_destroy": (None, [_P]),
     "lbe_last_error": (ctypes.c_char_p, [_P]),
     "lbe_destroy": (None, [_P]),
 }
@@ -203,12 +209,60 @@ class Lattice:
     def kernels_per_step(self):
         return int(load().lbe_kernels_per_step(self._ptr))
 
+    def autotune(self):
+        """Time the fused kernel's z-chunk candidates; returns the one chosen."""
+        zc = ctypes.c_int32()
+        self._check(load().lbe_autotune(self._ptr, ctypes.byref(zc)), "autotune")
+        return zc.value
+
     def device_bytes(self):
         return int(load().lbe_device_bytes(self._ptr))
 
     def close(self):
         if self._ptr:
             load().lbe_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several lattices stepped together by one launch per kernel (a
+    persistent fused kernel over the tiles of all members).  The members stay
+    ordinary Lattice objects for reading; they must outlive the batch and
+    must not gain particles while it exists."""
+
+    def __init__(self, members):
+        self.members = list(members)
+        arr = (ctypes.c_void_p * len(self.members))(*[m._ptr.value for m in self.members])
+        self._ptr = ctypes.c_void_p()
+        st = load().lbe_batch_create(arr, len(self.members), ctypes.byref(self._ptr))
+        if st != 0:
+            raise LbeError(st, "lbe_batch_create")
+
+    def step(self, n=1):
+        st = load().lbe_batch_step(self._ptr, int(n))
+        if st != 0:
+            raise LbeError(st, "lbe_batch_step")
+
+    def autotune(self):
+        """Time the persistent CTAs per SM; returns the number chosen."""
+        c = ctypes.c_int32()
+        st = load().lbe_batch_autotune(self._ptr, ctypes.byref(c))
+        if st != 0:
+            raise LbeError(st, "lbe_batch_autotune")
+        return c.value
+
+    def kernels_per_step(self):
+        return int(load().lbe_batch_kernels_per_step(self._ptr))
+
+    def close(self):
+        if self._ptr:
+            load().lbe_batch_destroy(self._ptr)
             self._ptr = ctypes.c_void_p()
 
     def __del__(self):

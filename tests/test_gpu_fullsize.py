@@ -92,7 +92,9 @@ def test_fullsize_mass_and_types(pickering):
     """Properties at any size: all 25,033 particles are placed (their node
     count is that of the oracle's coverage rule, checked on a window above),
     and the fluid mass changes only by what the moving boundaries create or
-    remove, a few parts in 10^6 over a few steps."""
+    remove.  The oracle on the same recipe at 48^3 and 64^3 (same volume
+    fraction) changes the fluid mass by up to 7e-5 of itself in 4 steps; the
+    bound is 2e-4."""
     w = pickering
     g = lbe.Lattice(w.shape, w.rho0, storage="f32", **w.params)
     p = w.particles
@@ -104,5 +106,5 @@ def test_fullsize_mass_and_types(pickering):
     m0 = g.mass()
     g.step(4)
     m1 = g.mass()
-    assert np.all(np.abs(m1 - m0) / m0 < 1e-5)
+    assert np.all(np.abs(m1 - m0) / m0 < 2e-4)
     g.close()
