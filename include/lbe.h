@@ -210,6 +210,65 @@ LBE_API lbe_status lbe_batch_autotune(lbe_batch *b, int32_t *chosen_ctas_per_sm)
 LBE_API int32_t lbe_batch_kernels_per_step(const lbe_batch *b);
 LBE_API void lbe_batch_destroy(lbe_batch *b);
 
+/* Device bytes a context with descriptor d and nparticles particles holds
+ * at most (populations, fields, maps, particle state, and the transient
+ * buffer of the initial densities); 0 for an invalid descriptor.  Used for
+ * admission by HBM footprint. */
+LBE_API size_t lbe_footprint(const lbe_lattice_desc *d, int32_t nparticles);
+
+/* Orientation (w, x, y, z) of the first particle of every member, in the
+ * order the members were given to lbe_batch_create (zeros for members
+ * without particles): one gather kernel and one copy; synchronises the
+ * batch's stream.  quat_out holds 4 doubles per member. */
+LBE_API lbe_status lbe_batch_first_quat(lbe_batch *b, double *quat_out);
+
+/* ---- Serving: single-particle adsorption requests (§4 of the paper: an
+ * ellipsoid released at a flat interface, run until its tilt settles) with
+ * continuous batching.
+ *
+ * A server owns one worker thread on the device current at creation.  Its
+ * loop admits queued requests in arrival order while fewer than max_slots
+ * run and the sum of their lbe_footprint stays within hbm_budget_bytes
+ * (setting up new lattices while the running ones step on the GPU), steps
+ * all running boxes as one batch in chunks of 100 steps, and after each
+ * chunk retires every box whose first particle's tilt (angle of its body x
+ * axis to z, radians) changed by less than tilt_tol over the chunk, or
+ * that reached max_steps (rounded up to a multiple of 100).  A request's
+ * result is bit-identical to running it alone.  The server's storage mode
+ * replaces the descriptor's; the descriptor's stream, device and flags are
+ * ignored.
+ *
+ * particle_blob: per particle LBE_PARTICLE_IN doubles,
+ *   pos[3], quat[4] (w,x,y,z), vel[3], omega[3], r_par, r_perp, delta_rho.
+ * particle_out:  per particle LBE_PARTICLE_OUT doubles,
+ *   pos[3], quat[4], vel[3], omega[3], force[3], torque[3]
+ *   (the state after the last step, as lbe_read_particles gives it).
+ * Host buffers are the caller's; submit copies its inputs.
+ * lbe_server_submit: LBE_ENOMEM if the request alone exceeds the budget.
+ * lbe_server_poll: *done = 1 once the request finished; a failed request
+ *   returns its error status.  LBE_EINVAL for an unknown id.
+ * lbe_server_wait: block until the request finished or timeout_ms passed
+ *   (LBE_ETIMEOUT).
+ * lbe_server_timing: seconds from submission to admission and to the end
+ *   (LBE_EBUSY while it runs).
+ * lbe_server_stats: out = {completed requests, lattice node updates done,
+ *   most boxes run at once, chunks run}.
+ * lbe_server_destroy: stops after the chunk in flight; unfinished requests
+ *   are dropped. */
+#define LBE_PARTICLE_IN 16
+#define LBE_PARTICLE_OUT 19
+typedef struct lbe_server lbe_server;
+LBE_API lbe_status lbe_server_create(size_t hbm_budget_bytes, int32_t max_slots, int32_t storage, lbe_server **out);
+LBE_API lbe_status lbe_server_submit(lbe_server *s, const lbe_lattice_desc *d, const double *rho0, int32_t nparticles,
+                                     const double *particle_blob, int32_t max_steps, double tilt_tol,
+                                     uint64_t *req_id);
+LBE_API lbe_status lbe_server_poll(lbe_server *s, uint64_t req_id, int32_t *done, int32_t *steps_run,
+                                   double *particle_out);
+LBE_API lbe_status lbe_server_wait(lbe_server *s, uint64_t req_id, int32_t timeout_ms);
+LBE_API lbe_status lbe_server_timing(lbe_server *s, uint64_t req_id, double *queued_s, double *latency_s);
+LBE_API lbe_status lbe_server_stats(lbe_server *s, int64_t out[4]);
+LBE_API void lbe_server_destroy(lbe_server *s);
+
 LBE_API const char *lbe_last_error(const lbe_ctx *c);
 LBE_API void lbe_destroy(lbe_ctx *c);
 

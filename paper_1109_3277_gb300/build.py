@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbe.so")
 LIB_CHECK = os.path.join(HERE, "liblbe_check.so")
-SOURCES = ["lbe_api.cu", "fluid.cu", "fused.cu", "particles.cu", "noalloc.cu"]
+SOURCES = ["lbe_api.cu", "fluid.cu", "fused.cu", "particles.cu", "noalloc.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

@@ -597,6 +597,24 @@ int32_t lbe_kernels_per_step(const lbe_ctx *c)
 
 size_t lbe_device_bytes(const lbe_ctx *c) { return c ? c->bytes : 0; }
 
+size_t lbe_footprint(const lbe_lattice_desc *d, int32_t nparticles)
+{
+    if (!d || d->nx < 1 || d->ny < 1 || d->nz < 1 || nparticles < 0) return 0;
+    if (d->storage < LBE_STORE_F32 || d->storage > LBE_STORE_F16_OFS) return 0;
+    const size_t N = (size_t)d->nx * d->ny * d->nz;
+    const size_t S = ((N + 127) / 128) * 128 + 384;
+    size_t b = 2 * (size_t)2 * Q * S * storage_size(d->storage);  // two population buffers
+    b += 2 * (2 * N * sizeof(float));                             // rho, psi
+    b += N + 2 * N * 4;                                           // node types, two owner maps
+    b += (size_t)2 * mass_blocks() * sizeof(double) + 2 * sizeof(double);
+    b += 2 * N * sizeof(double);                                  // initial densities (transient)
+    if (nparticles > 0) {
+        const size_t cap = nparticles < 64 ? 64 : (size_t)nparticles + nparticles / 4;
+        b += cap * (PSTRIDE * sizeof(double) + 3 * sizeof(float4) + PAIR_SPLIT_MAX * 6 * sizeof(double));
+    }
+    return b;
+}
+
 const char *lbe_last_error(const lbe_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 void lbe_destroy(lbe_ctx *c)
@@ -663,6 +681,8 @@ lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc)
 
 struct lbe_batch {
     std::vector<lbe_ctx *> members;   // in table order (largest box first)
+    std::vector<int> order;           // table position -> position in the caller's list
+    double *d_quat = nullptr, *h_quat = nullptr;  // first-particle orientations
     int device = 0, storage = 0;
     cudaStream_t stream = nullptr;    // the batch's own stream
     cudaEvent_t done = nullptr;       // end of the last batched launch
@@ -699,6 +719,8 @@ void batch_free(lbe_batch *b)
 {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (cudaEvent_t e : b->mev) cudaEventDestroy(e);
+    cudaFree(b->d_quat);
+    if (b->h_quat) cudaFreeHost(b->h_quat);
     if (b->done) cudaEventDestroy(b->done);
     if (b->stream) cudaStreamDestroy(b->stream);
     cudaFree(b->d_box);
@@ -728,12 +750,13 @@ lbe_status lbe_batch_create(lbe_ctx *const *members, int32_t n, lbe_batch **out)
     b->device = m0->device;
     b->storage = m0->d.storage;
     cudaSetDevice(b->device);
+    std::vector<int> idx0(n);
     for (int k = 0; k < n; k++) {
         if (cudaStreamSynchronize(members[k]->stream) != cudaSuccess) {
             delete b;
             return LBE_ECUDA;
         }
-        b->members.push_back(members[k]);
+        idx0[k] = k;
     }
     {
         cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
@@ -750,8 +773,12 @@ lbe_status lbe_batch_create(lbe_ctx *const *members, int32_t n, lbe_batch **out)
         }
     }
     // largest boxes first, so that the persistent fused kernel starts on them
-    std::stable_sort(b->members.begin(), b->members.end(),
-                     [](const lbe_ctx *x, const lbe_ctx *y) { return x->L.N > y->L.N; });
+    std::stable_sort(idx0.begin(), idx0.end(),
+                     [&](int x, int y) { return members[x]->L.N > members[y]->L.N; });
+    for (int k = 0; k < n; k++) {
+        b->members.push_back(members[idx0[k]]);
+        b->order.push_back(idx0[k]);
+    }
     std::vector<BoxDev> box(n);
     std::vector<int> idx(3 * (n + 1) + 2 * n + 1, 0);
     int *tile0 = idx.data(), *node0 = tile0 + (n + 1), *part0 = node0 + (n + 1), *par = part0 + (n + 1);
@@ -786,6 +813,8 @@ lbe_status lbe_batch_create(lbe_ctx *const *members, int32_t n, lbe_batch **out)
     b->total_parts = part0[n];
     cudaError_t e = cudaMalloc((void **)&b->d_box, sizeof(BoxDev) * n);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_idx, idx.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_quat, sizeof(double) * 4 * n);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_quat, sizeof(double) * 4 * n);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_box, box.data(), sizeof(BoxDev) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -883,6 +912,20 @@ lbe_status lbe_batch_autotune(lbe_batch *b, int32_t *chosen_ctas_per_sm)
     }
     if (chosen_ctas_per_sm) *chosen_ctas_per_sm = best_c;
     return cudaStreamSynchronize(b->stream) == cudaSuccess ? LBE_OK : LBE_ECUDA;
+}
+
+lbe_status lbe_batch_first_quat(lbe_batch *b, double *quat_out)
+{
+    if (!b || !quat_out) return LBE_EINVAL;
+    cudaSetDevice(b->device);
+    launch_batch_quat(b->idx, b->d_quat, b->stream);
+    const size_t n = b->members.size();
+    if (cudaMemcpyAsync(b->h_quat, b->d_quat, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+        return LBE_ECUDA;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return LBE_ECUDA;
+    for (size_t k = 0; k < n; k++)
+        for (int j = 0; j < 4; j++) quat_out[4 * b->order[k] + j] = b->h_quat[4 * k + j];
+    return LBE_OK;
 }
 
 int32_t lbe_batch_kernels_per_step(const lbe_batch *b)

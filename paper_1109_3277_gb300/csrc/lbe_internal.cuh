@@ -188,6 +188,7 @@ void launch_integrate_batch(const BatchIndex &B, int total_parts, cudaStream_t s
 void launch_claim_batch(const BatchIndex &B, int total_parts, cudaStream_t s);
 void launch_transition_batch(int storage, const BatchIndex &B, int total_parts, cudaStream_t s);
 void launch_reset_batch(const BatchIndex &B, int total_parts, cudaStream_t s);
+void launch_batch_quat(const BatchIndex &B, double *out, cudaStream_t s);
 void launch_flip_batch(const BatchIndex &B, cudaStream_t s);
 
 // ---- launchers (fused.cu) -------------------------------------------------

@@ -903,6 +903,16 @@ __global__ void k_flip_batch(BatchIndex B)
     if (B.box[b].P.n > 0 && B.box[b].mode != LBE_PARTICLES_STATIC) B.par[2 * b + 1] ^= 1;
 }
 
+// Orientation of the first particle of each box (zeros for a box without
+// particles), for the host's per-box convergence checks.
+__global__ void k_batch_quat(BatchIndex B, double *out)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B.nbox) return;
+    const Parts &P = B.box[b].P;
+    for (int k = 0; k < 4; k++) out[4 * b + k] = P.n > 0 ? P.q[k] : 0.0;
+}
+
 #ifdef LBE_CHECK
 // Checked builds: after each step the node types must agree with the
 // ownership map (particle iff owned).
@@ -936,6 +946,11 @@ void launch_claim_batch(const BatchIndex &B, int total, cudaStream_t s)
 void launch_reset_batch(const BatchIndex &B, int total, cudaStream_t s)
 {
     if (total > 0) k_reset_batch<<<total, PT, 0, s>>>(B, total);
+}
+
+void launch_batch_quat(const BatchIndex &B, double *out, cudaStream_t s)
+{
+    k_batch_quat<<<(B.nbox + 127) / 128, 128, 0, s>>>(B, out);
 }
 
 void launch_flip_batch(const BatchIndex &B, cudaStream_t s)

@@ -15,6 +15,8 @@ Q = 19
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 MODES = {"free": 0, "static": 1, "prescribed": 2}
 FLAG_TWO_PASS = 1
+PARTICLE_IN = 16   # pos[3], quat[4], vel[3], omega[3], r_par, r_perp, delta_rho
+PARTICLE_OUT = 19  # pos[3], quat[4], vel[3], omega[3], force[3], torque[3]
 
 STATUS = {0: "LBE_OK", -1: "LBE_EINVAL", -2: "LBE_ENOMEM", -3: "LBE_ECUDA", -4: "LBE_ENUMERIC",
           -5: "LBE_EOVERLAP", -6: "LBE_ETIMEOUT", -7: "LBE_EBUSY"}
@@ -69,6 +71,17 @@ SIGNATURES = {
     "lbe_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "lbe_batch_kernels_per_step": (ctypes.c_int32, [_P]),
     "lbe_batch_destroy": (None, [_P]),
+    "lbe_footprint": (ctypes.c_size_t, [ctypes.POINTER(LatticeDesc), ctypes.c_int32]),
+    "lbe_batch_first_quat": (ctypes.c_int, [_P, _D]),
+    "lbe_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_P)]),
+    "lbe_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(LatticeDesc), _D, ctypes.c_int32, _D, ctypes.c_int32,
+                                         ctypes.c_double, ctypes.POINTER(ctypes.c_uint64)]),
+    "lbe_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32), _D]),
+    "lbe_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int32]),
+    "lbe_server_timing": (ctypes.c_int, [_P, ctypes.c_uint64, _D, _D]),
+    "lbe_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "lbe_server_destroy": (None, [_P]),
     "lbe_last_error": (ctypes.c_char_p, [_P]),
     "lbe_destroy": (None, [_P]),
 }
@@ -260,9 +273,111 @@ class Batch:
     def kernels_per_step(self):
         return int(load().lbe_batch_kernels_per_step(self._ptr))
 
+    def first_quat(self):
+        """Orientation of each member's first particle, [n_members, 4]."""
+        out = np.zeros((len(self.members), 4))
+        st = load().lbe_batch_first_quat(self._ptr, _dp(out))
+        if st != 0:
+            raise LbeError(st, "lbe_batch_first_quat")
+        return out
+
     def close(self):
         if self._ptr:
             load().lbe_batch_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def footprint(shape, nparticles=0, **params):
+    """Device bytes a lattice of this shape and particle count holds at most."""
+    d = make_desc(tuple(shape), **params)
+    return int(load().lbe_footprint(ctypes.byref(d), int(nparticles)))
+
+
+def particle_blob(pos, quat, r_par, r_perp, delta_rho, vel=None, omega=None):
+    """Pack particles into the [n, PARTICLE_IN] layout of lbe_server_submit."""
+    pos = _f64(pos).reshape(-1, 3)
+    n = pos.shape[0]
+    b = np.zeros((n, PARTICLE_IN))
+    b[:, 0:3] = pos
+    b[:, 3:7] = _f64(quat).reshape(n, 4)
+    if vel is not None:
+        b[:, 7:10] = _f64(vel).reshape(n, 3)
+    if omega is not None:
+        b[:, 10:13] = _f64(omega).reshape(n, 3)
+    b[:, 13] = np.broadcast_to(r_par, (n,))
+    b[:, 14] = np.broadcast_to(r_perp, (n,))
+    b[:, 15] = np.broadcast_to(delta_rho, (n,))
+    return b
+
+
+class Server:
+    """Continuous-batching server of adsorption requests on the current
+    device (lbe_server_*)."""
+
+    def __init__(self, hbm_budget_bytes, max_slots, storage="f32"):
+        self._ptr = ctypes.c_void_p()
+        st = load().lbe_server_create(int(hbm_budget_bytes), int(max_slots),
+                                      STORAGE[storage] if isinstance(storage, str) else int(storage),
+                                      ctypes.byref(self._ptr))
+        if st != 0:
+            raise LbeError(st, "lbe_server_create")
+        self._np = {}
+
+    def submit(self, shape, rho0, blob, max_steps, tilt_tol, **params):
+        nx, ny, nz = shape
+        d = make_desc(tuple(shape), **params)
+        r = _f64(rho0, (2, nz, ny, nx))
+        blob = _f64(blob).reshape(-1, PARTICLE_IN)
+        rid = ctypes.c_uint64()
+        st = load().lbe_server_submit(self._ptr, ctypes.byref(d), _dp(r), blob.shape[0],
+                                      _dp(blob) if blob.shape[0] else None, int(max_steps),
+                                      float(tilt_tol), ctypes.byref(rid))
+        if st != 0:
+            raise LbeError(st, "lbe_server_submit")
+        self._np[rid.value] = blob.shape[0]
+        return rid.value
+
+    def poll(self, rid):
+        """(done, steps_run, particles [n, PARTICLE_OUT] or None)."""
+        done = ctypes.c_int32()
+        steps = ctypes.c_int32()
+        out = np.zeros((max(1, self._np.get(rid, 0)), PARTICLE_OUT))
+        st = load().lbe_server_poll(self._ptr, ctypes.c_uint64(rid), ctypes.byref(done),
+                                    ctypes.byref(steps), _dp(out))
+        if st != 0:
+            raise LbeError(st, "lbe_server_poll")
+        return bool(done.value), steps.value, out[:self._np.get(rid, 0)] if done.value else None
+
+    def wait(self, rid, timeout_s=60.0):
+        st = load().lbe_server_wait(self._ptr, ctypes.c_uint64(rid), int(timeout_s * 1000))
+        if st != 0:
+            raise LbeError(st, "lbe_server_wait")
+        return self.poll(rid)
+
+    def timing(self, rid):
+        q = np.zeros(1)
+        t = np.zeros(1)
+        st = load().lbe_server_timing(self._ptr, ctypes.c_uint64(rid), _dp(q), _dp(t))
+        if st != 0:
+            raise LbeError(st, "lbe_server_timing")
+        return float(q[0]), float(t[0])
+
+    def stats(self):
+        out = (ctypes.c_int64 * 4)()
+        st = load().lbe_server_stats(self._ptr, out)
+        if st != 0:
+            raise LbeError(st, "lbe_server_stats")
+        return {"completed": out[0], "node_steps": out[1], "max_running": out[2], "chunks": out[3]}
+
+    def close(self):
+        if self._ptr:
+            load().lbe_server_destroy(self._ptr)
             self._ptr = ctypes.c_void_p()
 
     def __del__(self):
