@@ -137,19 +137,24 @@ __device__ __forceinline__ int site_nb(const Lat &L, const Site &s, int i)
     return nidx(L, b, i);
 }
 
+// Densities of a fluid node with a non-fluid neighbour; returns the mask of
+// the directions whose neighbour is a particle node (0 for other nodes).
 template <class S>
-__device__ __forceinline__ void bnd_rho_node(const Lat &L, const typename S::T *__restrict__ f,
-                                             const uint8_t *__restrict__ type, float *__restrict__ rho,
-                                             const Site &s)
+__device__ __forceinline__ uint32_t bnd_rho_node(const Lat &L, const typename S::T *__restrict__ f,
+                                                 const uint8_t *__restrict__ type, float *__restrict__ rho,
+                                                 const Site &s)
 {
-    if (type[s.n] != FLUID) return;
+    if (type[s.n] != FLUID) return 0;
     bool bnd = false;
+    uint32_t pm = 0;
 #pragma unroll
     for (int i = 1; i < Q; i++) {
         int m = site_nb(L, s, i);
-        bnd |= m < 0 || type[m] != FLUID;
+        const uint8_t t = m < 0 ? WALL : type[m];
+        bnd |= t != FLUID;
+        pm |= (uint32_t)(t == PART) << i;
     }
-    if (!bnd) return;
+    if (!bnd) return 0;
 #pragma unroll
     for (int cc = 0; cc < 2; cc++) {
         float r = 0.f;
@@ -157,15 +162,36 @@ __device__ __forceinline__ void bnd_rho_node(const Lat &L, const typename S::T *
         for (int i = 0; i < Q; i++) r += S::ld(slot<S>(f, L, cc, i) + s.n, L.base[cc][i]);
         rho[(size_t)cc * L.N + s.n] = r;
     }
+    return pm;
+}
+
+// Append (n, pm) for the lanes with pm != 0 to the link list of their box:
+// lanes of the same box share one atomic on the box's counter.  Called by
+// all 32 lanes (key: the box, or -1 for a lane without a node).
+__device__ __forceinline__ void append_links(const LinkList &ll, int key, int n, uint32_t pm)
+{
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    const unsigned want = __ballot_sync(0xffffffffu, pm != 0) & grp;
+    const int lane = threadIdx.x & 31;
+    const int leader = want ? __ffs(want) - 1 : lane;
+    int base = 0;
+    if (want && lane == leader) base = atomicAdd(ll.count, __popc(want));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (pm) {
+        const int k = base + __popc(want & ((1u << lane) - 1u));
+        if (k < ll.cap) ll.ent[k] = make_uint2((unsigned)n, pm);
+    }
 }
 
 template <class S>
 __global__ void __launch_bounds__(128) k_bnd_rho(Lat L, const typename S::T *__restrict__ f,
-                                                 const uint8_t *__restrict__ type, float *__restrict__ rho)
+                                                 const uint8_t *__restrict__ type, float *__restrict__ rho,
+                                                 LinkList ll)
 {
     Site s;
-    if (!site_of(L, s)) return;
-    bnd_rho_node<S>(L, f, type, rho, s);
+    const bool valid = site_of(L, s);
+    const uint32_t pm = valid ? bnd_rho_node<S>(L, f, type, rho, s) : 0u;
+    if (ll.ent) append_links(ll, 0, s.n, pm);
 }
 
 // Node g of a batch (all boxes' nodes in box order) as a site of its box.
@@ -186,11 +212,24 @@ __device__ __forceinline__ const BoxDev &batch_site(const BatchIndex &B, int g, 
 template <class S>
 __global__ void __launch_bounds__(256) k_bnd_rho_batch(BatchIndex B, int total)
 {
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
-        Site s;
-        const BoxDev &bx = batch_site(B, g, s);
-        const int b = find_box(B.node0, B.nbox, g);
-        bnd_rho_node<S>(bx.L, (const typename S::T *)bx.f[B.par[2 * b]], bx.type, bx.rho, s);
+    // warp-uniform trip count: every lane takes part in the appends
+    const int stride = gridDim.x * blockDim.x;
+    for (int w0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < total; w0 += stride) {
+        const int g = w0 + (threadIdx.x & 31);
+        int key = -1, n = 0;
+        uint32_t pm = 0;
+        LinkList ll{nullptr, nullptr, 0};
+        if (g < total) {
+            Site s;
+            const BoxDev &bx = batch_site(B, g, s);
+            const int b = find_box(B.node0, B.nbox, g);
+            pm = bnd_rho_node<S>(bx.L, (const typename S::T *)bx.f[B.par[2 * b]], bx.type, bx.rho, s);
+            ll = bx.links;
+            if (ll.ent) key = b;
+            else pm = 0;
+            n = s.n;
+        }
+        append_links(ll, key, n, pm);
     }
 }
 
@@ -514,10 +553,10 @@ void launch_moments(int storage, const Lat &L, const void *f, const uint8_t *typ
 }
 
 void launch_bnd_rho(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho,
-                    cudaStream_t s)
+                    const LinkList &ll, cudaStream_t s)
 {
     dim3 grid((L.nx + 127) / 128, L.ny, L.nz);
-    LBE_DISPATCH(storage, (k_bnd_rho<S><<<grid, 128, 0, s>>>(L, (const typename S::T *)f, type, rho)));
+    LBE_DISPATCH(storage, (k_bnd_rho<S><<<grid, 128, 0, s>>>(L, (const typename S::T *)f, type, rho, ll)));
 }
 
 static unsigned batch_grid(int total)

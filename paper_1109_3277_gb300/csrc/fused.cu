@@ -13,12 +13,11 @@
 // The halo densities re-read neighbouring tiles' populations, which their
 // own CTAs are streaming through L2 at the same time.
 //
-// Links into particle nodes get the moving bounce-back term C (Eq. 4) in
-// registers as they are reflected.  Their momentum exchange (Eq. 5) and
-// torque are summed per particle in 64-bit fixed point (2^-40 units): each
-// FP32 link term is rounded once to an integer, and integer atomics in a
-// per-CTA shared-memory table, then in the per-particle totals, add them
-// exactly, so the sums do not depend on the order the links are met in.
+// Populations streaming into a wall or particle node are reflected into the
+// opposite slot of their own node (halfway bounce-back).  For particle
+// nodes the moving-boundary term and the momentum exchange are added
+// afterwards by the link kernel, over the list of fluid nodes next to
+// particle nodes that the boundary-density kernel collects.
 #include "lbe_internal.cuh"
 
 namespace lbe {
@@ -45,8 +44,6 @@ __device__ __forceinline__ int wrapc(int v, int n)
     return v < 0 ? v + n : v;
 }
 
-constexpr int TAB = 128;       // per-CTA particle table (power of two)
-
 __constant__ int c_x[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
 __constant__ int c_y[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
 __constant__ int c_z[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
@@ -57,17 +54,11 @@ struct Smem {
     static constexpr size_t fbuf = 0;                                          // T [2][2Q][NT]
     static constexpr size_t sps = fbuf + 2 * 2 * Q * NT * sizeof(typename S::T);  // float [3][2][HN]
     static constexpr size_t smo = sps + 3 * 2 * HN * sizeof(float);             // float [2][5][NT]
-    static constexpr size_t tacc = smo + 2 * 5 * NT * sizeof(float);           // int64 [6][TAB]
-    static constexpr size_t tid_ = tacc + 6 * TAB * sizeof(long long);          // int [TAB]
-    static constexpr size_t sow = tid_ + TAB * sizeof(int);                     // int [3][HN] owners
-    static constexpr size_t lq = sow + 3 * HN * sizeof(int);                    // uint16 [NT] link nodes
-    static constexpr size_t lpm = lq + NT * sizeof(unsigned short);             // uint32 [NT] link masks
-    static constexpr size_t lqn = lpm + NT * sizeof(uint32_t);                  // int
-    static constexpr size_t sty = lqn + 16;                                      // uint8 [3][HN]
+    static constexpr size_t sty = smo + 2 * 5 * NT * sizeof(float);            // uint8 [3][HN]
     static constexpr size_t bytes = sty + 3 * HN;
 };
 
-// ---- node arithmetic shared by the collision and the link pass ----------
+// ---- node arithmetic ------------------------------------------------------
 // Every product or sum that rounds is written with a round-to-nearest
 // intrinsic (which the compiler never contracts), so that each kernel that
 // inlines these computes the same bits: the single-lattice and the batched
@@ -98,32 +89,6 @@ __device__ __forceinline__ void feq_parts(float w, float r, float cu, float uu15
 // BGK relaxation f + (f^eq - f)/τ.
 __device__ __forceinline__ float relax(float f, float feq, float it) { return __fmaf_rn(__fsub_rn(feq, f), it, f); }
 
-// FP32 value to 64-bit fixed point in units of 2^-40 (two's complement in an
-// unsigned word, so that wrap-around addition is exact); |v| is clamped to
-// 2^22, far beyond any link term.
-__device__ __forceinline__ unsigned long long to_fixed(float v)
-{
-    v = fminf(fmaxf(v, -4194304.f), 4194304.f);
-    return (unsigned long long)__float2ll_rn(v * 1099511627776.f);
-}
-
-// Slot of particle p in the CTA's table (linear probing, at most TAB
-// probes); -1 when the table is full.
-__device__ __forceinline__ int tab_slot(int *ids, int p)
-{
-    int h = (int)(((unsigned)p * 2654435761u) >> 25) & (TAB - 1);
-    for (int k = 0; k < TAB; k++) {
-        int cur = *(volatile int *)&ids[h];
-        if (cur == p) return h;
-        if (cur == -1) {
-            int old = atomicCAS(&ids[h], -1, p);
-            if (old == -1 || old == p) return h;
-        }
-        h = (h + 1) & (TAB - 1);
-    }
-    return -1;
-}
-
 // Wrapped neighbour index of a node on the lattice boundary (off the hot
 // path; scalar arguments only, so that nothing is copied to local memory).
 __device__ __noinline__ int wrapped_nbr(int nx, int ny, int nz, int gx, int gy, int z, int i)
@@ -135,173 +100,18 @@ __device__ __noinline__ int wrapped_nbr(int nx, int ny, int nz, int gx, int gy, 
     return x + nx * (y + ny * zz);
 }
 
-// Add this lane's fixed-point sums v[6] for particle p (or nothing, p < 0)
-// to the CTA table: lanes of the warp with the same particle are combined
-// first (exact integer reductions over 16/16/32-bit limbs), and one lane per
-// particle does the atomics.  Must be called by all 32 lanes.
-__device__ __forceinline__ void warp_add(int p, const unsigned long long v[6], const Links &lk, int *tids,
-                                         unsigned long long *tacc)
-{
-    const unsigned grp = __match_any_sync(0xffffffffu, p);
-    const int lane = threadIdx.x & 31;
-    const bool leader = lane == __ffs(grp) - 1;
-    unsigned long long tot[6];
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-        const unsigned lo = (unsigned)v[k], hi = (unsigned)(v[k] >> 32);
-        const unsigned s0 = __reduce_add_sync(grp, lo & 0xffffu);
-        const unsigned s1 = __reduce_add_sync(grp, lo >> 16);
-        const unsigned s2 = __reduce_add_sync(grp, hi);
-        tot[k] = ((unsigned long long)s2 << 32) + ((unsigned long long)s1 << 16) + (unsigned long long)s0;
-    }
-    if (p < 0 || !leader) return;
-    const int h = tab_slot(tids, p);
-#pragma unroll
-    for (int k = 0; k < 6; k++) {
-        if (h >= 0)
-            atomicAdd(&tacc[k * TAB + h], tot[k]);
-        else
-            atomicAdd(&lk.fix[6 * p + k], tot[k]);
-    }
-}
-
-// All particle links of node t of the CTA's tile (plane z); t < 0: no node
-// (the lane still takes part in the warp reductions).  The node's moments,
-// the ψ ring and the staged populations are still in shared memory, so its
-// equilibrium velocity and the post-collision populations f*_i are
-// recomputed here.  The population reflected along -c_i gains
-// C = 6 w_i ρ^c u_surf.(-c_i) (Eq. 4), u_surf = V + ω x r_b at the link
-// midpoint r_b = node + c_i/2 - X, and the particle receives (2 f*_i + C) c_i
-// and r_b x that (Eq. 5), summed in 2^-40 fixed point.
-template <class S>
-__device__ __forceinline__ void link_node(const Lat &L, const Links &lk, int t, uint32_t pm, int z, int x0, int y0,
-                                          const typename S::T *fbuf, const float *smo, const float *sps,
-                                          const int *sow, typename S::T *fout, int *tids, unsigned long long *tacc)
-{
-    unsigned long long acc[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
-    int pcur = -1;
-    const int tt = t < 0 ? 0 : t;
-    const int ttx = tt % TX, tty = tt / TX;
-    const int lx = wrapc(x0 + ttx, L.nx), ly = wrapc(y0 + tty, L.ny);
-    const int nn = lx + L.nx * (ly + L.ny * z);
-    const int ec = (tty + 1) * HX + (ttx + 1);
-    const int sl0 = (z + 2) % 3, sl1 = z % 3, sl2 = (z + 1) % 3;
-    const int par = z & 1;
-    float ue[2][3], uu[2], rho[2];
-    float4 X = make_float4(0.f, 0.f, 0.f, 0.f), V = X, W = X;
-    if (pm) {
-        // the node's equilibrium velocity, as in the collision
-        const float *mo = smo + par * 5 * NT + tt;
-        rho[0] = mo[0];
-        rho[1] = mo[NT];
-        const float up[3] = {mo[2 * NT], mo[3 * NT], mo[4 * NT]};
-        float s[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-#pragma unroll
-        for (int j = 1; j < Q; j++) {
-            const int slj = cz(j) < 0 ? sl0 : (cz(j) == 0 ? sl1 : sl2);
-            const float *pp = sps + slj * 2 * HN + ec + cy(j) * HX + cx(j);
-            const float p0 = pp[0], p1 = pp[HN];
-            if (cx(j)) { s[0][0] += cx(j) * p1; s[1][0] += cx(j) * p0; }
-            if (cy(j)) { s[0][1] += cy(j) * p1; s[1][1] += cy(j) * p0; }
-            if (cz(j)) { s[0][2] += cz(j) * p1; s[1][2] += cz(j) * p0; }
-        }
-        const float pc[2] = {sps[sl1 * 2 * HN + ec], sps[sl1 * 2 * HN + HN + ec]};
-#pragma unroll
-        for (int c = 0; c < 2; c++) eq_velocity(L, c, rho[c], pc[c], s[c], up, ue[c], uu[c]);
-    }
-    const typename S::T *fbt = fbuf + par * 2 * Q * NT + tt;
-    while (pm) {
-        const int i = __ffs(pm) - 1;
-        pm &= pm - 1;
-        const int cxi = c_x[i], cyi = c_y[i], czi = c_z[i];
-        const int sli = czi < 0 ? sl0 : (czi == 0 ? sl1 : sl2);
-        const int p = sow[sli * HN + ec + cyi * HX + cxi];
-        if (p != pcur) {
-            if (pcur >= 0) {  // a second particle at this node: add the first directly
-                const int h = tab_slot(tids, pcur);
-#pragma unroll
-                for (int k = 0; k < 6; k++) {
-                    if (h >= 0)
-                        atomicAdd(&tacc[k * TAB + h], acc[k]);
-                    else
-                        atomicAdd(&lk.fix[6 * pcur + k], acc[k]);
-                    acc[k] = 0ull;
-                }
-            }
-            pcur = p;
-            X = lk.X32[p];
-            V = lk.K32[2 * p];
-            W = lk.K32[2 * p + 1];
-        }
-        float rx = (float)lx - X.x, ry = (float)ly - X.y, rz = (float)z - X.z;
-        if (rx > 0.5f * L.nx) rx -= L.nx;
-        if (rx < -0.5f * L.nx) rx += L.nx;
-        if (ry > 0.5f * L.ny) ry -= L.ny;
-        if (ry < -0.5f * L.ny) ry += L.ny;
-        if (!L.walls) {
-            if (rz > 0.5f * L.nz) rz -= L.nz;
-            if (rz < -0.5f * L.nz) rz += L.nz;
-        }
-        rx += 0.5f * cxi;
-        ry += 0.5f * cyi;
-        rz += 0.5f * czi;
-        // surface velocity V + ω × r_b at the link midpoint
-        const float usx = __fsub_rn(__fmaf_rn(W.y, rz, V.x), __fmul_rn(W.z, ry));
-        const float usy = __fsub_rn(__fmaf_rn(W.z, rx, V.y), __fmul_rn(W.x, rz));
-        const float usz = __fsub_rn(__fmaf_rn(W.x, ry, V.z), __fmul_rn(W.y, rx));
-        const float uci = usx * cxi + usy * cyi + usz * czi;
-        const bool axis = i < 7;
-        const float w = axis ? 1.f / 18.f : 1.f / 36.f;
-        const int io = (i & 1) ? i + 1 : i - 1;
-        float a = 0.f;
-#pragma unroll
-        for (int c = 0; c < 2; c++) {
-            const float r = rho[c];
-            const float cu = cxi * ue[c][0] + cyi * ue[c][1] + czi * ue[c][2];
-            float even, odd;
-            feq_parts(w, r, cu, uu[c], even, odd);
-            const float base = axis ? L.base[c][1] : L.base[c][7];
-            const float fi = S::cvt(fbt[(c * Q + i) * NT], base);
-            const float fs = relax(fi, __fadd_rn(even, odd), L.itau[c]);
-            const float C = __fmul_rn(__fmul_rn(-6.f * w, r), uci);
-            S::st(fout + nn + (long long)(c * Q + io) * L.S, __fadd_rn(fs, C), base);
-            a = __fadd_rn(a, __fmaf_rn(2.f, fs, C));
-        }
-        const float Fx = a * cxi, Fy = a * cyi, Fz = a * czi;
-        acc[0] += to_fixed(Fx);
-        acc[1] += to_fixed(Fy);
-        acc[2] += to_fixed(Fz);
-        acc[3] += to_fixed(__fsub_rn(__fmul_rn(ry, Fz), __fmul_rn(rz, Fy)));
-        acc[4] += to_fixed(__fsub_rn(__fmul_rn(rz, Fx), __fmul_rn(rx, Fz)));
-        acc[5] += to_fixed(__fsub_rn(__fmul_rn(rx, Fy), __fmul_rn(ry, Fx)));
-    }
-    warp_add(pcur, acc, lk, tids, tacc);
-}
-
 // One tile (column bx, by, z chunk bz) of one lattice.
 template <class S>
 __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__restrict__ fin,
                                            typename S::T *__restrict__ fout, const float *__restrict__ psi,
-                                           const uint8_t *__restrict__ type, int zc, const Links &lk,
-                                           const FusedOfs &ofs, int bx, int by, int bz, unsigned char *smem)
+                                           const uint8_t *__restrict__ type, int zc, const FusedOfs &ofs, int bx,
+                                           int by, int bz, unsigned char *smem)
 {
     using T = typename S::T;
     T *fbuf = reinterpret_cast<T *>(smem + Smem<S>::fbuf);          // [parity][c*Q+i][tid]
     float *sps = reinterpret_cast<float *>(smem + Smem<S>::sps);    // [slot][c][e]
     float *smo = reinterpret_cast<float *>(smem + Smem<S>::smo);    // [parity][k][tid]
     uint8_t *sty = smem + Smem<S>::sty;                             // [slot][e]
-    unsigned long long *tacc = reinterpret_cast<unsigned long long *>(smem + Smem<S>::tacc);  // [k][TAB]
-    int *tids = reinterpret_cast<int *>(smem + Smem<S>::tid_);      // [TAB]
-    int *sow = reinterpret_cast<int *>(smem + Smem<S>::sow);        // [slot][e] particle owners
-    unsigned short *lq = reinterpret_cast<unsigned short *>(smem + Smem<S>::lq);  // link queue
-    uint32_t *lpm = reinterpret_cast<uint32_t *>(smem + Smem<S>::lpm);  // link mask per node
-    int *lqn = reinterpret_cast<int *>(smem + Smem<S>::lqn);        // queue length
-    if (threadIdx.x == 0) *lqn = 0;
-    for (int e = threadIdx.x; e < TAB; e += NT) {
-        tids[e] = -1;
-#pragma unroll
-        for (int k = 0; k < 6; k++) tacc[k * TAB + e] = 0ull;
-    }
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int x0 = bx * TX, y0 = by * TY;
     const int zb = bz * zc, ze = min(zb + zc, L.nz);
@@ -346,7 +156,6 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
         }
         float *ps = sps + slot * 2 * HN;
         uint8_t *ts = sty + slot * HN;
-        int *os = sow + slot * HN;
         {
             float p0 = 0.f, p1 = 0.f;
             uint8_t t = WALL;
@@ -400,7 +209,6 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
                 } else {
                     p0 = psi[n];
                     p1 = psi[(size_t)L.N + n];
-                    if (t == PART) os[ec] = (int)lk.owner[n];
                 }
             }
             ps[ec] = p0;
@@ -426,7 +234,6 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
                 } else {
                     p0 = psi[n];
                     p1 = psi[(size_t)L.N + n];
-                    if (t == PART) os[he] = (int)lk.owner[n];
                 }
             }
             ps[he] = p0;
@@ -453,7 +260,7 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
             const float up[3] = {mo[2 * NT], mo[3 * NT], mo[4 * NT]};
             const T *fb = fbuf + par * 2 * Q * NT + tid;
             float s[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-            uint32_t solid = 0, part = 0;  // bit i: neighbour i is not fluid / is a particle node
+            uint32_t solid = 0;  // bit i: neighbour i is not fluid
 #pragma unroll
             for (int i = 1; i < Q; i++) {
                 const int e = ec + cy(i) * HX + cx(i);
@@ -461,7 +268,6 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
                 const float p0 = pp[e], p1 = pp[HN + e];
                 const uint8_t tn = tl[cz(i) + 1][e];
                 solid |= (uint32_t)(tn != FLUID) << i;
-                part |= (uint32_t)(tn == PART) << i;
                 if (cx(i)) { s[0][0] += cx(i) * p1; s[1][0] += cx(i) * p0; }
                 if (cy(i)) { s[0][1] += cy(i) * p1; s[1][1] += cy(i) * p0; }
                 if (cz(i)) { s[0][2] += cz(i) * p1; s[1][2] += cz(i) * p0; }
@@ -470,14 +276,14 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
             T *dst = fout + n;
             // store of the post-collision population fs of direction i:
             // streamed to the neighbour, or reflected into slot opp(i) of
-            // this node; reflections off particle nodes are left to the link
-            // pass after the plane (moving bounce-back, momentum exchange)
-            auto put = [&](int c, int i, float fs, float r) {
+            // this node (walls and particle nodes; the link kernel adds the
+            // moving-boundary term for the latter)
+            auto put = [&](int c, int i, float fs) {
                 const int ci = c * Q + i;
                 if (!(solid & (1u << i))) {
                     T *q = inner ? dst + ofs.push[ci] : fout + ofs.pop[ci] + wrapped_nbr(L.nx, L.ny, L.nz, gx, gy, z, i);
                     S::st(q, fs, L.base[c][i]);
-                } else if (!(part & (1u << i))) {
+                } else {
                     S::st(dst + ofs.pop[c * Q + opp(i)], fs, L.base[c][opp(i)]);
                 }
             };
@@ -498,41 +304,15 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
                     const float fa = S::cvt(fb[(c * Q + i) * NT], L.base[c][i]);
                     const float fbv = S::cvt(fb[(c * Q + i + 1) * NT], L.base[c][i + 1]);
                     seq = __fadd_rn(seq, 2.f * even);
-                    put(c, i, relax(fa, __fadd_rn(even, odd), it), r);
-                    put(c, i + 1, relax(fbv, __fsub_rn(even, odd), it), r);
+                    put(c, i, relax(fa, __fadd_rn(even, odd), it));
+                    put(c, i + 1, relax(fbv, __fsub_rn(even, odd), it));
                 }
                 // rest population: equilibrium ρ - Σ_{i>0} f^eq_i (exact mass)
                 const float f0 = S::cvt(fb[(c * Q) * NT], L.base[c][0]);
                 S::st(dst + ofs.pop[c * Q], relax(f0, __fsub_rn(r, seq), it), L.base[c][0]);
             }
-            if (part) {
-                // queue this node for the link pass
-                lpm[tid] = part;
-                lq[atomicAdd(lqn, 1)] = (unsigned short)tid;
-            }
         }
         __syncthreads();
-        // Link pass: every thread takes one queued node and all its links;
-        // consecutive queue entries go to different warps, so that the
-        // work spreads over the whole CTA.
-        const int nq = *lqn;
-        if (nq > 0) {
-            const int qi = (tid & 31) * (NT / 32) + (tid >> 5);
-            const int t = qi < nq ? lq[qi] : -1;
-            link_node<S>(L, lk, t, t >= 0 ? lpm[t] : 0u, z, x0, y0, fbuf, smo, sps, sow, fout, tids, tacc);
-            __syncthreads();
-        }
-        if (tid == 0) *lqn = 0;
-    }
-    // flush the per-particle link sums of this CTA
-    for (int e = threadIdx.x; e < TAB; e += NT) {
-        const int p = tids[e];
-        if (p < 0) continue;
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            atomicAdd(&lk.fix[6 * p + k], tacc[k * TAB + e]);
-            atomicAdd(&lk.fix[6 * p + 3 + k], tacc[(3 + k) * TAB + e]);
-        }
     }
 }
 
@@ -540,11 +320,10 @@ template <class S>
 __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__restrict__ fin,
                                               typename S::T *__restrict__ fout,
                                               const float *__restrict__ psi,
-                                              const uint8_t *__restrict__ type, int zc, Links lk,
-                                              FusedOfs ofs)
+                                              const uint8_t *__restrict__ type, int zc, FusedOfs ofs)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    fused_tile<S>(L, fin, fout, psi, type, zc, lk, ofs, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+    fused_tile<S>(L, fin, fout, psi, type, zc, ofs, blockIdx.x, blockIdx.y, blockIdx.z, smem);
 }
 
 // Persistent multi-lattice variant: CTAs take tiles of all boxes of a batch
@@ -571,10 +350,9 @@ __global__ void __launch_bounds__(NT, 3) k_fused_batch(BatchIndex B, int total)
         __syncthreads();
         const int lt = t - B.tile0[s_box];
         const int bx = lt % sb.ntx, by = (lt / sb.ntx) % sb.nty, bz = lt / (sb.ntx * sb.nty);
-        const int cur = B.par[2 * s_box], ocur = B.par[2 * s_box + 1];
-        Links lk{sb.owner[ocur], sb.P.X32, sb.P.K32, sb.P.fix};
+        const int cur = B.par[2 * s_box];
         fused_tile<S>(sb.L, (const typename S::T *)sb.f[cur], (typename S::T *)sb.f[1 - cur], sb.psi, sb.type, sb.zc,
-                      lk, sb.ofs, bx, by, bz, smem);
+                      sb.ofs, bx, by, bz, smem);
     }
 }
 
@@ -613,7 +391,7 @@ FusedOfs fused_offsets(const Lat &L)
 
 template <class S>
 static void launch_fused_t(const Lat &L, const void *fin, void *fout, const float *psi, const uint8_t *type,
-                           const Links &lk, cudaStream_t s, int zc_override)
+                           cudaStream_t s, int zc_override)
 {
     static bool configured = false;  // the attribute is per function and process
     if (!configured) {
@@ -624,13 +402,13 @@ static void launch_fused_t(const Lat &L, const void *fin, void *fout, const floa
     dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
     FusedOfs ofs = fused_offsets(L);
     k_fused<S><<<grid, NT, Smem<S>::bytes, s>>>(L, (const typename S::T *)fin, (typename S::T *)fout, psi, type,
-                                                 zc, lk, ofs);
+                                                 zc, ofs);
 }
 
 void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
-                  const uint8_t *type, const Links &lk, cudaStream_t s, int zc_override)
+                  const uint8_t *type, cudaStream_t s, int zc_override)
 {
-    LBE_DISPATCH(storage, (launch_fused_t<S>(L, fin, fout, psi, type, lk, s, zc_override)));
+    LBE_DISPATCH(storage, (launch_fused_t<S>(L, fin, fout, psi, type, s, zc_override)));
 }
 
 template <class S>

@@ -33,6 +33,7 @@ struct lbe_ctx {
     float4 *x32 = nullptr;
     double *ppart = nullptr;
     Parts P{};
+    LinkList ll{nullptr, nullptr, 0};  // link nodes of the step (allocated with the first particles)
     // graphs keyed by (cur, ocur)
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
     int zc_tuned = 0;  // fused-kernel z chunk chosen by lbe_autotune (0: heuristic)
@@ -132,6 +133,8 @@ void free_all(lbe_ctx *c)
     cudaFree(c->pbuf);
     cudaFree(c->x32);
     cudaFree(c->ppart);
+    cudaFree(c->ll.ent);
+    cudaFree(c->ll.count);
     if (c->L.err) cudaFree(c->L.err);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
@@ -160,10 +163,13 @@ void enqueue_step(lbe_ctx *c)
     int st = c->d.storage;
     void *fin = c->f[c->cur], *fout = c->f[1 - c->cur];
     const bool two_pass = (c->d.flags & LBE_FLAG_TWO_PASS) != 0;
-    if (two_pass)
+    const bool links = c->np > 0 && !two_pass;
+    if (two_pass) {
         launch_moments(st, L, fin, c->type, c->rho, c->psi, s);
-    else
-        launch_bnd_rho(st, L, fin, c->type, c->rho, s);
+    } else {
+        if (links) cudaMemsetAsync(c->ll.count, 0, sizeof(int), s);
+        launch_bnd_rho(st, L, fin, c->type, c->rho, links ? c->ll : LinkList{nullptr, nullptr, 0}, s);
+    }
     launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, s);
     if (c->profiling) {
         if (c->ev_used + 2 > c->ev.size()) {
@@ -175,19 +181,23 @@ void enqueue_step(lbe_ctx *c)
         }
         cudaEventRecord(c->ev[c->ev_used], s);
     }
-    if (two_pass) {
+    if (two_pass)
         launch_collide_stream(st, L, fin, fout, c->psi, c->type, s);
-    } else {
-        Links lk{c->owner[c->ocur], c->P.X32, c->P.K32, c->P.fix};
-        launch_fused(st, L, fin, fout, c->psi, c->type, lk, s, c->zc_tuned);
-    }
+    else
+        launch_fused(st, L, fin, fout, c->psi, c->type, s, c->zc_tuned);
     if (c->profiling) {
         cudaEventRecord(c->ev[c->ev_used + 1], s);
         c->ev_used += 2;
     }
     if (c->np > 0) {
         c->P.n = c->np;
-        if (two_pass) launch_links(st, L, c->P, fout, c->rho, c->type, c->owner[c->ocur], s);
+        if (two_pass)
+            launch_links(st, L, c->P, fout, c->rho, c->type, c->owner[c->ocur], s);
+        else {
+            launch_link(st, L, c->ll, c->rho, c->owner[c->ocur], c->P, fout, s);
+            // the list is empty between steps (batched steps rely on it)
+            cudaMemsetAsync(c->ll.count, 0, sizeof(int), s);
+        }
         launch_pairs(L, c->P, c->pair, s);
         launch_integrate(L, c->P, c->d.particle_mode, s);
         if (c->d.particle_mode != LBE_PARTICLES_STATIC) {
@@ -424,6 +434,13 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
         c->cap = ncap;
         c->bytes += (size_t)ncap * per_cap;
     }
+    if (!c->ll.ent) {
+        // a fluid node enters the link list at most once per step: N entries
+        CK(c, dalloc(c, &c->ll.ent, (size_t)c->L.N * sizeof(uint2)));
+        CK(c, dalloc(c, &c->ll.count, sizeof(int)));
+        CK(c, cudaMemset(c->ll.count, 0, sizeof(int)));
+        c->ll.cap = c->L.N;
+    }
     CK(c, cudaMemcpy(c->pbuf, blk.data(), blk.size() * sizeof(double), cudaMemcpyHostToDevice));
     CK(c, cudaMemcpy(c->x32, x32.data(), x32.size() * sizeof(float4), cudaMemcpyHostToDevice));
     c->np = np;
@@ -589,7 +606,7 @@ int32_t lbe_kernels_per_step(const lbe_ctx *c)
     const bool two_pass = (c->d.flags & LBE_FLAG_TWO_PASS) != 0;
     int k = 3;  // densities (boundary or all), shell fill, fused fluid (or collide+stream)
     if (c->np > 0) {
-        k += two_pass ? 3 : 2;  // (links), pairs, integrate
+        k += 3;  // links, pairs, integrate
         if (c->d.particle_mode != LBE_PARTICLES_STATIC) k += 3;  // claim, transition, reset
     }
     return k;
@@ -611,6 +628,7 @@ size_t lbe_footprint(const lbe_lattice_desc *d, int32_t nparticles)
     if (nparticles > 0) {
         const size_t cap = nparticles < 64 ? 64 : (size_t)nparticles + nparticles / 4;
         b += cap * (PSTRIDE * sizeof(double) + 3 * sizeof(float4) + PAIR_SPLIT_MAX * 6 * sizeof(double));
+        b += N * sizeof(uint2) + sizeof(int);  // link list
     }
     return b;
 }
@@ -638,8 +656,7 @@ lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc)
     }
     // Candidates for the z chunk of the fused kernel.  Each runs from the
     // current populations into the spare buffer, which the next step
-    // overwrites anyway, so the state is not changed (the link sums it
-    // accumulates are cleared afterwards).
+    // overwrites anyway, so the state is not changed.
     const Lat &L = c->L;
     std::vector<int> cand;
     for (int zc = 4; zc < L.nz; zc *= 2) cand.push_back(zc);
@@ -648,15 +665,14 @@ lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc)
     CK(c, cudaEventCreate(&e0));
     CK(c, cudaEventCreate(&e1));
     void *fin = c->f[c->cur], *fout = c->f[1 - c->cur];
-    Links lk{c->owner[c->ocur], c->P.X32, c->P.K32, c->P.fix};
-    launch_bnd_rho(c->d.storage, L, fin, c->type, c->rho, c->stream);
+    launch_bnd_rho(c->d.storage, L, fin, c->type, c->rho, LinkList{nullptr, nullptr, 0}, c->stream);
     launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, c->stream);
     float best = 1e30f;
     int best_zc = fused_zchunk(L);
     for (int zc : cand) {
-        launch_fused(c->d.storage, L, fin, fout, c->psi, c->type, lk, c->stream, zc);  // warm-up
+        launch_fused(c->d.storage, L, fin, fout, c->psi, c->type, c->stream, zc);  // warm-up
         cudaEventRecord(e0, c->stream);
-        for (int r = 0; r < 3; r++) launch_fused(c->d.storage, L, fin, fout, c->psi, c->type, lk, c->stream, zc);
+        for (int r = 0; r < 3; r++) launch_fused(c->d.storage, L, fin, fout, c->psi, c->type, c->stream, zc);
         cudaEventRecord(e1, c->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) break;
         float ms = 0.f;
@@ -668,7 +684,6 @@ lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc)
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (c->np > 0) CK(c, cudaMemsetAsync(c->P.fix, 0, (size_t)6 * c->np * sizeof(unsigned long long), c->stream));
     c->zc_tuned = best_zc;
     drop_graphs(c);
     if (chosen_zc) *chosen_zc = best_zc;
@@ -706,6 +721,7 @@ void batch_enqueue_step(lbe_batch *b)
     cudaMemsetAsync(b->idx.counter, 0, sizeof(int), s);
     launch_fused_batch(b->storage, b->idx, b->total_tiles, 152 * b->ctas_per_sm, s);
     if (b->total_parts > 0) {
+        launch_link_batch(b->storage, b->idx, s);
         launch_pairs_batch(b->idx, b->total_parts, s);
         launch_integrate_batch(b->idx, b->total_parts, s);
         launch_claim_batch(b->idx, b->total_parts, s);
@@ -742,6 +758,7 @@ lbe_status lbe_batch_create(lbe_ctx *const *members, int32_t n, lbe_batch **out)
         if (!c || c->device != m0->device || c->d.storage != m0->d.storage) return LBE_EINVAL;
         if (c->d.flags & LBE_FLAG_TWO_PASS) return LBE_EINVAL;
         if (c->np > LBE_BATCH_MAX_PARTICLES) return LBE_EINVAL;
+        if (n > 65535) return LBE_EINVAL;
         for (int j = 0; j < k; j++)
             if (members[j] == c) return LBE_EINVAL;
     }
@@ -798,6 +815,7 @@ lbe_status lbe_batch_create(lbe_ctx *const *members, int32_t n, lbe_batch **out)
         d.P.n = c->np;
         d.pair = c->pair;
         d.mode = c->d.particle_mode;
+        d.links = c->np > 0 ? c->ll : LinkList{nullptr, nullptr, 0};
         d.zc = c->zc_tuned > 0 ? c->zc_tuned : fused_zchunk(c->L);
         d.ntx = (c->L.nx + FUSED_TX - 1) / FUSED_TX;
         d.nty = (c->L.ny + FUSED_TY - 1) / FUSED_TY;
@@ -830,6 +848,10 @@ lbe_status lbe_batch_create(lbe_ctx *const *members, int32_t n, lbe_batch **out)
     b->idx.par = b->d_idx + 3 * (n + 1);
     b->idx.counter = b->idx.par + 2 * n;
     b->ctas_per_sm = fused_batch_ctas_per_sm(b->storage);
+    // link lists start empty; the last kernel of each batched step empties them
+    for (lbe_ctx *c : b->members)
+        if (c->np > 0 && c->ll.count) cudaMemsetAsync(c->ll.count, 0, sizeof(int), c->stream);
+    for (lbe_ctx *c : b->members) cudaStreamSynchronize(c->stream);
     *out = b;
     return LBE_OK;
 }
@@ -931,7 +953,7 @@ lbe_status lbe_batch_first_quat(lbe_batch *b, double *quat_out)
 int32_t lbe_batch_kernels_per_step(const lbe_batch *b)
 {
     if (!b) return 0;
-    return b->total_parts > 0 ? 9 : 4;
+    return b->total_parts > 0 ? 10 : 4;
 }
 
 void lbe_batch_destroy(lbe_batch *b)

@@ -112,10 +112,14 @@ struct Parts {
 
 // What the fused fluid kernel needs for the moving bounce-back (Eq. 4) and
 // the momentum exchange (Eq. 5) of the links it streams.
-struct Links {
-    const uint32_t *owner;          // current ownership map
-    const float4 *X32, *K32;        // particle position / velocity / ω (FP32)
-    unsigned long long *fix;        // per-particle force, torque sums (2^-40 fixed point)
+// Fluid nodes next to particle nodes, collected each step by the
+// boundary-density kernel: entry (node, mask of the directions i whose
+// neighbour node + c_i is a particle node).  A node enters at most once per
+// step, so cap = N cannot overflow.
+struct LinkList {
+    uint2 *ent;   // [cap]
+    int *count;   // entries this step (reset before the density kernel)
+    int cap;
 };
 
 constexpr double FIXED_UNIT = 1.0 / 1099511627776.0;  // 2^-40
@@ -147,6 +151,7 @@ struct BoxDev {
     Parts P;                 // nsplit = 1 inside a batch
     Pair pair;
     int mode;                // particle mode
+    LinkList links;          // link nodes of this box (ent null without particles)
     int zc, ntx, nty, nzc;   // fused-kernel tiling of this box
 };
 
@@ -165,7 +170,7 @@ void launch_init_f(int storage, const Lat &L, const double *rho0, void *f, const
 void launch_moments(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho,
                     float *psi, cudaStream_t s);
 void launch_bnd_rho(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho,
-                    cudaStream_t s);
+                    const LinkList &ll, cudaStream_t s);
 void launch_shell(const Lat &L, const float *rho, float *psi, const uint8_t *type,
                   const uint32_t *owner, const double *drho, cudaStream_t s);
 void launch_collide_stream(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
@@ -189,11 +194,12 @@ void launch_claim_batch(const BatchIndex &B, int total_parts, cudaStream_t s);
 void launch_transition_batch(int storage, const BatchIndex &B, int total_parts, cudaStream_t s);
 void launch_reset_batch(const BatchIndex &B, int total_parts, cudaStream_t s);
 void launch_batch_quat(const BatchIndex &B, double *out, cudaStream_t s);
+void launch_link_batch(int storage, const BatchIndex &B, cudaStream_t s);
 void launch_flip_batch(const BatchIndex &B, cudaStream_t s);
 
 // ---- launchers (fused.cu) -------------------------------------------------
 void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
-                  const uint8_t *type, const Links &lk, cudaStream_t s, int zc_override = 0);
+                  const uint8_t *type, cudaStream_t s, int zc_override = 0);
 int fused_zchunk(const Lat &L);
 constexpr int FUSED_TX = 32, FUSED_TY = 8;
 
@@ -214,6 +220,8 @@ __device__ __forceinline__ int find_box(const int *off, int nbox, int i)
 // ---- launchers (particles.cu) ---------------------------------------------
 void launch_links(int storage, const Lat &L, const Parts &P, void *fnew, const float *rho,
                   const uint8_t *type, const uint32_t *owner, cudaStream_t s);
+void launch_link(int storage, const Lat &L, const LinkList &ll, const float *rho, const uint32_t *owner,
+                 const Parts &P, void *fout, cudaStream_t s);
 void launch_pairs(const Lat &L, const Parts &P, const Pair &pp, cudaStream_t s);
 constexpr int PAIR_SPLIT_MAX = 32;
 int pair_splits(int n);

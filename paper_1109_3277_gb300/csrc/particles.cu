@@ -314,6 +314,173 @@ __global__ void __launch_bounds__(PT) k_links(Lat L, Parts P, typename S::T *__r
     }
 }
 
+// ------------------------------------------------------------ link nodes
+// For every fluid node y of the step's link list and every direction i
+// whose neighbour x = y + c_i is a particle node: the fluid kernel reflected
+// the post-collision f*_i(y) into slot ī of y; add C = -6 w_i ρ^c(y)
+// (u_surf·c_i) with u_surf = V + ω × r_b at the link midpoint r_b = y +
+// c_i/2 - X (Eq. 4), and give the particle (2 f*_i + C) c_i and r_b × that
+// (Eq. 5).  ρ^c(y) is the density the boundary-density kernel wrote this
+// step.  Force and torque are summed in 64-bit fixed point (2^-40 units):
+// each FP32 link term is rounded once to an integer and integer additions
+// are exact, so the totals do not depend on the order of the links.
+
+__constant__ int k_cx[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+__constant__ int k_cy[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+__constant__ int k_cz[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+
+// FP32 value to 64-bit fixed point in units of 2^-40 (two's complement in an
+// unsigned word, so that wrap-around addition is exact); |v| is clamped to
+// 2^22, far beyond any link term.
+__device__ __forceinline__ unsigned long long to_fixed(float v)
+{
+    v = fminf(fmaxf(v, -4194304.f), 4194304.f);
+    return (unsigned long long)__float2ll_rn(v * 1099511627776.f);
+}
+
+// Add this lane's sums v[6] for particle p (nothing for p < 0) to the
+// particle's totals: lanes of the warp with the same particle are combined
+// first (exact integer reductions over 16/16/32-bit limbs) and one lane per
+// particle does the atomics.  Called by all 32 lanes.
+__device__ __forceinline__ void warp_add_fix(int p, const unsigned long long v[6], unsigned long long *fix)
+{
+    const unsigned grp = __match_any_sync(0xffffffffu, p);
+    const bool leader = (int)(threadIdx.x & 31) == __ffs(grp) - 1;
+    unsigned long long tot[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        const unsigned lo = (unsigned)v[k], hi = (unsigned)(v[k] >> 32);
+        const unsigned s0 = __reduce_add_sync(grp, lo & 0xffffu);
+        const unsigned s1 = __reduce_add_sync(grp, lo >> 16);
+        const unsigned s2 = __reduce_add_sync(grp, hi);
+        tot[k] = ((unsigned long long)s2 << 32) + ((unsigned long long)s1 << 16) + (unsigned long long)s0;
+    }
+    if (p < 0 || !leader) return;
+#pragma unroll
+    for (int k = 0; k < 6; k++) atomicAdd(&fix[6 * p + k], tot[k]);
+}
+
+// One link node (e = (node, direction mask)); valid = false for a lane
+// without an entry (it still takes part in the warp reduction).
+template <class S>
+__device__ __forceinline__ void link_entry(const Lat &L, uint2 e, bool valid, const float *__restrict__ rho,
+                                           const uint32_t *__restrict__ owner, const float4 *__restrict__ X32,
+                                           const float4 *__restrict__ K32, unsigned long long *fix,
+                                           typename S::T *fout)
+{
+    unsigned long long acc[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+    int pcur = -1;
+    uint32_t pm = valid ? e.y : 0u;
+    const int n = valid ? (int)e.x : 0;
+    const int x = n % L.nx, t = n / L.nx, y = t % L.ny, z = t / L.ny;
+    float rh[2] = {0.f, 0.f};
+    if (pm) {
+        rh[0] = rho[n];
+        rh[1] = rho[(size_t)L.N + n];
+    }
+    float4 X = make_float4(0.f, 0.f, 0.f, 0.f), V = X, W = X;
+    while (pm) {
+        const int i = __ffs(pm) - 1;
+        pm &= pm - 1;
+        const int cxi = k_cx[i], cyi = k_cy[i], czi = k_cz[i];
+        int xn = x + cxi, yn = y + cyi, zn = z + czi;
+        xn = xn < 0 ? xn + L.nx : (xn >= L.nx ? xn - L.nx : xn);
+        yn = yn < 0 ? yn + L.ny : (yn >= L.ny ? yn - L.ny : yn);
+        zn = zn < 0 ? zn + L.nz : (zn >= L.nz ? zn - L.nz : zn);
+        const int p = (int)owner[xn + L.nx * (yn + L.ny * zn)];
+        if ((unsigned)p >= (unsigned)L.np) {  // a particle node is always owned
+            idx_ok(L, p, L.np, 20);
+            continue;
+        }
+        if (p != pcur) {
+            if (pcur >= 0) {  // a second particle at this node: add the first directly
+#pragma unroll
+                for (int k = 0; k < 6; k++) {
+                    atomicAdd(&fix[6 * pcur + k], acc[k]);
+                    acc[k] = 0ull;
+                }
+            }
+            pcur = p;
+            X = X32[p];
+            V = K32[2 * p];
+            W = K32[2 * p + 1];
+        }
+        float rx = (float)x - X.x, ry = (float)y - X.y, rz = (float)z - X.z;
+        if (rx > 0.5f * L.nx) rx -= L.nx;
+        if (rx < -0.5f * L.nx) rx += L.nx;
+        if (ry > 0.5f * L.ny) ry -= L.ny;
+        if (ry < -0.5f * L.ny) ry += L.ny;
+        if (!L.walls) {
+            if (rz > 0.5f * L.nz) rz -= L.nz;
+            if (rz < -0.5f * L.nz) rz += L.nz;
+        }
+        rx += 0.5f * cxi;
+        ry += 0.5f * cyi;
+        rz += 0.5f * czi;
+        // surface velocity V + ω × r_b at the link midpoint
+        const float usx = __fsub_rn(__fmaf_rn(W.y, rz, V.x), __fmul_rn(W.z, ry));
+        const float usy = __fsub_rn(__fmaf_rn(W.z, rx, V.y), __fmul_rn(W.x, rz));
+        const float usz = __fsub_rn(__fmaf_rn(W.x, ry, V.z), __fmul_rn(W.y, rx));
+        const float uci = __fadd_rn(__fadd_rn(usx * cxi, usy * cyi), usz * czi);
+        const bool axis = i < 7;
+        const float w6 = axis ? -6.f / 18.f : -6.f / 36.f;
+        const int io = (i & 1) ? i + 1 : i - 1;
+        float a = 0.f;
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            const float base = axis ? L.base[c][1] : L.base[c][7];
+            typename S::T *q = fout + (size_t)(c * Q + io) * (size_t)L.S + n;
+            const float fs = S::ldc(q, base);
+            const float C = __fmul_rn(__fmul_rn(w6, rh[c]), uci);
+            S::st(q, __fadd_rn(fs, C), base);
+            a = __fadd_rn(a, __fmaf_rn(2.f, fs, C));
+        }
+        const float Fx = a * cxi, Fy = a * cyi, Fz = a * czi;
+        acc[0] += to_fixed(Fx);
+        acc[1] += to_fixed(Fy);
+        acc[2] += to_fixed(Fz);
+        acc[3] += to_fixed(__fsub_rn(__fmul_rn(ry, Fz), __fmul_rn(rz, Fy)));
+        acc[4] += to_fixed(__fsub_rn(__fmul_rn(rz, Fx), __fmul_rn(rx, Fz)));
+        acc[5] += to_fixed(__fsub_rn(__fmul_rn(rx, Fy), __fmul_rn(ry, Fx)));
+    }
+    warp_add_fix(pcur, acc, fix);
+}
+
+// Warp-uniform trip count over the entries (every lane takes part in the
+// reductions).
+template <class S>
+__device__ __forceinline__ void link_list(const Lat &L, const LinkList &ll, const float *rho, const uint32_t *owner,
+                                          const Parts &P, typename S::T *fout, int first, int stride)
+{
+    const int count = min(*ll.count, ll.cap);
+    for (int w0 = first + (int)(threadIdx.x & ~31u); w0 < count; w0 += stride) {
+        const int e = w0 + (threadIdx.x & 31);
+        const bool valid = e < count;
+        link_entry<S>(L, valid ? ll.ent[e] : make_uint2(0u, 0u), valid, rho, owner, P.X32, P.K32, P.fix, fout);
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(256) k_link(Lat L, LinkList ll, const float *rho, const uint32_t *owner, Parts P,
+                                              typename S::T *fout)
+{
+    link_list<S>(L, ll, rho, owner, P, fout, blockIdx.x * blockDim.x, gridDim.x * blockDim.x);
+}
+
+// Batched: blockIdx.y is the box; LINK_BATCH_CTAS CTAs per box.
+constexpr int LINK_BATCH_CTAS = 4;
+
+template <class S>
+__global__ void __launch_bounds__(256) k_link_batch(BatchIndex B)
+{
+    const int b = blockIdx.y;
+    const BoxDev &bx = B.box[b];
+    if (!bx.links.ent || bx.P.n == 0) return;
+    const int cur = B.par[2 * b], ocur = B.par[2 * b + 1];
+    link_list<S>(bx.L, bx.links, bx.rho, bx.owner[ocur], bx.P, (typename S::T *)bx.f[1 - cur],
+                 blockIdx.x * blockDim.x, gridDim.x * blockDim.x);
+}
+
 // --------------------------------------------------------- pair forces
 
 __device__ __forceinline__ double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
@@ -901,6 +1068,7 @@ __global__ void k_flip_batch(BatchIndex B)
     if (b >= B.nbox) return;
     B.par[2 * b] ^= 1;
     if (B.box[b].P.n > 0 && B.box[b].mode != LBE_PARTICLES_STATIC) B.par[2 * b + 1] ^= 1;
+    if (B.box[b].links.count) *B.box[b].links.count = 0;  // ready for the next step's list
 }
 
 // Orientation of the first particle of each box (zeros for a box without
@@ -1023,6 +1191,21 @@ void launch_transition_batch(int storage, const BatchIndex &B, int total, cudaSt
 {
     if (total == 0) return;
     LBE_DISPATCH(storage, (k_transition_batch<S><<<total, PT, 0, s>>>(B, total)));
+}
+
+void launch_link(int storage, const Lat &L, const LinkList &ll, const float *rho, const uint32_t *owner,
+                 const Parts &P, void *fout, cudaStream_t s)
+{
+    if (P.n == 0 || !ll.ent) return;
+    int blocks = (L.N + 255) / 256;
+    if (blocks > 8 * 152) blocks = 8 * 152;
+    LBE_DISPATCH(storage, (k_link<S><<<blocks, 256, 0, s>>>(L, ll, rho, owner, P, (typename S::T *)fout)));
+}
+
+void launch_link_batch(int storage, const BatchIndex &B, cudaStream_t s)
+{
+    dim3 grid(LINK_BATCH_CTAS, B.nbox);
+    LBE_DISPATCH(storage, (k_link_batch<S><<<grid, 256, 0, s>>>(B)));
 }
 
 void launch_reset(const Lat &L, const Parts &P, int use_old, uint32_t *owner, cudaStream_t s)
