@@ -165,11 +165,29 @@ __device__ __forceinline__ uint32_t bnd_rho_node(const Lat &L, const typename S:
     return pm;
 }
 
-// Append (n, pm) for the lanes with pm != 0 to the link list of their box:
-// lanes of the same box share one atomic on the box's counter.  Called by
-// all 32 lanes (key: the box, or -1 for a lane without a node).
-__device__ __forceinline__ void append_links(const LinkList &ll, int key, int n, uint32_t pm)
+// Append (n, pm) for the lanes with pm != 0 to the list: one atomic per
+// warp.  Called by all 32 lanes.
+__device__ __forceinline__ void append_links(const LinkList &ll, int n, uint32_t pm)
 {
+    const unsigned want = __ballot_sync(0xffffffffu, pm != 0);
+    if (!want) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(want) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(ll.count, __popc(want));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (pm) {
+        const int k = base + __popc(want & ((1u << lane) - 1u));
+        if (k < ll.cap) ll.ent[k] = make_uint2((unsigned)n, pm);
+    }
+}
+
+// Batched form: lanes may belong to different boxes (key: the box, or -1
+// for a lane without a node); lanes of the same box share one atomic on the
+// box's counter.  Called by all 32 lanes.
+__device__ __forceinline__ void append_links_keyed(const LinkList &ll, int key, int n, uint32_t pm)
+{
+    if (!__any_sync(0xffffffffu, pm != 0)) return;
     const unsigned grp = __match_any_sync(0xffffffffu, key);
     const unsigned want = __ballot_sync(0xffffffffu, pm != 0) & grp;
     const int lane = threadIdx.x & 31;
@@ -188,10 +206,10 @@ __global__ void __launch_bounds__(128) k_bnd_rho(Lat L, const typename S::T *__r
                                                  const uint8_t *__restrict__ type, float *__restrict__ rho,
                                                  LinkList ll)
 {
-    Site s;
+    Site s{};
     const bool valid = site_of(L, s);
     const uint32_t pm = valid ? bnd_rho_node<S>(L, f, type, rho, s) : 0u;
-    if (ll.ent) append_links(ll, 0, s.n, pm);
+    if (ll.ent) append_links(ll, s.n, pm);
 }
 
 // Node g of a batch (all boxes' nodes in box order) as a site of its box.
@@ -229,7 +247,7 @@ __global__ void __launch_bounds__(256) k_bnd_rho_batch(BatchIndex B, int total)
             else pm = 0;
             n = s.n;
         }
-        append_links(ll, key, n, pm);
+        append_links_keyed(ll, key, n, pm);
     }
 }
 

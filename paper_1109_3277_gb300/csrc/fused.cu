@@ -44,16 +44,13 @@ __device__ __forceinline__ int wrapc(int v, int n)
     return v < 0 ? v + n : v;
 }
 
-__constant__ int c_x[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
-__constant__ int c_y[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
-__constant__ int c_z[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
 
 // Dynamic shared memory layout (bytes).
 template <class S>
 struct Smem {
     static constexpr size_t fbuf = 0;                                          // T [2][2Q][NT]
-    static constexpr size_t sps = fbuf + 2 * 2 * Q * NT * sizeof(typename S::T);  // float [3][2][HN]
-    static constexpr size_t smo = sps + 3 * 2 * HN * sizeof(float);             // float [2][5][NT]
+    static constexpr size_t sps = fbuf + 2 * 2 * Q * NT * sizeof(typename S::T);  // float2 [3][HN] (ψ_r, ψ_b)
+    static constexpr size_t smo = sps + 3 * HN * sizeof(float2);                // float [2][5][NT]
     static constexpr size_t sty = smo + 2 * 5 * NT * sizeof(float);            // uint8 [3][HN]
     static constexpr size_t bytes = sty + 3 * HN;
 };
@@ -89,17 +86,6 @@ __device__ __forceinline__ void feq_parts(float w, float r, float cu, float uu15
 // BGK relaxation f + (f^eq - f)/τ.
 __device__ __forceinline__ float relax(float f, float feq, float it) { return __fmaf_rn(__fsub_rn(feq, f), it, f); }
 
-// Wrapped neighbour index of a node on the lattice boundary (off the hot
-// path; scalar arguments only, so that nothing is copied to local memory).
-__device__ __noinline__ int wrapped_nbr(int nx, int ny, int nz, int gx, int gy, int z, int i)
-{
-    int x = gx + c_x[i], y = gy + c_y[i], zz = z + c_z[i];
-    x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-    y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-    zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
-    return x + nx * (y + ny * zz);
-}
-
 // One tile (column bx, by, z chunk bz) of one lattice.
 template <class S>
 __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__restrict__ fin,
@@ -109,7 +95,7 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
 {
     using T = typename S::T;
     T *fbuf = reinterpret_cast<T *>(smem + Smem<S>::fbuf);          // [parity][c*Q+i][tid]
-    float *sps = reinterpret_cast<float *>(smem + Smem<S>::sps);    // [slot][c][e]
+    float2 *sps = reinterpret_cast<float2 *>(smem + Smem<S>::sps);  // [slot][e]
     float *smo = reinterpret_cast<float *>(smem + Smem<S>::smo);    // [parity][k][tid]
     uint8_t *sty = smem + Smem<S>::sty;                             // [slot][e]
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
@@ -120,23 +106,25 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
     const int nxy = L.nx * L.ny;
     const int ec = (ty + 1) * HX + (tx + 1);
 
-    // halo entry of this thread (threads tid < NHALO): top row, bottom row,
-    // left column, right column of the (TX+2) x (TY+2) tile
+    // halo entry h of this thread: top row, bottom row, left column, right
+    // column of the (TX+2) x (TY+2) tile; threads 2h and 2h+1 take the two
+    // components of entry h
+    const int h = tid >> 1, hc = tid & 1;
     int he = 0, hn2 = 0;
-    if (tid < NHALO) {
+    if (h < NHALO) {
         int hx, hy;
-        if (tid < HX) {
-            hx = tid;
+        if (h < HX) {
+            hx = h;
             hy = 0;
-        } else if (tid < 2 * HX) {
-            hx = tid - HX;
+        } else if (h < 2 * HX) {
+            hx = h - HX;
             hy = HY - 1;
-        } else if (tid < 2 * HX + TY) {
+        } else if (h < 2 * HX + TY) {
             hx = 0;
-            hy = tid - 2 * HX + 1;
+            hy = h - 2 * HX + 1;
         } else {
             hx = HX - 1;
-            hy = tid - 2 * HX - TY + 1;
+            hy = h - 2 * HX - TY + 1;
         }
         he = hy * HX + hx;
         hn2 = wrapc(x0 + hx - 1, L.nx) + L.nx * wrapc(y0 + hy - 1, L.ny);
@@ -154,7 +142,7 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
         } else {
             gz = zz < 0 ? zz + L.nz : (zz >= L.nz ? zz - L.nz : zz);
         }
-        float *ps = sps + slot * 2 * HN;
+        float2 *ps = sps + slot * HN;
         uint8_t *ts = sty + slot * HN;
         {
             float p0 = 0.f, p1 = 0.f;
@@ -211,34 +199,28 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
                     p1 = psi[(size_t)L.N + n];
                 }
             }
-            ps[ec] = p0;
-            ps[HN + ec] = p1;
+            ps[ec] = make_float2(p0, p1);
             ts[ec] = t;
         }
-        if (tid < NHALO) {
-            float p0 = 0.f, p1 = 0.f;
+        if (h < NHALO) {
+            float p = 0.f;
             uint8_t t = WALL;
             if (zin) {
                 const int n = hn2 + nxy * gz;
                 t = type[n];
                 if (t == FLUID) {
                     const T *src = fin + n;
-                    float r0 = 0.f, r1 = 0.f;
+                    // same summation order as for the own nodes
+                    float r = S::cvt(__ldg(src + ofs.pop[hc * Q]), L.base[hc][0]);
 #pragma unroll
-                    for (int i = 0; i < Q; i++) {
-                        r0 += S::cvt(__ldg(src + ofs.pop[i]), L.base[0][i]);
-                        r1 += S::cvt(__ldg(src + ofs.pop[Q + i]), L.base[1][i]);
-                    }
-                    p0 = 1.f - expf(-r0);
-                    p1 = 1.f - expf(-r1);
+                    for (int i = 1; i < Q; i++) r += S::cvt(__ldg(src + ofs.pop[hc * Q + i]), L.base[hc][i]);
+                    p = 1.f - expf(-r);
                 } else {
-                    p0 = psi[n];
-                    p1 = psi[(size_t)L.N + n];
+                    p = psi[(size_t)hc * L.N + n];
                 }
             }
-            ps[he] = p0;
-            ps[HN + he] = p1;
-            ts[he] = t;
+            reinterpret_cast<float *>(ps + he)[hc] = p;
+            if (hc == 0) ts[he] = t;
         }
     };
 
@@ -249,7 +231,7 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
         load_plane(z + 1, z + 1 < ze);
         __syncthreads();
         // ring slots of planes z-1, z, z+1
-        const float *pl[3] = {sps + ((z + 2) % 3) * 2 * HN, sps + (z % 3) * 2 * HN, sps + ((z + 1) % 3) * 2 * HN};
+        const float2 *pl[3] = {sps + ((z + 2) % 3) * HN, sps + (z % 3) * HN, sps + ((z + 1) % 3) * HN};
         const uint8_t *tl[3] = {sty + ((z + 2) % 3) * HN, sty + (z % 3) * HN, sty + ((z + 1) % 3) * HN};
         if (active && tl[1][ec] == FLUID) {
             const int n = own2 + nxy * z;
@@ -264,28 +246,42 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
 #pragma unroll
             for (int i = 1; i < Q; i++) {
                 const int e = ec + cy(i) * HX + cx(i);
-                const float *pp = pl[cz(i) + 1];
-                const float p0 = pp[e], p1 = pp[HN + e];
+                const float2 pp = pl[cz(i) + 1][e];
+                const float p0 = pp.x, p1 = pp.y;
                 const uint8_t tn = tl[cz(i) + 1][e];
                 solid |= (uint32_t)(tn != FLUID) << i;
                 if (cx(i)) { s[0][0] += cx(i) * p1; s[1][0] += cx(i) * p0; }
                 if (cy(i)) { s[0][1] += cy(i) * p1; s[1][1] += cy(i) * p0; }
                 if (cz(i)) { s[0][2] += cz(i) * p1; s[1][2] += cz(i) * p0; }
             }
-            const float pc[2] = {pl[1][ec], pl[1][HN + ec]};
+            const float2 pcc = pl[1][ec];
+            const float pc[2] = {pcc.x, pcc.y};
             T *dst = fout + n;
-            // store of the post-collision population fs of direction i:
-            // streamed to the neighbour, or reflected into slot opp(i) of
-            // this node (walls and particle nodes; the link kernel adds the
-            // moving-boundary term for the latter)
-            auto put = [&](int c, int i, float fs) {
-                const int ci = c * Q + i;
-                if (!(solid & (1u << i))) {
-                    T *q = inner ? dst + ofs.push[ci] : fout + ofs.pop[ci] + wrapped_nbr(L.nx, L.ny, L.nz, gx, gy, z, i);
-                    S::st(q, fs, L.base[c][i]);
-                } else {
-                    S::st(dst + ofs.pop[c * Q + opp(i)], fs, L.base[c][opp(i)]);
+            // Push offsets of nodes on the lattice boundary wrap around the
+            // periodic axes: corrections for c = +1 ([0]) and c = -1 ([1]).
+            int wx[2] = {0, 0}, wy[2] = {0, 0}, wz[2] = {0, 0};
+            if (!inner) {
+                wx[0] = gx == L.nx - 1 ? -L.nx : 0;
+                wx[1] = gx == 0 ? L.nx : 0;
+                wy[0] = gy == L.ny - 1 ? -nxy : 0;
+                wy[1] = gy == 0 ? nxy : 0;
+                if (!L.walls) {  // with walls z = 0 and nz-1 are wall nodes
+                    wz[0] = z == L.nz - 1 ? -L.N : 0;
+                    wz[1] = z == 0 ? L.N : 0;
                 }
+            }
+            // store of the post-collision population fs of direction i:
+            // pushed to the neighbour, or reflected into slot opp(i) of this
+            // node (walls and particle nodes; the link kernel adds the
+            // moving-boundary term for the latter).  Both slots have the
+            // same weight, hence the same storage offset; the address is a
+            // select, not a branch.
+            auto put = [&](int c, int i, float fs) {
+                const int corr = (cx(i) > 0 ? wx[0] : (cx(i) < 0 ? wx[1] : 0)) +
+                                 (cy(i) > 0 ? wy[0] : (cy(i) < 0 ? wy[1] : 0)) +
+                                 (cz(i) > 0 ? wz[0] : (cz(i) < 0 ? wz[1] : 0));
+                const long long o = ((solid >> i) & 1u) ? ofs.pop[c * Q + opp(i)] : ofs.push[c * Q + i] + corr;
+                S::st(dst + o, fs, L.base[c][i]);
             };
 #pragma unroll
             for (int c = 0; c < 2; c++) {

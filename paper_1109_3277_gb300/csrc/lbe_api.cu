@@ -603,7 +603,6 @@ lbe_status lbe_profile_read(lbe_ctx *c, double *ms_total, int64_t *launches)
 int32_t lbe_kernels_per_step(const lbe_ctx *c)
 {
     if (!c) return 0;
-    const bool two_pass = (c->d.flags & LBE_FLAG_TWO_PASS) != 0;
     int k = 3;  // densities (boundary or all), shell fill, fused fluid (or collide+stream)
     if (c->np > 0) {
         k += 3;  // links, pairs, integrate
