@@ -104,12 +104,41 @@ __global__ void __launch_bounds__(256) k_moments(Lat L, const typename S::T *__r
     }
 }
 
-// ------------------------------------------------------ boundary densities
-// ρ^c on the fluid nodes that have a solid neighbour: the only densities the
-// shell fill reads (the fused kernel computes the others itself).  Both this
-// kernel and the shell fill run on a 3D grid (x per thread, one y row and z
-// plane per block row), so no index division is needed, and interior nodes
-// reach their neighbours by a fixed offset.
+// ------------------------------------------------------------ densities
+// ρ^c = Σ_i f_i^c on every fluid node, for the shell fill, the link kernel
+// and the halo of the fused kernel (which sums its own nodes' populations
+// in the same order, so the two agree bit for bit).  One thread per pair of
+// consecutive nodes, with paired loads; the slot stride S is padded past N,
+// so the pair loads of the last node stay inside the allocation.
+
+template <class S>
+__global__ void __launch_bounds__(256) k_rho(Lat L, const typename S::T *__restrict__ f,
+                                             const uint8_t *__restrict__ type, float *__restrict__ rho)
+{
+    const long long n = 2ll * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+    if (n >= L.N) return;
+    const bool two = n + 1 < L.N;
+    const bool fl0 = type[n] == FLUID, fl1 = two && type[n + 1] == FLUID;
+    if (!fl0 && !fl1) return;
+#pragma unroll
+    for (int c = 0; c < 2; c++) {
+        float a0, a1;
+        S::ld2(slot<S>(f, L, c, 0) + n, L.base[c][0], a0, a1);
+#pragma unroll
+        for (int i = 1; i < Q; i++) {
+            float v0, v1;
+            S::ld2(slot<S>(f, L, c, i) + n, L.base[c][i], v0, v1);
+            a0 += v0;
+            a1 += v1;
+        }
+        if (fl0) rho[(size_t)c * L.N + n] = a0;
+        if (fl1) rho[(size_t)c * L.N + n + 1] = a1;
+    }
+}
+
+// Neighbour indexing on a 3D grid (x per thread, one y row and z plane per
+// block row): no index division, and interior nodes reach their neighbours
+// by a fixed offset.
 
 __device__ __forceinline__ int nb_off(const Lat &L, int i) { return cx(i) + L.nx * (cy(i) + L.ny * cz(i)); }
 
@@ -137,79 +166,40 @@ __device__ __forceinline__ int site_nb(const Lat &L, const Site &s, int i)
     return nidx(L, b, i);
 }
 
-// Densities of a fluid node with a non-fluid neighbour; returns the mask of
-// the directions whose neighbour is a particle node (0 for other nodes).
-template <class S>
-__device__ __forceinline__ uint32_t bnd_rho_node(const Lat &L, const typename S::T *__restrict__ f,
-                                                 const uint8_t *__restrict__ type, float *__restrict__ rho,
-                                                 const Site &s)
+// Append (n, m) for the lanes with m != 0 to the list: one atomic per warp.
+// Called by all 32 lanes.
+__device__ __forceinline__ void append_links(const LinkList &ll, int n, uint32_t m)
 {
-    if (type[s.n] != FLUID) return 0;
-    bool bnd = false;
-    uint32_t pm = 0;
-#pragma unroll
-    for (int i = 1; i < Q; i++) {
-        int m = site_nb(L, s, i);
-        const uint8_t t = m < 0 ? WALL : type[m];
-        bnd |= t != FLUID;
-        pm |= (uint32_t)(t == PART) << i;
-    }
-    if (!bnd) return 0;
-#pragma unroll
-    for (int cc = 0; cc < 2; cc++) {
-        float r = 0.f;
-#pragma unroll
-        for (int i = 0; i < Q; i++) r += S::ld(slot<S>(f, L, cc, i) + s.n, L.base[cc][i]);
-        rho[(size_t)cc * L.N + s.n] = r;
-    }
-    return pm;
-}
-
-// Append (n, pm) for the lanes with pm != 0 to the list: one atomic per
-// warp.  Called by all 32 lanes.
-__device__ __forceinline__ void append_links(const LinkList &ll, int n, uint32_t pm)
-{
-    const unsigned want = __ballot_sync(0xffffffffu, pm != 0);
+    const unsigned want = __ballot_sync(0xffffffffu, m != 0);
     if (!want) return;
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(want) - 1;
     int base = 0;
     if (lane == leader) base = atomicAdd(ll.count, __popc(want));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (pm) {
+    if (m) {
         const int k = base + __popc(want & ((1u << lane) - 1u));
-        if (k < ll.cap) ll.ent[k] = make_uint2((unsigned)n, pm);
+        if (k < ll.cap) ll.ent[k] = make_uint2((unsigned)n, m);
     }
 }
 
 // Batched form: lanes may belong to different boxes (key: the box, or -1
 // for a lane without a node); lanes of the same box share one atomic on the
 // box's counter.  Called by all 32 lanes.
-__device__ __forceinline__ void append_links_keyed(const LinkList &ll, int key, int n, uint32_t pm)
+__device__ __forceinline__ void append_links_keyed(const LinkList &ll, int key, int n, uint32_t m)
 {
-    if (!__any_sync(0xffffffffu, pm != 0)) return;
+    if (!__any_sync(0xffffffffu, m != 0)) return;
     const unsigned grp = __match_any_sync(0xffffffffu, key);
-    const unsigned want = __ballot_sync(0xffffffffu, pm != 0) & grp;
+    const unsigned want = __ballot_sync(0xffffffffu, m != 0) & grp;
     const int lane = threadIdx.x & 31;
     const int leader = want ? __ffs(want) - 1 : lane;
     int base = 0;
     if (want && lane == leader) base = atomicAdd(ll.count, __popc(want));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (pm) {
+    if (m) {
         const int k = base + __popc(want & ((1u << lane) - 1u));
-        if (k < ll.cap) ll.ent[k] = make_uint2((unsigned)n, pm);
+        if (k < ll.cap) ll.ent[k] = make_uint2((unsigned)n, m);
     }
-}
-
-template <class S>
-__global__ void __launch_bounds__(128) k_bnd_rho(Lat L, const typename S::T *__restrict__ f,
-                                                 const uint8_t *__restrict__ type, float *__restrict__ rho,
-                                                 LinkList ll)
-{
-    Site s{};
-    const bool valid = site_of(L, s);
-    const uint32_t pm = valid ? bnd_rho_node<S>(L, f, type, rho, s) : 0u;
-    if (ll.ent) append_links(ll, s.n, pm);
 }
 
 // Node g of a batch (all boxes' nodes in box order) as a site of its box.
@@ -227,44 +217,44 @@ __device__ __forceinline__ const BoxDev &batch_site(const BatchIndex &B, int g, 
     return bx;
 }
 
+// Densities of the fluid nodes of all boxes, one node per thread (batched
+// boxes are small).
 template <class S>
-__global__ void __launch_bounds__(256) k_bnd_rho_batch(BatchIndex B, int total)
+__global__ void __launch_bounds__(256) k_rho_batch(BatchIndex B, int total)
 {
-    // warp-uniform trip count: every lane takes part in the appends
-    const int stride = gridDim.x * blockDim.x;
-    for (int w0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < total; w0 += stride) {
-        const int g = w0 + (threadIdx.x & 31);
-        int key = -1, n = 0;
-        uint32_t pm = 0;
-        LinkList ll{nullptr, nullptr, 0};
-        if (g < total) {
-            Site s;
-            const BoxDev &bx = batch_site(B, g, s);
-            const int b = find_box(B.node0, B.nbox, g);
-            pm = bnd_rho_node<S>(bx.L, (const typename S::T *)bx.f[B.par[2 * b]], bx.type, bx.rho, s);
-            ll = bx.links;
-            if (ll.ent) key = b;
-            else pm = 0;
-            n = s.n;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
+        Site s;
+        const BoxDev &bx = batch_site(B, g, s);
+        if (bx.type[s.n] != FLUID) continue;
+        const int b = find_box(B.node0, B.nbox, g);
+        const typename S::T *f = (const typename S::T *)bx.f[B.par[2 * b]];
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            float r = S::ld(slot<S>(f, bx.L, c, 0) + s.n, bx.L.base[c][0]);
+#pragma unroll
+            for (int i = 1; i < Q; i++) r += S::ld(slot<S>(f, bx.L, c, i) + s.n, bx.L.base[c][i]);
+            bx.rho[(size_t)c * bx.L.N + s.n] = r;
         }
-        append_links_keyed(ll, key, n, pm);
     }
 }
 
 // ---------------------------------------------------------- shell fill
 // Solid nodes with at least one fluid neighbour take the mean ρ^c of those
 // neighbours (Eq. 10); the colour Δρ of the owning particle is added to red
-// if positive, else |Δρ| to blue.  Walls take Δρ = 0.
+// if positive, else |Δρ| to blue.  Walls take Δρ = 0.  A particle node
+// among them returns the mask of its fluid neighbours (its links), 0
+// otherwise.
 
-__device__ __forceinline__ void shell_node(const Lat &L, const float *__restrict__ rho, float *__restrict__ psi,
-                                           const uint8_t *__restrict__ type, const uint32_t *__restrict__ owner,
-                                           const double *__restrict__ drho, const Site &s)
+__device__ __forceinline__ uint32_t shell_node(const Lat &L, const float *__restrict__ rho, float *__restrict__ psi,
+                                               const uint8_t *__restrict__ type, const uint32_t *__restrict__ owner,
+                                               const double *__restrict__ drho, const Site &s)
 {
     const int n = s.n;
     uint8_t t = type[n];
-    if (t == FLUID) return;
+    if (t == FLUID) return 0;
     float s0 = 0.f, s1 = 0.f;
     int cnt = 0;
+    uint32_t fm = 0;
 #pragma unroll
     for (int i = 1; i < Q; i++) {
         int m = site_nb(L, s, i);
@@ -272,8 +262,9 @@ __device__ __forceinline__ void shell_node(const Lat &L, const float *__restrict
         s0 += rho[m];
         s1 += rho[(size_t)L.N + m];
         cnt++;
+        fm |= 1u << i;
     }
-    if (cnt == 0) return;  // interior: never read by a fluid node
+    if (cnt == 0) return 0;  // interior: never read by a fluid node
     float r0 = s0 / (float)cnt, r1 = s1 / (float)cnt;
     float dr = 0.f;
     if (t == PART) {
@@ -286,26 +277,41 @@ __device__ __forceinline__ void shell_node(const Lat &L, const float *__restrict
         r1 += fabsf(dr);
     psi[n] = 1.f - expf(-r0);
     psi[(size_t)L.N + n] = 1.f - expf(-r1);
+    return t == PART ? fm : 0u;
 }
 
-__global__ void __launch_bounds__(128) k_shell(Lat L, const float *__restrict__ rho,
-                                               float *__restrict__ psi,
-                                               const uint8_t *__restrict__ type,
-                                               const uint32_t *__restrict__ owner,
-                                               const double *__restrict__ drho)
+__global__ void __launch_bounds__(128) k_shell(Lat L, const float *__restrict__ rho, float *__restrict__ psi,
+                                               const uint8_t *__restrict__ type, const uint32_t *__restrict__ owner,
+                                               const double *__restrict__ drho, LinkList ll)
 {
-    Site s;
-    if (!site_of(L, s)) return;
-    shell_node(L, rho, psi, type, owner, drho, s);
+    Site s{};
+    const bool valid = site_of(L, s);
+    const uint32_t fm = valid ? shell_node(L, rho, psi, type, owner, drho, s) : 0u;
+    if (ll.ent) append_links(ll, s.n, fm);
 }
 
 __global__ void __launch_bounds__(256) k_shell_batch(BatchIndex B, int total)
 {
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < total; g += gridDim.x * blockDim.x) {
-        Site s;
-        const BoxDev &bx = batch_site(B, g, s);
-        const int b = find_box(B.node0, B.nbox, g);
-        shell_node(bx.L, bx.rho, bx.psi, bx.type, bx.owner[B.par[2 * b + 1]], bx.P.drho, s);
+    // warp-uniform trip count: every lane takes part in the appends
+    const int stride = gridDim.x * blockDim.x;
+    for (int w0 = blockIdx.x * blockDim.x + (threadIdx.x & ~31); w0 < total; w0 += stride) {
+        const int g = w0 + (threadIdx.x & 31);
+        int key = -1, n = 0;
+        uint32_t fm = 0;
+        LinkList ll{nullptr, nullptr, 0};
+        if (g < total) {
+            Site s;
+            const BoxDev &bx = batch_site(B, g, s);
+            const int b = find_box(B.node0, B.nbox, g);
+            fm = shell_node(bx.L, bx.rho, bx.psi, bx.type, bx.owner[B.par[2 * b + 1]], bx.P.drho, s);
+            ll = bx.links;
+            if (ll.ent)
+                key = b;
+            else
+                fm = 0;
+            n = s.n;
+        }
+        append_links_keyed(ll, key, n, fm);
     }
 }
 
@@ -570,11 +576,10 @@ void launch_moments(int storage, const Lat &L, const void *f, const uint8_t *typ
                               L, (const typename S::T *)f, type, rho, psi)));
 }
 
-void launch_bnd_rho(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho,
-                    const LinkList &ll, cudaStream_t s)
+void launch_rho(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho, cudaStream_t s)
 {
-    dim3 grid((L.nx + 127) / 128, L.ny, L.nz);
-    LBE_DISPATCH(storage, (k_bnd_rho<S><<<grid, 128, 0, s>>>(L, (const typename S::T *)f, type, rho, ll)));
+    const size_t pairs = ((size_t)L.N + 1) / 2;
+    LBE_DISPATCH(storage, (k_rho<S><<<blocks_for(pairs, 256), 256, 0, s>>>(L, (const typename S::T *)f, type, rho)));
 }
 
 static unsigned batch_grid(int total)
@@ -583,9 +588,9 @@ static unsigned batch_grid(int total)
     return g > 8 * 152 ? 8 * 152 : (g ? g : 1);
 }
 
-void launch_bnd_rho_batch(int storage, const BatchIndex &B, int total_nodes, cudaStream_t s)
+void launch_rho_batch(int storage, const BatchIndex &B, int total_nodes, cudaStream_t s)
 {
-    LBE_DISPATCH(storage, (k_bnd_rho_batch<S><<<batch_grid(total_nodes), 256, 0, s>>>(B, total_nodes)));
+    LBE_DISPATCH(storage, (k_rho_batch<S><<<batch_grid(total_nodes), 256, 0, s>>>(B, total_nodes)));
 }
 
 void launch_shell_batch(const BatchIndex &B, int total_nodes, cudaStream_t s)
@@ -593,11 +598,11 @@ void launch_shell_batch(const BatchIndex &B, int total_nodes, cudaStream_t s)
     k_shell_batch<<<batch_grid(total_nodes), 256, 0, s>>>(B, total_nodes);
 }
 
-void launch_shell(const Lat &L, const float *rho, float *psi, const uint8_t *type,
-                  const uint32_t *owner, const double *drho, cudaStream_t s)
+void launch_shell(const Lat &L, const float *rho, float *psi, const uint8_t *type, const uint32_t *owner,
+                  const double *drho, const LinkList &ll, cudaStream_t s)
 {
     dim3 grid((L.nx + 127) / 128, L.ny, L.nz);
-    k_shell<<<grid, 128, 0, s>>>(L, rho, psi, type, owner, drho);
+    k_shell<<<grid, 128, 0, s>>>(L, rho, psi, type, owner, drho, ll);
 }
 
 void launch_collide_stream(int storage, const Lat &L, const void *fin, void *fout, const float *psi,

@@ -89,9 +89,9 @@ __device__ __forceinline__ float relax(float f, float feq, float it) { return __
 // One tile (column bx, by, z chunk bz) of one lattice.
 template <class S>
 __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__restrict__ fin,
-                                           typename S::T *__restrict__ fout, const float *__restrict__ psi,
-                                           const uint8_t *__restrict__ type, int zc, const FusedOfs &ofs, int bx,
-                                           int by, int bz, unsigned char *smem)
+                                           typename S::T *__restrict__ fout, const float *__restrict__ rho,
+                                           const float *__restrict__ psi, const uint8_t *__restrict__ type, int zc,
+                                           const FusedOfs &ofs, int bx, int by, int bz, unsigned char *smem)
 {
     using T = typename S::T;
     T *fbuf = reinterpret_cast<T *>(smem + Smem<S>::fbuf);          // [parity][c*Q+i][tid]
@@ -209,12 +209,8 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
                 const int n = hn2 + nxy * gz;
                 t = type[n];
                 if (t == FLUID) {
-                    const T *src = fin + n;
-                    // same summation order as for the own nodes
-                    float r = S::cvt(__ldg(src + ofs.pop[hc * Q]), L.base[hc][0]);
-#pragma unroll
-                    for (int i = 1; i < Q; i++) r += S::cvt(__ldg(src + ofs.pop[hc * Q + i]), L.base[hc][i]);
-                    p = 1.f - expf(-r);
+                    // the density kernel's ρ: the same sum as for own nodes
+                    p = 1.f - expf(-__ldg(rho + (size_t)hc * L.N + n));
                 } else {
                     p = psi[(size_t)hc * L.N + n];
                 }
@@ -314,12 +310,12 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
 
 template <class S>
 __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__restrict__ fin,
-                                              typename S::T *__restrict__ fout,
+                                              typename S::T *__restrict__ fout, const float *__restrict__ rho,
                                               const float *__restrict__ psi,
                                               const uint8_t *__restrict__ type, int zc, FusedOfs ofs)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    fused_tile<S>(L, fin, fout, psi, type, zc, ofs, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+    fused_tile<S>(L, fin, fout, rho, psi, type, zc, ofs, blockIdx.x, blockIdx.y, blockIdx.z, smem);
 }
 
 // Persistent multi-lattice variant: CTAs take tiles of all boxes of a batch
@@ -347,8 +343,8 @@ __global__ void __launch_bounds__(NT, 3) k_fused_batch(BatchIndex B, int total)
         const int lt = t - B.tile0[s_box];
         const int bx = lt % sb.ntx, by = (lt / sb.ntx) % sb.nty, bz = lt / (sb.ntx * sb.nty);
         const int cur = B.par[2 * s_box];
-        fused_tile<S>(sb.L, (const typename S::T *)sb.f[cur], (typename S::T *)sb.f[1 - cur], sb.psi, sb.type, sb.zc,
-                      sb.ofs, bx, by, bz, smem);
+        fused_tile<S>(sb.L, (const typename S::T *)sb.f[cur], (typename S::T *)sb.f[1 - cur], sb.rho, sb.psi, sb.type,
+                      sb.zc, sb.ofs, bx, by, bz, smem);
     }
 }
 
@@ -386,8 +382,8 @@ FusedOfs fused_offsets(const Lat &L)
 }
 
 template <class S>
-static void launch_fused_t(const Lat &L, const void *fin, void *fout, const float *psi, const uint8_t *type,
-                           cudaStream_t s, int zc_override)
+static void launch_fused_t(const Lat &L, const void *fin, void *fout, const float *rho, const float *psi,
+                           const uint8_t *type, cudaStream_t s, int zc_override)
 {
     static bool configured = false;  // the attribute is per function and process
     if (!configured) {
@@ -397,14 +393,14 @@ static void launch_fused_t(const Lat &L, const void *fin, void *fout, const floa
     const int zc = zc_override > 0 ? zc_override : fused_zchunk(L);
     dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
     FusedOfs ofs = fused_offsets(L);
-    k_fused<S><<<grid, NT, Smem<S>::bytes, s>>>(L, (const typename S::T *)fin, (typename S::T *)fout, psi, type,
-                                                 zc, ofs);
+    k_fused<S><<<grid, NT, Smem<S>::bytes, s>>>(L, (const typename S::T *)fin, (typename S::T *)fout, rho, psi,
+                                                 type, zc, ofs);
 }
 
-void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
+void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *rho, const float *psi,
                   const uint8_t *type, cudaStream_t s, int zc_override)
 {
-    LBE_DISPATCH(storage, (launch_fused_t<S>(L, fin, fout, psi, type, s, zc_override)));
+    LBE_DISPATCH(storage, (launch_fused_t<S>(L, fin, fout, rho, psi, type, s, zc_override)));
 }
 
 template <class S>

@@ -168,9 +168,10 @@ void enqueue_step(lbe_ctx *c)
         launch_moments(st, L, fin, c->type, c->rho, c->psi, s);
     } else {
         if (links) cudaMemsetAsync(c->ll.count, 0, sizeof(int), s);
-        launch_bnd_rho(st, L, fin, c->type, c->rho, links ? c->ll : LinkList{nullptr, nullptr, 0}, s);
+        launch_rho(st, L, fin, c->type, c->rho, s);
     }
-    launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, s);
+    launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho,
+                 links ? c->ll : LinkList{nullptr, nullptr, 0}, s);
     if (c->profiling) {
         if (c->ev_used + 2 > c->ev.size()) {
             for (int k = 0; k < 256; k++) {
@@ -184,7 +185,7 @@ void enqueue_step(lbe_ctx *c)
     if (two_pass)
         launch_collide_stream(st, L, fin, fout, c->psi, c->type, s);
     else
-        launch_fused(st, L, fin, fout, c->psi, c->type, s, c->zc_tuned);
+        launch_fused(st, L, fin, fout, c->rho, c->psi, c->type, s, c->zc_tuned);
     if (c->profiling) {
         cudaEventRecord(c->ev[c->ev_used + 1], s);
         c->ev_used += 2;
@@ -496,7 +497,7 @@ lbe_status lbe_read_fields(lbe_ctx *c, double *rho, double *vel, uint8_t *node_t
     const Lat &L = c->L;
     size_t N = (size_t)L.N;
     launch_moments(c->d.storage, L, c->f[c->cur], c->type, c->rho, c->psi, s);
-    launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, s);
+    launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, LinkList{nullptr, nullptr, 0}, s);
     double *dr = nullptr, *dv = nullptr;
     if (rho) CK(c, cudaMallocAsync((void **)&dr, 2 * N * sizeof(double), s));
     if (vel) {
@@ -664,14 +665,14 @@ lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc)
     CK(c, cudaEventCreate(&e0));
     CK(c, cudaEventCreate(&e1));
     void *fin = c->f[c->cur], *fout = c->f[1 - c->cur];
-    launch_bnd_rho(c->d.storage, L, fin, c->type, c->rho, LinkList{nullptr, nullptr, 0}, c->stream);
-    launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, c->stream);
+    launch_rho(c->d.storage, L, fin, c->type, c->rho, c->stream);
+    launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, LinkList{nullptr, nullptr, 0}, c->stream);
     float best = 1e30f;
     int best_zc = fused_zchunk(L);
     for (int zc : cand) {
-        launch_fused(c->d.storage, L, fin, fout, c->psi, c->type, c->stream, zc);  // warm-up
+        launch_fused(c->d.storage, L, fin, fout, c->rho, c->psi, c->type, c->stream, zc);  // warm-up
         cudaEventRecord(e0, c->stream);
-        for (int r = 0; r < 3; r++) launch_fused(c->d.storage, L, fin, fout, c->psi, c->type, c->stream, zc);
+        for (int r = 0; r < 3; r++) launch_fused(c->d.storage, L, fin, fout, c->rho, c->psi, c->type, c->stream, zc);
         cudaEventRecord(e1, c->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) break;
         float ms = 0.f;
@@ -715,7 +716,7 @@ namespace {
 void batch_enqueue_step(lbe_batch *b)
 {
     cudaStream_t s = b->stream;
-    launch_bnd_rho_batch(b->storage, b->idx, b->total_nodes, s);
+    launch_rho_batch(b->storage, b->idx, b->total_nodes, s);
     launch_shell_batch(b->idx, b->total_nodes, s);
     cudaMemsetAsync(b->idx.counter, 0, sizeof(int), s);
     launch_fused_batch(b->storage, b->idx, b->total_tiles, 152 * b->ctas_per_sm, s);

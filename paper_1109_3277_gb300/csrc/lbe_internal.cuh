@@ -45,6 +45,13 @@ struct StF32 {
     static __device__ __forceinline__ void st(T *p, float v, float) { *p = v; }
     static __device__ __forceinline__ float cvt(T v, float) { return v; }
     static __device__ __forceinline__ T enc(float v, float) { return v; }
+    // two consecutive elements (p 8-byte aligned)
+    static __device__ __forceinline__ void ld2(const T *p, float, float &x, float &y)
+    {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        x = v.x;
+        y = v.y;
+    }
 };
 struct StF16 {
     using T = __half;
@@ -53,6 +60,12 @@ struct StF16 {
     static __device__ __forceinline__ void st(T *p, float v, float b) { *p = __float2half_rn(v - b); }
     static __device__ __forceinline__ float cvt(T v, float b) { return b + __half2float(v); }
     static __device__ __forceinline__ T enc(float v, float b) { return __float2half_rn(v - b); }
+    static __device__ __forceinline__ void ld2(const T *p, float b, float &x, float &y)
+    {
+        const __half2 v = __ldg(reinterpret_cast<const __half2 *>(p));
+        x = b + __low2float(v);
+        y = b + __high2float(v);
+    }
 };
 struct StBF16 {
     using T = __nv_bfloat16;
@@ -61,6 +74,12 @@ struct StBF16 {
     static __device__ __forceinline__ void st(T *p, float v, float b) { *p = __float2bfloat16_rn(v - b); }
     static __device__ __forceinline__ float cvt(T v, float b) { return b + __bfloat162float(v); }
     static __device__ __forceinline__ T enc(float v, float b) { return __float2bfloat16_rn(v - b); }
+    static __device__ __forceinline__ void ld2(const T *p, float b, float &x, float &y)
+    {
+        const __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162 *>(p));
+        x = b + __low2float(v);
+        y = b + __high2float(v);
+    }
 };
 
 // Lattice parameters passed by value to every kernel.
@@ -112,10 +131,10 @@ struct Parts {
 
 // What the fused fluid kernel needs for the moving bounce-back (Eq. 4) and
 // the momentum exchange (Eq. 5) of the links it streams.
-// Fluid nodes next to particle nodes, collected each step by the
-// boundary-density kernel: entry (node, mask of the directions i whose
-// neighbour node + c_i is a particle node).  A node enters at most once per
-// step, so cap = N cannot overflow.
+// Particle nodes next to fluid nodes, collected each step by the shell-fill
+// kernel: entry (particle node s, mask of the directions j whose neighbour
+// s + c_j is a fluid node).  A node enters at most once per step, so cap = N
+// cannot overflow.
 struct LinkList {
     uint2 *ent;   // [cap]
     int *count;   // entries this step (reset before the density kernel)
@@ -169,10 +188,9 @@ void launch_init_f(int storage, const Lat &L, const double *rho0, void *f, const
                    cudaStream_t s);
 void launch_moments(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho,
                     float *psi, cudaStream_t s);
-void launch_bnd_rho(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho,
-                    const LinkList &ll, cudaStream_t s);
+void launch_rho(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho, cudaStream_t s);
 void launch_shell(const Lat &L, const float *rho, float *psi, const uint8_t *type,
-                  const uint32_t *owner, const double *drho, cudaStream_t s);
+                  const uint32_t *owner, const double *drho, const LinkList &ll, cudaStream_t s);
 void launch_collide_stream(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
                            const uint8_t *type, cudaStream_t s);
 void launch_fields(int storage, const Lat &L, const void *f, const float *psi, const uint8_t *type,
@@ -184,7 +202,7 @@ void launch_set_f(int storage, const Lat &L, const double *in, void *f, cudaStre
 int mass_blocks();
 
 // ---- batched launchers (one launch steps every box of a batch) -------------
-void launch_bnd_rho_batch(int storage, const BatchIndex &B, int total_nodes, cudaStream_t s);
+void launch_rho_batch(int storage, const BatchIndex &B, int total_nodes, cudaStream_t s);
 void launch_shell_batch(const BatchIndex &B, int total_nodes, cudaStream_t s);
 void launch_fused_batch(int storage, const BatchIndex &B, int total_tiles, int ctas, cudaStream_t s);
 int fused_batch_ctas_per_sm(int storage);
@@ -198,7 +216,7 @@ void launch_link_batch(int storage, const BatchIndex &B, cudaStream_t s);
 void launch_flip_batch(const BatchIndex &B, cudaStream_t s);
 
 // ---- launchers (fused.cu) -------------------------------------------------
-void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
+void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *rho, const float *psi,
                   const uint8_t *type, cudaStream_t s, int zc_override = 0);
 int fused_zchunk(const Lat &L);
 constexpr int FUSED_TX = 32, FUSED_TY = 8;

@@ -315,15 +315,16 @@ __global__ void __launch_bounds__(PT) k_links(Lat L, Parts P, typename S::T *__r
 }
 
 // ------------------------------------------------------------ link nodes
-// For every fluid node y of the step's link list and every direction i
-// whose neighbour x = y + c_i is a particle node: the fluid kernel reflected
-// the post-collision f*_i(y) into slot ī of y; add C = -6 w_i ρ^c(y)
-// (u_surf·c_i) with u_surf = V + ω × r_b at the link midpoint r_b = y +
-// c_i/2 - X (Eq. 4), and give the particle (2 f*_i + C) c_i and r_b × that
-// (Eq. 5).  ρ^c(y) is the density the boundary-density kernel wrote this
-// step.  Force and torque are summed in 64-bit fixed point (2^-40 units):
-// each FP32 link term is rounded once to an integer and integer additions
-// are exact, so the totals do not depend on the order of the links.
+// For every particle node s of the step's link list and every direction j
+// whose neighbour y = s + c_j is a fluid node (the link runs from y along
+// c_i = -c_j into s): the fluid kernel reflected the post-collision
+// f*_i(y) into slot j of y; add C = -6 w_i ρ^c(y) (u_surf·c_i) with u_surf =
+// V + ω × r_b at the link midpoint r_b = s + c_j/2 - X (Eq. 4), and give
+// the particle (2 f*_i + C) c_i and r_b × that (Eq. 5).  ρ^c(y) is the
+// density kernel's, this step.  Force and torque are summed in 64-bit fixed
+// point (2^-40 units): each FP32 link term is rounded once to an integer and
+// integer additions are exact, so the totals do not depend on the order of
+// the links.
 
 __constant__ int k_cx[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
 __constant__ int k_cy[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
@@ -360,8 +361,8 @@ __device__ __forceinline__ void warp_add_fix(int p, const unsigned long long v[6
     for (int k = 0; k < 6; k++) atomicAdd(&fix[6 * p + k], tot[k]);
 }
 
-// One link node (e = (node, direction mask)); valid = false for a lane
-// without an entry (it still takes part in the warp reduction).
+// One particle node (e = (node, mask of fluid neighbours)); valid = false
+// for a lane without an entry (it still takes part in the warp reduction).
 template <class S>
 __device__ __forceinline__ void link_entry(const Lat &L, uint2 e, bool valid, const float *__restrict__ rho,
                                            const uint32_t *__restrict__ owner, const float4 *__restrict__ X32,
@@ -369,73 +370,63 @@ __device__ __forceinline__ void link_entry(const Lat &L, uint2 e, bool valid, co
                                            typename S::T *fout)
 {
     unsigned long long acc[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
-    int pcur = -1;
-    uint32_t pm = valid ? e.y : 0u;
-    const int n = valid ? (int)e.x : 0;
-    const int x = n % L.nx, t = n / L.nx, y = t % L.ny, z = t / L.ny;
-    float rh[2] = {0.f, 0.f};
-    if (pm) {
-        rh[0] = rho[n];
-        rh[1] = rho[(size_t)L.N + n];
-    }
+    uint32_t fm = valid ? e.y : 0u;
+    const int s = valid ? (int)e.x : 0;
+    int p = -1;
     float4 X = make_float4(0.f, 0.f, 0.f, 0.f), V = X, W = X;
-    while (pm) {
-        const int i = __ffs(pm) - 1;
-        pm &= pm - 1;
-        const int cxi = k_cx[i], cyi = k_cy[i], czi = k_cz[i];
-        int xn = x + cxi, yn = y + cyi, zn = z + czi;
-        xn = xn < 0 ? xn + L.nx : (xn >= L.nx ? xn - L.nx : xn);
-        yn = yn < 0 ? yn + L.ny : (yn >= L.ny ? yn - L.ny : yn);
-        zn = zn < 0 ? zn + L.nz : (zn >= L.nz ? zn - L.nz : zn);
-        const int p = (int)owner[xn + L.nx * (yn + L.ny * zn)];
+    if (fm) {
+        p = (int)owner[s];
         if ((unsigned)p >= (unsigned)L.np) {  // a particle node is always owned
             idx_ok(L, p, L.np, 20);
-            continue;
-        }
-        if (p != pcur) {
-            if (pcur >= 0) {  // a second particle at this node: add the first directly
-#pragma unroll
-                for (int k = 0; k < 6; k++) {
-                    atomicAdd(&fix[6 * pcur + k], acc[k]);
-                    acc[k] = 0ull;
-                }
-            }
-            pcur = p;
+            p = -1;
+            fm = 0;
+        } else {
             X = X32[p];
             V = K32[2 * p];
             W = K32[2 * p + 1];
         }
-        float rx = (float)x - X.x, ry = (float)y - X.y, rz = (float)z - X.z;
-        if (rx > 0.5f * L.nx) rx -= L.nx;
-        if (rx < -0.5f * L.nx) rx += L.nx;
-        if (ry > 0.5f * L.ny) ry -= L.ny;
-        if (ry < -0.5f * L.ny) ry += L.ny;
-        if (!L.walls) {
-            if (rz > 0.5f * L.nz) rz -= L.nz;
-            if (rz < -0.5f * L.nz) rz += L.nz;
-        }
-        rx += 0.5f * cxi;
-        ry += 0.5f * cyi;
-        rz += 0.5f * czi;
+    }
+    const int x = s % L.nx, t = s / L.nx, y = t % L.ny, z = t / L.ny;
+    // s - X, nearest image
+    float dx = (float)x - X.x, dy = (float)y - X.y, dz = (float)z - X.z;
+    if (dx > 0.5f * L.nx) dx -= L.nx;
+    if (dx < -0.5f * L.nx) dx += L.nx;
+    if (dy > 0.5f * L.ny) dy -= L.ny;
+    if (dy < -0.5f * L.ny) dy += L.ny;
+    if (!L.walls) {
+        if (dz > 0.5f * L.nz) dz -= L.nz;
+        if (dz < -0.5f * L.nz) dz += L.nz;
+    }
+    while (fm) {
+        const int j = __ffs(fm) - 1;
+        fm &= fm - 1;
+        const int cxj = k_cx[j], cyj = k_cy[j], czj = k_cz[j];
+        int xn = x + cxj, yn = y + cyj, zn = z + czj;
+        xn = xn < 0 ? xn + L.nx : (xn >= L.nx ? xn - L.nx : xn);
+        yn = yn < 0 ? yn + L.ny : (yn >= L.ny ? yn - L.ny : yn);
+        zn = zn < 0 ? zn + L.nz : (zn >= L.nz ? zn - L.nz : zn);
+        const int yf = xn + L.nx * (yn + L.ny * zn);  // the fluid node
+        const float rx = dx + 0.5f * cxj, ry = dy + 0.5f * cyj, rz = dz + 0.5f * czj;
         // surface velocity V + ω × r_b at the link midpoint
         const float usx = __fsub_rn(__fmaf_rn(W.y, rz, V.x), __fmul_rn(W.z, ry));
         const float usy = __fsub_rn(__fmaf_rn(W.z, rx, V.y), __fmul_rn(W.x, rz));
         const float usz = __fsub_rn(__fmaf_rn(W.x, ry, V.z), __fmul_rn(W.y, rx));
-        const float uci = __fadd_rn(__fadd_rn(usx * cxi, usy * cyi), usz * czi);
-        const bool axis = i < 7;
+        // u_surf·c_i with c_i = -c_j
+        const float uci = -__fadd_rn(__fadd_rn(usx * cxj, usy * cyj), usz * czj);
+        const bool axis = j < 7;
         const float w6 = axis ? -6.f / 18.f : -6.f / 36.f;
-        const int io = (i & 1) ? i + 1 : i - 1;
         float a = 0.f;
 #pragma unroll
         for (int c = 0; c < 2; c++) {
             const float base = axis ? L.base[c][1] : L.base[c][7];
-            typename S::T *q = fout + (size_t)(c * Q + io) * (size_t)L.S + n;
+            typename S::T *q = fout + (size_t)(c * Q + j) * (size_t)L.S + yf;
             const float fs = S::ldc(q, base);
-            const float C = __fmul_rn(__fmul_rn(w6, rh[c]), uci);
+            const float C = __fmul_rn(__fmul_rn(w6, __ldg(rho + (size_t)c * L.N + yf)), uci);
             S::st(q, __fadd_rn(fs, C), base);
             a = __fadd_rn(a, __fmaf_rn(2.f, fs, C));
         }
-        const float Fx = a * cxi, Fy = a * cyi, Fz = a * czi;
+        // F = a c_i = -a c_j
+        const float Fx = -a * cxj, Fy = -a * cyj, Fz = -a * czj;
         acc[0] += to_fixed(Fx);
         acc[1] += to_fixed(Fy);
         acc[2] += to_fixed(Fz);
@@ -443,7 +434,7 @@ __device__ __forceinline__ void link_entry(const Lat &L, uint2 e, bool valid, co
         acc[4] += to_fixed(__fsub_rn(__fmul_rn(rz, Fx), __fmul_rn(rx, Fz)));
         acc[5] += to_fixed(__fsub_rn(__fmul_rn(rx, Fy), __fmul_rn(ry, Fx)));
     }
-    warp_add_fix(pcur, acc, fix);
+    warp_add_fix(p, acc, fix);
 }
 
 // Warp-uniform trip count over the entries (every lane takes part in the
