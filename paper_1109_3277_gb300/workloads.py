@@ -196,10 +196,12 @@ def adsorption_box(seed=1110, shape=(32, 32, 48), steps=200):
 
 def spinodal(seed=1111, n=128, steps=2000):
     """n^3 periodic, both components 0.7 + uniform noise in [-0.01, 0.01),
-    g=0.1, τ=1, no particles."""
+    g=0.1, τ=1, no particles.  The 16-bit offset base is each component's
+    initial mean density, so the seeding noise is stored at full relative
+    precision."""
     shape = (n, n, n)
     return Workload(f"spinodal-{n}^3", shape,
-                    dict(walls_z=False, tau=(1.0, 1.0), g_br=0.1, rho_ref=(0.37, 0.37)),
+                    dict(walls_z=False, tau=(1.0, 1.0), g_br=0.1, rho_ref=(0.7, 0.7)),
                     uniform_mixture(shape, 0.7, 0.01, seed), steps)
 
 
