@@ -33,6 +33,8 @@ struct lbe_ctx {
     float4 *x32 = nullptr;
     double *ppart = nullptr;
     Parts P{};
+    Cells cells{};   // pair-force cell list (with the particles)
+    size_t cells_bytes = 0;
     LinkList ll{nullptr, nullptr, 0};  // link nodes of the step (allocated with the first particles)
     // graphs keyed by (cur, ocur)
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -113,7 +115,7 @@ void bind_parts(lbe_ctx *c)
     P.X32 = c->x32;
     P.K32 = c->x32 ? c->x32 + c->cap : nullptr;
     P.ppart = c->ppart;
-    P.nsplit = c->np > 0 ? pair_splits(c->np) : 1;
+    P.nsplit = 1;
 }
 
 void free_all(lbe_ctx *c)
@@ -133,6 +135,8 @@ void free_all(lbe_ctx *c)
     cudaFree(c->pbuf);
     cudaFree(c->x32);
     cudaFree(c->ppart);
+    cudaFree(c->cells.count);
+    cudaFree(c->cells.idx);
     cudaFree(c->ll.ent);
     cudaFree(c->ll.count);
     if (c->L.err) cudaFree(c->L.err);
@@ -199,7 +203,7 @@ void enqueue_step(lbe_ctx *c)
             // the list is empty between steps (batched steps rely on it)
             cudaMemsetAsync(c->ll.count, 0, sizeof(int), s);
         }
-        launch_pairs(L, c->P, c->pair, s);
+        launch_pairs(L, c->P, c->pair, c->cells, s);
         launch_integrate(L, c->P, c->d.particle_mode, s);
         if (c->d.particle_mode != LBE_PARTICLES_STATIC) {
             uint32_t *oo = c->owner[c->ocur], *on = c->owner[1 - c->ocur];
@@ -211,6 +215,53 @@ void enqueue_step(lbe_ctx *c)
         }
     }
     c->cur = 1 - c->cur;
+}
+
+// Cell list for the pair forces: cells of edge >= the largest pair reach
+// (2 max radius + Δc + the prefilter's margin), at least 2 nodes a side.
+lbe_status build_cells(lbe_ctx *c, const std::vector<double> &blk, int cap)
+{
+    double rmax = 0.0;
+    for (int p = 0; p < c->np; p++)
+        rmax = std::fmax(rmax, std::fmax(blk[(size_t)ORP * cap + p], blk[(size_t)ORO * cap + p]));
+    const double reach = 2.0 * rmax + c->pair.lub_cut + 0.1;
+    Cells &C = c->cells;
+    const int dim[3] = {c->L.nx, c->L.ny, c->L.nz};
+    long long ncell = 1;
+    for (int k = 0; k < 3; k++) {
+        int n = (int)std::floor(dim[k] / reach);
+        n = std::max(1, std::min(n, dim[k] / 2));
+        C.n[k] = n;
+        C.inv[k] = (float)((double)n / dim[k]);
+        ncell *= n;
+    }
+    if (C.count) {
+        cudaFree(C.count);
+        cudaFree(C.idx);
+        C.count = C.idx = nullptr;
+        c->bytes -= c->cells_bytes;
+        c->cells_bytes = 0;
+    }
+    // count | start | fill in one buffer, idx | cid in another
+    C.ncell = (int)ncell;
+    const size_t b0 = (size_t)(3 * ncell + 1) * sizeof(int), b1 = (size_t)2 * cap * sizeof(int);
+    cudaError_t e = cudaMalloc((void **)&C.count, b0);
+    if (e != cudaSuccess) {
+        C.count = nullptr;
+        return cuda_fail(c, e, "add_particles: cudaMalloc(cells)");
+    }
+    e = cudaMalloc((void **)&C.idx, b1);
+    if (e != cudaSuccess) {
+        cudaFree(C.count);
+        C.count = C.idx = nullptr;
+        return cuda_fail(c, e, "add_particles: cudaMalloc(cells)");
+    }
+    C.start = C.count + ncell;
+    C.fill = C.start + ncell + 1;
+    C.cid = C.idx + cap;
+    c->cells_bytes = b0 + b1;
+    c->bytes += c->cells_bytes;
+    return LBE_OK;
 }
 
 lbe_status check_async(lbe_ctx *c, const char *where)
@@ -416,13 +467,13 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
         double *npp = nullptr;
         CK(c, cudaMalloc((void **)&nb, blk.size() * sizeof(double)));
         cudaError_t e = cudaMalloc((void **)&nx32, x32.size() * sizeof(float4));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&npp, (size_t)PAIR_SPLIT_MAX * 6 * ncap * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&npp, (size_t)6 * ncap * sizeof(double));
         if (e != cudaSuccess) {
             cudaFree(nb);
             cudaFree(nx32);
             return cuda_fail(c, e, "add_particles: cudaMalloc");
         }
-        const size_t per_cap = PSTRIDE * sizeof(double) + 3 * sizeof(float4) + PAIR_SPLIT_MAX * 6 * sizeof(double);
+        const size_t per_cap = PSTRIDE * sizeof(double) + 3 * sizeof(float4) + 6 * sizeof(double);
         if (c->pbuf) {
             cudaFree(c->pbuf);
             cudaFree(c->x32);
@@ -447,6 +498,8 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
     c->np = np;
     c->L.np = np;
     bind_parts(c);
+    lbe_status cst = build_cells(c, blk, ncap);
+    if (cst != LBE_OK) return cst;
     drop_graphs(c);
     cudaStream_t s = c->stream;
     uint32_t *oo = c->owner[c->ocur], *on = c->owner[1 - c->ocur];
@@ -606,7 +659,7 @@ int32_t lbe_kernels_per_step(const lbe_ctx *c)
     if (!c) return 0;
     int k = 3;  // densities (boundary or all), shell fill, fused fluid (or collide+stream)
     if (c->np > 0) {
-        k += 3;  // links, pairs, integrate
+        k += 6;  // links, pair cells (count, prefix, fill), pairs, integrate
         if (c->d.particle_mode != LBE_PARTICLES_STATIC) k += 3;  // claim, transition, reset
     }
     return k;
@@ -627,7 +680,8 @@ size_t lbe_footprint(const lbe_lattice_desc *d, int32_t nparticles)
     b += 2 * N * sizeof(double);                                  // initial densities (transient)
     if (nparticles > 0) {
         const size_t cap = nparticles < 64 ? 64 : (size_t)nparticles + nparticles / 4;
-        b += cap * (PSTRIDE * sizeof(double) + 3 * sizeof(float4) + PAIR_SPLIT_MAX * 6 * sizeof(double));
+        b += cap * (PSTRIDE * sizeof(double) + 3 * sizeof(float4) + 6 * sizeof(double) + 2 * sizeof(int));
+        b += (3 * (N / 8) + 1) * sizeof(int);  // cells (at least 2 nodes a side)
         b += N * sizeof(uint2) + sizeof(int);  // link list
     }
     return b;

@@ -129,8 +129,6 @@ struct Parts {
     float4 *K32;                    // FP32 velocity [2p] and ω [2p+1] for the fused links
 };
 
-// What the fused fluid kernel needs for the moving bounce-back (Eq. 4) and
-// the momentum exchange (Eq. 5) of the links it streams.
 // Particle nodes next to fluid nodes, collected each step by the shell-fill
 // kernel: entry (particle node s, mask of the directions j whose neighbour
 // s + c_j is a fluid node).  A node enters at most once per step, so cap = N
@@ -142,6 +140,20 @@ struct LinkList {
 };
 
 constexpr double FIXED_UNIT = 1.0 / 1099511627776.0;  // 2^-40
+
+// Cell list of the particles for the pair forces: cubic-ish cells of edge
+// >= the largest pair reach, so a particle's partners lie in its own cell
+// and the 26 around it.
+struct Cells {
+    int n[3];          // cells per axis
+    float inv[3];      // cells per lattice unit
+    int ncell;
+    int *count;        // [ncell] particles per cell
+    int *start;        // [ncell + 1] exclusive prefix
+    int *fill;         // [ncell] fill cursor
+    int *idx;          // [cap] particle indices by cell
+    int *cid;          // [cap] cell of each particle
+};
 
 // Offsets of the population arrays of a lattice: pop[c*Q+i] = (c*Q+i)*S and
 // push[c*Q+i] = pop[c*Q+i] + (cx + cy*nx + cz*nx*ny), so the address of a
@@ -240,9 +252,7 @@ void launch_links(int storage, const Lat &L, const Parts &P, void *fnew, const f
                   const uint8_t *type, const uint32_t *owner, cudaStream_t s);
 void launch_link(int storage, const Lat &L, const LinkList &ll, const float *rho, const uint32_t *owner,
                  const Parts &P, void *fout, cudaStream_t s);
-void launch_pairs(const Lat &L, const Parts &P, const Pair &pp, cudaStream_t s);
-constexpr int PAIR_SPLIT_MAX = 32;
-int pair_splits(int n);
+void launch_pairs(const Lat &L, const Parts &P, const Pair &pp, const Cells &C, cudaStream_t s);
 void launch_integrate(const Lat &L, const Parts &P, int mode, cudaStream_t s);
 void launch_claim(const Lat &L, const Parts &P, int first, uint32_t *owner_new, cudaStream_t s);
 void launch_transition(int storage, const Lat &L, const Parts &P, void *f, uint8_t *type,

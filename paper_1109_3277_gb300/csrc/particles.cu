@@ -326,10 +326,6 @@ __global__ void __launch_bounds__(PT) k_links(Lat L, Parts P, typename S::T *__r
 // integer additions are exact, so the totals do not depend on the order of
 // the links.
 
-__constant__ int k_cx[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
-__constant__ int k_cy[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
-__constant__ int k_cz[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
-
 // FP32 value to 64-bit fixed point in units of 2^-40 (two's complement in an
 // unsigned word, so that wrap-around addition is exact); |v| is clamped to
 // 2^22, far beyond any link term.
@@ -397,28 +393,33 @@ __device__ __forceinline__ void link_entry(const Lat &L, uint2 e, bool valid, co
         if (dz > 0.5f * L.nz) dz -= L.nz;
         if (dz < -0.5f * L.nz) dz += L.nz;
     }
-    while (fm) {
-        const int j = __ffs(fm) - 1;
-        fm &= fm - 1;
-        const int cxj = k_cx[j], cyj = k_cy[j], czj = k_cz[j];
-        int xn = x + cxj, yn = y + cyj, zn = z + czj;
-        xn = xn < 0 ? xn + L.nx : (xn >= L.nx ? xn - L.nx : xn);
-        yn = yn < 0 ? yn + L.ny : (yn >= L.ny ? yn - L.ny : yn);
-        zn = zn < 0 ? zn + L.nz : (zn >= L.nz ? zn - L.nz : zn);
-        const int yf = xn + L.nx * (yn + L.ny * zn);  // the fluid node
-        const float rx = dx + 0.5f * cxj, ry = dy + 0.5f * cyj, rz = dz + 0.5f * czj;
+    // Directions in lockstep over the warp: neighbouring entries (particle
+    // nodes along x) then touch neighbouring elements of the same slot
+    // array.  Each direction's offsets are compile-time constants.
+    const bool edge = x == 0 || x == L.nx - 1 || y == 0 || y == L.ny - 1 || z == 0 || z == L.nz - 1;
+#pragma unroll
+    for (int j = 1; j < Q; j++) {
+        if (!((fm >> j) & 1u)) continue;
+        int yf = s + cx(j) + L.nx * (cy(j) + L.ny * cz(j));  // the fluid node
+        if (edge) {
+            int xn = x + cx(j), yn = y + cy(j), zn = z + cz(j);
+            xn = xn < 0 ? xn + L.nx : (xn >= L.nx ? xn - L.nx : xn);
+            yn = yn < 0 ? yn + L.ny : (yn >= L.ny ? yn - L.ny : yn);
+            zn = zn < 0 ? zn + L.nz : (zn >= L.nz ? zn - L.nz : zn);
+            yf = xn + L.nx * (yn + L.ny * zn);
+        }
+        const float rx = dx + 0.5f * cx(j), ry = dy + 0.5f * cy(j), rz = dz + 0.5f * cz(j);
         // surface velocity V + ω × r_b at the link midpoint
         const float usx = __fsub_rn(__fmaf_rn(W.y, rz, V.x), __fmul_rn(W.z, ry));
         const float usy = __fsub_rn(__fmaf_rn(W.z, rx, V.y), __fmul_rn(W.x, rz));
         const float usz = __fsub_rn(__fmaf_rn(W.x, ry, V.z), __fmul_rn(W.y, rx));
         // u_surf·c_i with c_i = -c_j
-        const float uci = -__fadd_rn(__fadd_rn(usx * cxj, usy * cyj), usz * czj);
-        const bool axis = j < 7;
-        const float w6 = axis ? -6.f / 18.f : -6.f / 36.f;
+        const float uci = -__fadd_rn(__fadd_rn(usx * cx(j), usy * cy(j)), usz * cz(j));
+        const float w6 = j < 7 ? -6.f / 18.f : -6.f / 36.f;
         float a = 0.f;
 #pragma unroll
         for (int c = 0; c < 2; c++) {
-            const float base = axis ? L.base[c][1] : L.base[c][7];
+            const float base = L.base[c][j];
             typename S::T *q = fout + (size_t)(c * Q + j) * (size_t)L.S + yf;
             const float fs = S::ldc(q, base);
             const float C = __fmul_rn(__fmul_rn(w6, __ldg(rho + (size_t)c * L.N + yf)), uci);
@@ -426,7 +427,7 @@ __device__ __forceinline__ void link_entry(const Lat &L, uint2 e, bool valid, co
             a = __fadd_rn(a, __fmaf_rn(2.f, fs, C));
         }
         // F = a c_i = -a c_j
-        const float Fx = -a * cxj, Fy = -a * cyj, Fz = -a * czj;
+        const float Fx = -a * cx(j), Fy = -a * cy(j), Fz = -a * cz(j);
         acc[0] += to_fixed(Fx);
         acc[1] += to_fixed(Fy);
         acc[2] += to_fixed(Fz);
@@ -530,13 +531,11 @@ __device__ double hertz_bp(double K, double rp, double ro, const double r[3], co
     return sigma;
 }
 
-// One thread per particle i sums the Hertz and lubrication (Eq. 9 with 2R
-// -> σ, R^2 -> (σ/2)^2, only for gaps 0 < r - σ < Δc, opposing the normal
-// approach) contributions of every other particle in index order.  The
-// other particles stream through shared memory as FP32 (x, y, z, reach)
-// tiles; a pair is evaluated in FP64 only when the FP32 distance is within
-// reach_i + reach_j + Δc (+0.05 for the FP32 error).
-constexpr int PAIR_T = 128;
+// The Hertz and lubrication (Eq. 9 with 2R -> σ, R^2 -> (σ/2)^2, only for
+// gaps 0 < r - σ < Δc, opposing the normal approach) contribution of
+// partner j to particle i.  A pair is evaluated in FP64 only when the FP32
+// distance of the centres is within reach_i + reach_j + Δc (+0.05 for the
+// FP32 error).
 
 __device__ void pair_term(const Lat &L, const Parts &P, const Pair &pp, int i, int j, const double oi[3],
                           double F[3], double T[3])
@@ -580,49 +579,143 @@ __device__ __forceinline__ bool near_pair(float4 me, float4 o, const float nl[3]
     return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, dz * dz)) <= reach * reach;
 }
 
-// The j range is split over gridDim.y CTAs per i tile (enough CTAs to fill
-// the GPU); each split writes its partial sums, which k_integrate adds in
-// split order.
-__global__ void __launch_bounds__(PAIR_T) k_pairs(Lat L, Parts P, Pair pp)
+// ---------------------------------------------------------------- cells
+// Per step: count the particles of each cell, exclusive prefix over the
+// cells (one CTA), place each particle's index, then each particle gathers
+// the candidates of the 27 cells around its own (each cell once when an
+// axis has fewer than 3 cells), keeps those the FP32 prefilter passes, and
+// sums the pair terms in increasing partner index: the same terms in the
+// same order as a loop over all partners, so the sums do not depend on the
+// order the cells were filled in.
+
+__device__ __forceinline__ int cell_axis(float x, float n, float inv, int nc, bool periodic)
 {
-    __shared__ float4 tile[PAIR_T];
-    int i = blockIdx.x * PAIR_T + threadIdx.x;
-    bool act = i < P.n;
-    float4 me = act ? P.X32[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    double oi[3] = {0, 0, 0};
-    if (act) {
-        double Ri[3][3];
-        rotmat(P.q + 4 * i, Ri);
-        oi[0] = Ri[0][0];
-        oi[1] = Ri[1][0];
-        oi[2] = Ri[2][0];
+    if (periodic) x -= n * floorf(x / n);
+    int c = (int)(x * inv);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+__global__ void k_cell_count(Lat L, Parts P, Cells C)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const float4 x = P.X32[i];
+    const int cx_ = cell_axis(x.x, (float)L.nx, C.inv[0], C.n[0], true);
+    const int cy_ = cell_axis(x.y, (float)L.ny, C.inv[1], C.n[1], true);
+    const int cz_ = cell_axis(x.z, (float)L.nz, C.inv[2], C.n[2], !L.walls);
+    const int c = cx_ + C.n[0] * (cy_ + C.n[1] * cz_);
+    C.cid[i] = c;
+    atomicAdd(&C.count[c], 1);
+}
+
+// Exclusive prefix of the cell counts; one CTA of 1024 threads, each over a
+// contiguous run of cells.
+__global__ void __launch_bounds__(1024) k_cell_scan(Cells C)
+{
+    __shared__ int part[1024];
+    const int t = threadIdx.x;
+    const int per = (C.ncell + 1023) / 1024;
+    const int c0 = min(t * per, C.ncell), c1 = min(c0 + per, C.ncell);
+    int s = 0;
+    for (int c = c0; c < c1; c++) s += C.count[c];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan of the run sums
+        const int v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
     }
-    float nl[3] = {(float)L.nx, (float)L.ny, (float)L.nz};
-    float inv[3] = {1.f / nl[0], 1.f / nl[1], 1.f / nl[2]};
-    bool per_z = !L.walls;
-    float extra = (float)pp.lub_cut + 0.05f;
+    int run = t > 0 ? part[t - 1] : 0;
+    for (int c = c0; c < c1; c++) {
+        C.start[c] = run;
+        C.fill[c] = 0;
+        run += C.count[c];
+    }
+    if (t == 1023) C.start[C.ncell] = part[1023];
+}
+
+__global__ void k_cell_fill(Parts P, Cells C)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const int c = C.cid[i];
+    C.idx[C.start[c] + atomicAdd(&C.fill[c], 1)] = i;
+}
+
+constexpr int CAND_MAX = 96;  // candidates held per particle; beyond that a full scan
+
+__global__ void __launch_bounds__(128) k_pairs(Lat L, Parts P, Pair pp, Cells C)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.n) return;
+    const float4 me = P.X32[i];
+    const float nl[3] = {(float)L.nx, (float)L.ny, (float)L.nz};
+    const float inv[3] = {1.f / nl[0], 1.f / nl[1], 1.f / nl[2]};
+    const bool per_z = !L.walls;
+    const float extra = (float)pp.lub_cut + 0.05f;
+    int cand[CAND_MAX];
+    int nc = 0;
+    bool overflow = false;
+    const int c0 = C.cid[i];
+    const int ci[3] = {c0 % C.n[0], (c0 / C.n[0]) % C.n[1], c0 / (C.n[0] * C.n[1])};
+    int lo[3], hi[3];
+    for (int k = 0; k < 3; k++) {
+        if (C.n[k] < 3) {  // every cell of the axis once
+            lo[k] = 0;
+            hi[k] = C.n[k] - 1;
+        } else {
+            lo[k] = ci[k] - 1;
+            hi[k] = ci[k] + 1;
+        }
+    }
+    for (int dz = lo[2]; dz <= hi[2]; dz++) {
+        int z = dz;
+        if (C.n[2] >= 3) {
+            if (per_z)
+                z = (z + C.n[2]) % C.n[2];
+            else if (z < 0 || z >= C.n[2])
+                continue;
+        }
+        for (int dy = lo[1]; dy <= hi[1]; dy++) {
+            const int y = C.n[1] >= 3 ? (dy + C.n[1]) % C.n[1] : dy;
+            for (int dx = lo[0]; dx <= hi[0]; dx++) {
+                const int x = C.n[0] >= 3 ? (dx + C.n[0]) % C.n[0] : dx;
+                const int c = x + C.n[0] * (y + C.n[1] * z);
+                for (int k = C.start[c]; k < C.start[c + 1]; k++) {
+                    const int j = C.idx[k];
+                    if (j == i || !near_pair(me, P.X32[j], nl, inv, per_z, extra)) continue;
+                    if (nc < CAND_MAX)
+                        cand[nc++] = j;
+                    else
+                        overflow = true;
+                }
+            }
+        }
+    }
+    double Ri[3][3];
+    rotmat(P.q + 4 * i, Ri);
+    const double oi[3] = {Ri[0][0], Ri[1][0], Ri[2][0]};
     double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-    const int tiles = (P.n + PAIR_T - 1) / PAIR_T;
-    const int per = (tiles + gridDim.y - 1) / gridDim.y;
-    const int t0 = blockIdx.y * per, t1 = min(t0 + per, tiles);
-    for (int tt = t0; tt < t1; tt++) {
-        const int base = tt * PAIR_T;
-        int j = base + threadIdx.x;
-        tile[threadIdx.x] = j < P.n ? P.X32[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        __syncthreads();
-        if (act) {
-            int lim = min(PAIR_T, P.n - base);
-            for (int t = 0; t < lim; t++)
-                if (near_pair(me, tile[t], nl, inv, per_z, extra) && base + t != i)
-                    pair_term(L, P, pp, i, base + t, oi, F, T);
+    if (!overflow) {
+        for (int a = 1; a < nc; a++) {  // insertion sort: increasing partner index
+            const int v = cand[a];
+            int b = a - 1;
+            while (b >= 0 && cand[b] > v) {
+                cand[b + 1] = cand[b];
+                b--;
+            }
+            cand[b + 1] = v;
         }
-        __syncthreads();
+        for (int a = 0; a < nc; a++) pair_term(L, P, pp, i, cand[a], oi, F, T);
+    } else {  // very dense: every partner in index order
+        for (int j = 0; j < P.n; j++)
+            if (j != i && near_pair(me, P.X32[j], nl, inv, per_z, extra)) pair_term(L, P, pp, i, j, oi, F, T);
     }
-    if (act)
-        for (int k = 0; k < 3; k++) {
-            P.ppart[((size_t)blockIdx.y * 6 + k) * P.n + i] = F[k];
-            P.ppart[((size_t)blockIdx.y * 6 + 3 + k) * P.n + i] = T[k];
-        }
+    for (int k = 0; k < 3; k++) {
+        P.ppart[(size_t)k * P.n + i] = F[k];
+        P.ppart[(size_t)(3 + k) * P.n + i] = T[k];
+    }
 }
 
 // ------------------------------------------------------------ integrate
@@ -1017,10 +1110,9 @@ __global__ void k_integrate_batch(BatchIndex B, int total)
     integrate_body(bx.L, bx.P, bx.mode, g - B.part0[b]);
 }
 
-// Pair forces within each box: one thread per particle runs over the same
-// j splits as k_pairs (split s covers the tiles [s*per, (s+1)*per) of
-// PAIR_T particles) and writes each split's sum, so k_integrate adds the
-// same terms in the same order as for the box stepped alone.
+// Pair forces within each box: one thread per particle over its box's
+// particles in index order (the same terms in the same order as the cell
+// list of a lattice stepped alone).
 __global__ void k_pairs_batch(BatchIndex B, int total)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1038,17 +1130,12 @@ __global__ void k_pairs_batch(BatchIndex B, int total)
     const float inv[3] = {1.f / nl[0], 1.f / nl[1], 1.f / nl[2]};
     const bool per_z = !L.walls;
     const float extra = (float)bx.pair.lub_cut + 0.05f;
-    const int tiles = (P.n + PAIR_T - 1) / PAIR_T;
-    const int per = (tiles + P.nsplit - 1) / P.nsplit;
-    for (int sp = 0; sp < P.nsplit; sp++) {
-        double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
-        const int j0 = min(sp * per * PAIR_T, P.n), j1 = min((sp + 1) * per * PAIR_T, P.n);
-        for (int j = j0; j < j1; j++)
-            if (near_pair(me, P.X32[j], nl, inv, per_z, extra) && j != i) pair_term(L, P, bx.pair, i, j, oi, F, T);
-        for (int k = 0; k < 3; k++) {
-            P.ppart[((size_t)sp * 6 + k) * P.n + i] = F[k];
-            P.ppart[((size_t)sp * 6 + 3 + k) * P.n + i] = T[k];
-        }
+    double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+    for (int j = 0; j < P.n; j++)
+        if (j != i && near_pair(me, P.X32[j], nl, inv, per_z, extra)) pair_term(L, P, bx.pair, i, j, oi, F, T);
+    for (int k = 0; k < 3; k++) {
+        P.ppart[(size_t)k * P.n + i] = F[k];
+        P.ppart[(size_t)(3 + k) * P.n + i] = T[k];
     }
 }
 
@@ -1140,21 +1227,15 @@ void launch_links(int storage, const Lat &L, const Parts &P, void *fnew, const f
     LBE_DISPATCH(storage, (k_links<S><<<P.n, PT, 0, s>>>(L, P, (typename S::T *)fnew, rho, type, owner)));
 }
 
-int pair_splits(int n)
-{
-    // about four CTAs per SM of a 152-SM GPU, at most PAIR_SPLIT_MAX splits
-    int tiles = (n + PAIR_T - 1) / PAIR_T;
-    int sp = (4 * 152 + tiles - 1) / tiles;
-    if (sp > tiles) sp = tiles;
-    if (sp > PAIR_SPLIT_MAX) sp = PAIR_SPLIT_MAX;
-    return sp < 1 ? 1 : sp;
-}
-
-void launch_pairs(const Lat &L, const Parts &P, const Pair &pp, cudaStream_t s)
+void launch_pairs(const Lat &L, const Parts &P, const Pair &pp, const Cells &C, cudaStream_t s)
 {
     if (P.n == 0) return;
-    dim3 grid((P.n + PAIR_T - 1) / PAIR_T, P.nsplit);
-    k_pairs<<<grid, PAIR_T, 0, s>>>(L, P, pp);
+    const int b = (P.n + 127) / 128;
+    cudaMemsetAsync(C.count, 0, (size_t)C.ncell * sizeof(int), s);
+    k_cell_count<<<b, 128, 0, s>>>(L, P, C);
+    k_cell_scan<<<1, 1024, 0, s>>>(C);
+    k_cell_fill<<<b, 128, 0, s>>>(P, C);
+    k_pairs<<<b, 128, 0, s>>>(L, P, pp, C);
 }
 
 void launch_integrate(const Lat &L, const Parts &P, int mode, cudaStream_t s)
