@@ -246,7 +246,8 @@ LBE_API lbe_status lbe_batch_first_quat(lbe_batch *b, double *quat_out);
  * Host buffers are the caller's; submit copies its inputs.
  * lbe_server_submit: LBE_ENOMEM if the request alone exceeds the budget.
  * lbe_server_poll: *done = 1 once the request finished; a failed request
- *   returns its error status.  LBE_EINVAL for an unknown id.
+ *   returns its error status (LBE_ENUMERIC if its particle state is not
+ *   finite at the end: the run diverged).  LBE_EINVAL for an unknown id.
  * lbe_server_wait: block until the request finished or timeout_ms passed
  *   (LBE_ETIMEOUT).
  * lbe_server_timing: seconds from submission to admission and to the end

@@ -1,23 +1,26 @@
-// Fused fluid step (§2 of Günther et al., arXiv:1109.3277): ψ = 1 - exp(-ρ)
-// from the populations, the Shan–Chen force (Eq. 3), the shifted-velocity
-// BGK collision (Eq. 2) and push streaming (Eq. 1) with halfway bounce-back,
-// in one pass over the populations.
+// Fused fluid step (§2 of Günther et al., arXiv:1109.3277): the Shan–Chen
+// force (Eq. 3), the shifted-velocity BGK collision (Eq. 2) and push
+// streaming (Eq. 1) with halfway bounce-back, in one pass over the
+// populations.
 //
-// A CTA owns a TX x TY column of nodes and walks a chunk of z planes.  For
-// every plane it computes ρ and ψ of the tile plus a one-node halo into a
-// three-plane ring in shared memory (solid nodes take the shell ψ written by
-// the shell-fill kernel), together with the moments of its own nodes.  The
-// own nodes' populations are read from HBM once, in that density pass, and
-// staged in shared memory (two plane buffers) for the collision one plane
-// later; the force at a node reads its 18 neighbours' ψ from shared memory.
-// The halo densities re-read neighbouring tiles' populations, which their
-// own CTAs are streaming through L2 at the same time.
+// A CTA owns a TX x TY column of nodes and walks a chunk of z planes.  The
+// populations of its nodes in a plane are staged in shared memory, two
+// planes deep: while the warps collide plane z, the next plane is on its way
+// into the other stage, as one TMA tensor copy (a 32 x 8 x 38-slot box of
+// the population array, completion on an mbarrier) where the lattice's row
+// pitch allows it, else by per-thread loads.  ψ = 1 - exp(-ρ) of the tile
+// and a one-node halo comes from the density kernel's ρ (fluid nodes) or the
+// shell fill's ψ (solid nodes), into a three-plane ring; the force at a
+// node reads its 18 neighbours' ψ from the ring.  Moments, force, collision
+// and the stores of one node run in one thread.
 //
 // Populations streaming into a wall or particle node are reflected into the
 // opposite slot of their own node (halfway bounce-back).  For particle
 // nodes the moving-boundary term and the momentum exchange are added
-// afterwards by the link kernel, over the list of fluid nodes next to
-// particle nodes that the boundary-density kernel collects.
+// afterwards by the link kernel.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "lbe_internal.cuh"
 
 namespace lbe {
@@ -27,33 +30,87 @@ namespace {
 constexpr int TX = 32, TY = 8, NT = TX * TY;
 constexpr int HX = TX + 2, HY = TY + 2, HN = HX * HY, NHALO = HN - NT;
 
-template <class S>
-__device__ __forceinline__ const typename S::T *cslot(const typename S::T *f, const Lat &L, int c, int i)
-{
-    return f + (size_t)(c * Q + i) * (size_t)L.S;
-}
-template <class S>
-__device__ __forceinline__ typename S::T *wslot(typename S::T *f, const Lat &L, int c, int i)
-{
-    return f + (size_t)(c * Q + i) * (size_t)L.S;
-}
-
 __device__ __forceinline__ int wrapc(int v, int n)
 {
     v %= n;
     return v < 0 ? v + n : v;
 }
 
-
-// Dynamic shared memory layout (bytes).
+// Dynamic shared memory layout (bytes from a 128-byte aligned base).
 template <class S>
 struct Smem {
-    static constexpr size_t fbuf = 0;                                          // T [2][2Q][NT]
-    static constexpr size_t sps = fbuf + 2 * 2 * Q * NT * sizeof(typename S::T);  // float2 [3][HN] (ψ_r, ψ_b)
-    static constexpr size_t smo = sps + 3 * HN * sizeof(float2);                // float [2][5][NT]
-    static constexpr size_t sty = smo + 2 * 5 * NT * sizeof(float);            // uint8 [3][HN]
-    static constexpr size_t bytes = sty + 3 * HN;
+    static constexpr size_t plane = 2 * Q * NT * sizeof(typename S::T);  // one staged plane
+    static constexpr size_t stage = 0;                                   // T [2][2Q][NT]
+    static constexpr size_t sps = stage + 2 * plane;                     // float2 [3][HN] (ψ_r, ψ_b)
+    static constexpr size_t sty = sps + 3 * HN * sizeof(float2);         // uint8 [3][HN]
+    static constexpr size_t bar = (sty + 3 * HN + 15) / 16 * 16;          // uint64 [2] mbarriers
+    static constexpr size_t bytes = bar + 2 * sizeof(unsigned long long) + 128;  // + alignment slack
 };
+
+__device__ __forceinline__ unsigned char *align128(unsigned char *p)
+{
+    return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 127) & ~uintptr_t(127));
+}
+
+// ---- TMA and mbarrier (PTX) -------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_inval(unsigned long long *b)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
+// make barrier initialisation visible to the asynchronous (TMA) proxy
+__device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// order this thread's earlier shared-memory accesses before later TMA writes
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with this parity; false if it has not completed
+// within the iteration limit (each try may suspend the thread for a while).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity)
+{
+    for (int k = 0; k < (1 << 22); k++)
+        if (mbar_try_wait(b, parity)) return true;
+    return false;
+}
+
+// One plane of the tile: the box (x0, y0, z, slot 0) of size 32 x 8 x 1 x 38
+// of the 4D population tensor into shared memory, completing on b.
+__device__ __forceinline__ void tma_plane(void *dst, const CUtensorMap *map, int x0, int y0, int z,
+                                          unsigned long long *b)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x0), "r"(y0), "r"(z), "r"(0), "r"(smem_u32(b))
+        : "memory");
+}
 
 // ---- node arithmetic ------------------------------------------------------
 // Every product or sum that rounds is written with a round-to-nearest
@@ -86,18 +143,22 @@ __device__ __forceinline__ void feq_parts(float w, float r, float cu, float uu15
 // BGK relaxation f + (f^eq - f)/τ.
 __device__ __forceinline__ float relax(float f, float feq, float it) { return __fmaf_rn(__fsub_rn(feq, f), it, f); }
 
-// One tile (column bx, by, z chunk bz) of one lattice.
-template <class S>
-__device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__restrict__ fin,
+// One tile (column bx, by, z chunk bz) of one lattice.  TMA: the planes
+// arrive as tensor copies described by *tmap; otherwise each thread loads
+// its node's populations.  Returns false if a copy never completed (the
+// lattice's status word records it).
+template <class S, bool TMA>
+__device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__restrict__ fin,
                                            typename S::T *__restrict__ fout, const float *__restrict__ rho,
                                            const float *__restrict__ psi, const uint8_t *__restrict__ type, int zc,
-                                           const FusedOfs &ofs, int bx, int by, int bz, unsigned char *smem)
+                                           const FusedOfs &ofs, const CUtensorMap *tmap, int bx, int by, int bz,
+                                           unsigned char *smem)
 {
     using T = typename S::T;
-    T *fbuf = reinterpret_cast<T *>(smem + Smem<S>::fbuf);          // [parity][c*Q+i][tid]
+    T *stage = reinterpret_cast<T *>(smem + Smem<S>::stage);        // [stage][c*Q+i][tid]
     float2 *sps = reinterpret_cast<float2 *>(smem + Smem<S>::sps);  // [slot][e]
-    float *smo = reinterpret_cast<float *>(smem + Smem<S>::smo);    // [parity][k][tid]
     uint8_t *sty = smem + Smem<S>::sty;                             // [slot][e]
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + Smem<S>::bar);
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int x0 = bx * TX, y0 = by * TY;
     const int zb = bz * zc, ze = min(zb + zc, L.nz);
@@ -131,9 +192,10 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
     }
     const int own2 = gx + L.nx * gy;
 
-    // ρ and ψ of plane zz (tile + halo) into the ring; for own nodes also
-    // the moments and, when own_pops, the raw populations (plane parity).
-    auto load_plane = [&](int zz, bool own_pops) {
+    // ψ and node type of plane zz (tile + halo) into the ring: 1 - exp(-ρ)
+    // from the density kernel on fluid nodes, the shell fill's ψ on solid
+    // nodes, walls beyond the lattice's z walls.
+    auto load_ring = [&](int zz) {
         const int slot = (zz + 3) % 3;
         bool zin = true;
         int gz = zz;
@@ -151,49 +213,8 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
                 const int n = own2 + nxy * gz;
                 t = type[n];
                 if (t == FLUID) {
-                    const int par = zz & 1;
-                    T *fb = fbuf + par * 2 * Q * NT + tid;
-                    const T *src = fin + n;
-                    float r[2], j[2][3];
-#pragma unroll
-                    for (int c = 0; c < 2; c++) {
-                        float v[Q];
-#pragma unroll
-                        for (int i = 0; i < Q; i++) {
-                            const T raw = __ldg(src + ofs.pop[c * Q + i]);
-                            if (own_pops) fb[(c * Q + i) * NT] = raw;
-                            v[i] = S::cvt(raw, L.base[c][i]);
-                        }
-                        float a = v[0];
-#pragma unroll
-                        for (int i = 1; i < Q; i++) a += v[i];
-                        r[c] = a;
-                        // opposite pairs (i, i+1): c_{i+1} = -c_i
-                        float jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-                        for (int i = 1; i < Q; i += 2) {
-                            const float d = v[i] - v[i + 1];
-                            if (cx(i)) jx += cx(i) * d;
-                            if (cy(i)) jy += cy(i) * d;
-                            if (cz(i)) jz += cz(i) * d;
-                        }
-                        j[c][0] = jx;
-                        j[c][1] = jy;
-                        j[c][2] = jz;
-                    }
-                    p0 = 1.f - expf(-r[0]);
-                    p1 = 1.f - expf(-r[1]);
-                    if (own_pops) {
-                        float *mo = smo + par * 5 * NT + tid;
-                        // shifted velocity u' = Σ_c j^c/τ_c / Σ_c ρ^c/τ_c
-                        const float den = __fmaf_rn(r[1], L.itau[1], __fmul_rn(r[0], L.itau[0]));
-                        const float iden = den > 0.f ? 1.f / den : 0.f;
-                        mo[0] = r[0];
-                        mo[NT] = r[1];
-#pragma unroll
-                        for (int k = 0; k < 3; k++)
-                            mo[(2 + k) * NT] = __fmul_rn(__fmaf_rn(j[1][k], L.itau[1], __fmul_rn(j[0][k], L.itau[0])), iden);
-                    }
+                    p0 = 1.f - expf(-__ldg(rho + n));
+                    p1 = 1.f - expf(-__ldg(rho + (size_t)L.N + n));
                 } else {
                     p0 = psi[n];
                     p1 = psi[(size_t)L.N + n];
@@ -208,35 +229,99 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
             if (zin) {
                 const int n = hn2 + nxy * gz;
                 t = type[n];
-                if (t == FLUID) {
-                    // the density kernel's ρ: the same sum as for own nodes
+                if (t == FLUID)
                     p = 1.f - expf(-__ldg(rho + (size_t)hc * L.N + n));
-                } else {
+                else
                     p = psi[(size_t)hc * L.N + n];
-                }
             }
             reinterpret_cast<float *>(ps + he)[hc] = p;
             if (hc == 0) ts[he] = t;
         }
     };
 
-    load_plane(zb - 1, false);
-    load_plane(zb, true);
-    const bool xy_inner = gx >= 1 && gx <= L.nx - 2 && gy >= 1 && gy <= L.ny - 2;
-    for (int z = zb; z < ze; z++) {
-        load_plane(z + 1, z + 1 < ze);
+    // Populations of plane zz into stage zz & 1 (after the barrier that
+    // ended the collision that last read that stage).
+    auto fill = [&](int zz) {
+        T *st = stage + (zz & 1) * 2 * Q * NT;
+        if (TMA) {
+            if (tid == 0) {
+                fence_proxy_async();
+                mbar_expect_tx(&bar[zz & 1], (unsigned)Smem<S>::plane);
+                tma_plane(st, tmap, x0, y0, zz, &bar[zz & 1]);
+            }
+        } else if (active) {
+            const int n = own2 + nxy * zz;
+            if (type[n] == FLUID) {
+                const T *src = fin + n;
+#pragma unroll
+                for (int ci = 0; ci < 2 * Q; ci++) st[ci * NT + tid] = __ldg(src + ofs.pop[ci]);
+            }
+        }
+    };
+
+    if (TMA) {
+        if (tid == 0) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            fence_barrier_init();
+        }
         __syncthreads();
+    }
+    fill(zb);
+    load_ring(zb - 1);
+    load_ring(zb);
+    const bool xy_inner = gx >= 1 && gx <= L.nx - 2 && gy >= 1 && gy <= L.ny - 2;
+    bool ok = true;
+    for (int z = zb; z < ze; z++) {
+        if (z + 1 < ze) fill(z + 1);
+        load_ring(z + 1);
+        bool late = false;
+        if (TMA) late = !mbar_wait(&bar[z & 1], ((z - zb) >> 1) & 1);
+        if (__syncthreads_or(late)) {
+            ok = false;
+            break;
+        }
         // ring slots of planes z-1, z, z+1
         const float2 *pl[3] = {sps + ((z + 2) % 3) * HN, sps + (z % 3) * HN, sps + ((z + 1) % 3) * HN};
         const uint8_t *tl[3] = {sty + ((z + 2) % 3) * HN, sty + (z % 3) * HN, sty + ((z + 1) % 3) * HN};
         if (active && tl[1][ec] == FLUID) {
             const int n = own2 + nxy * z;
             const bool inner = xy_inner && z >= 1 && z <= L.nz - 2;
-            const int par = z & 1;
-            const float *mo = smo + par * 5 * NT + tid;
-            const float rho[2] = {mo[0], mo[NT]};
-            const float up[3] = {mo[2 * NT], mo[3 * NT], mo[4 * NT]};
-            const T *fb = fbuf + par * 2 * Q * NT + tid;
+            const T *fb = stage + (z & 1) * 2 * Q * NT + tid;
+            // moments: ρ^c (the density kernel's sum, same order), j^c, and
+            // the shifted velocity u' = Σ_c j^c/τ_c / Σ_c ρ^c/τ_c
+            float rho_[2], jj[2][3];
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                // one pass over opposite pairs (i, i+1), c_{i+1} = -c_i; ρ
+                // accumulates in index order
+                float a = S::cvt(fb[(c * Q) * NT], L.base[c][0]);
+                float jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+                for (int i = 1; i < Q; i += 2) {
+                    const float va = S::cvt(fb[(c * Q + i) * NT], L.base[c][i]);
+                    const float vb = S::cvt(fb[(c * Q + i + 1) * NT], L.base[c][i + 1]);
+                    a += va;
+                    a += vb;
+                    const float d = va - vb;
+                    if (cx(i)) jx += cx(i) * d;
+                    if (cy(i)) jy += cy(i) * d;
+                    if (cz(i)) jz += cz(i) * d;
+                }
+                rho_[c] = a;
+                jj[c][0] = jx;
+                jj[c][1] = jy;
+                jj[c][2] = jz;
+            }
+            // the collision re-reads the stage: keeping the converted
+            // populations live in registers instead would spill
+            asm volatile("" ::: "memory");
+            const float den = __fmaf_rn(rho_[1], L.itau[1], __fmul_rn(rho_[0], L.itau[0]));
+            const float iden = den > 0.f ? 1.f / den : 0.f;
+            float up[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                up[k] = __fmul_rn(__fmaf_rn(jj[1][k], L.itau[1], __fmul_rn(jj[0][k], L.itau[0])), iden);
             float s[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
             uint32_t solid = 0;  // bit i: neighbour i is not fluid
 #pragma unroll
@@ -281,7 +366,7 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
             };
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                const float r = rho[c];
+                const float r = rho_[c];
                 float ue[3], uu15;
                 eq_velocity(L, c, r, pc[c], s[c], up, ue, uu15);
                 const float it = L.itau[c];
@@ -303,19 +388,46 @@ __device__ __forceinline__ void fused_tile(const Lat &L, const typename S::T *__
                 const float f0 = S::cvt(fb[(c * Q) * NT], L.base[c][0]);
                 S::st(dst + ofs.pop[c * Q], relax(f0, __fsub_rn(r, seq), it), L.base[c][0]);
             }
+        } else if (active) {
+            // A solid node's populations are never read (a node that a
+            // particle uncovers gets f^eq in all slots), but writing them
+            // keeps every sector of the output fully written: a partly
+            // written sector costs a DRAM read when it leaves L2.
+            T *d0 = fout + own2 + nxy * z;
+#pragma unroll
+            for (int ci = 0; ci < 2 * Q; ci++) d0[ofs.pop[ci]] = S::enc(0.f, 0.f);
         }
         __syncthreads();
     }
+    if (TMA) {
+        if (!ok && tid == 0) {
+            // let the copies in flight land (bounded) before the memory is reused
+            const int n_issued = ze - zb;
+            for (int st = 0; st < 2; st++) {
+                const int uses = (n_issued - st + 1) / 2;  // planes zb+st, zb+st+2, ...
+                if (uses > 0) mbar_wait(&bar[(zb + st) & 1], (uses - 1) & 1);
+            }
+            atomicOr(L.status, 1u);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            mbar_inval(&bar[0]);
+            mbar_inval(&bar[1]);
+        }
+    }
+    return ok;
 }
 
-template <class S>
+template <class S, bool TMA>
 __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__restrict__ fin,
                                               typename S::T *__restrict__ fout, const float *__restrict__ rho,
                                               const float *__restrict__ psi,
-                                              const uint8_t *__restrict__ type, int zc, FusedOfs ofs)
+                                              const uint8_t *__restrict__ type, int zc, FusedOfs ofs,
+                                              const __grid_constant__ CUtensorMap tmap)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    fused_tile<S>(L, fin, fout, rho, psi, type, zc, ofs, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    fused_tile<S, TMA>(L, fin, fout, rho, psi, type, zc, ofs, &tmap, blockIdx.x, blockIdx.y, blockIdx.z,
+                       align128(smem_raw));
 }
 
 // Persistent multi-lattice variant: CTAs take tiles of all boxes of a batch
@@ -323,9 +435,10 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
 template <class S>
 __global__ void __launch_bounds__(NT, 3) k_fused_batch(BatchIndex B, int total)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *smem = align128(smem_raw);
     __shared__ int s_tile, s_box;
-    __shared__ __align__(16) BoxDev sb;
+    __shared__ BoxDev sb;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -343,8 +456,16 @@ __global__ void __launch_bounds__(NT, 3) k_fused_batch(BatchIndex B, int total)
         const int lt = t - B.tile0[s_box];
         const int bx = lt % sb.ntx, by = (lt / sb.ntx) % sb.nty, bz = lt / (sb.ntx * sb.nty);
         const int cur = B.par[2 * s_box];
-        fused_tile<S>(sb.L, (const typename S::T *)sb.f[cur], (typename S::T *)sb.f[1 - cur], sb.rho, sb.psi, sb.type,
-                      sb.zc, sb.ofs, bx, by, bz, smem);
+        // the tensor map stays in global memory (a TMA operand cannot be in shared memory)
+        const CUtensorMap *tm = &B.box[s_box].tmap[cur];
+        bool ok;
+        if (sb.tma)
+            ok = fused_tile<S, true>(sb.L, (const typename S::T *)sb.f[cur], (typename S::T *)sb.f[1 - cur], sb.rho,
+                                     sb.psi, sb.type, sb.zc, sb.ofs, tm, bx, by, bz, smem);
+        else
+            ok = fused_tile<S, false>(sb.L, (const typename S::T *)sb.f[cur], (typename S::T *)sb.f[1 - cur], sb.rho,
+                                      sb.psi, sb.type, sb.zc, sb.ofs, tm, bx, by, bz, smem);
+        if (!ok) break;
     }
 }
 
@@ -369,6 +490,31 @@ int fused_zchunk(const Lat &L)
     return zc;
 }
 
+bool fused_plane_map(CUtensorMap *map, void *f, const Lat &L, int storage)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const size_t es = storage == LBE_STORE_F32 ? 4 : 2;
+    if (!encode || ((size_t)L.nx * es) % 16 != 0) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny, (cuuint64_t)L.nz, (cuuint64_t)(2 * Q)};
+    const cuuint64_t strides[3] = {(cuuint64_t)L.nx * es, (cuuint64_t)L.nx * L.ny * es, (cuuint64_t)L.S * es};
+    const cuuint32_t box[4] = {TX, TY, 1, 2 * Q};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    return encode(map, dt, 4, f, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 FusedOfs fused_offsets(const Lat &L)
 {
     FusedOfs ofs;
@@ -383,24 +529,32 @@ FusedOfs fused_offsets(const Lat &L)
 
 template <class S>
 static void launch_fused_t(const Lat &L, const void *fin, void *fout, const float *rho, const float *psi,
-                           const uint8_t *type, cudaStream_t s, int zc_override)
+                           const uint8_t *type, const CUtensorMap *tmap, cudaStream_t s, int zc_override)
 {
     static bool configured = false;  // the attribute is per function and process
     if (!configured) {
-        cudaFuncSetAttribute(k_fused<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem<S>::bytes);
+        cudaFuncSetAttribute(k_fused<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem<S>::bytes);
+        cudaFuncSetAttribute(k_fused<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem<S>::bytes);
         configured = true;
     }
     const int zc = zc_override > 0 ? zc_override : fused_zchunk(L);
     dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
     FusedOfs ofs = fused_offsets(L);
-    k_fused<S><<<grid, NT, Smem<S>::bytes, s>>>(L, (const typename S::T *)fin, (typename S::T *)fout, rho, psi,
-                                                 type, zc, ofs);
+    using T = typename S::T;
+    if (tmap) {
+        k_fused<S, true><<<grid, NT, Smem<S>::bytes, s>>>(L, (const T *)fin, (T *)fout, rho, psi, type, zc, ofs,
+                                                          *tmap);
+    } else {
+        const CUtensorMap none{};
+        k_fused<S, false><<<grid, NT, Smem<S>::bytes, s>>>(L, (const T *)fin, (T *)fout, rho, psi, type, zc, ofs,
+                                                           none);
+    }
 }
 
 void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *rho, const float *psi,
-                  const uint8_t *type, cudaStream_t s, int zc_override)
+                  const uint8_t *type, const CUtensorMap *tmap, cudaStream_t s, int zc_override)
 {
-    LBE_DISPATCH(storage, (launch_fused_t<S>(L, fin, fout, rho, psi, type, s, zc_override)));
+    LBE_DISPATCH(storage, (launch_fused_t<S>(L, fin, fout, rho, psi, type, tmap, s, zc_override)));
 }
 
 template <class S>

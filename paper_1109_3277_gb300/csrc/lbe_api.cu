@@ -19,6 +19,8 @@ struct lbe_ctx {
     Pair pair{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    CUtensorMap tmap[2];   // the fused kernel's plane copies of f[0], f[1]
+    bool tma = false;
     size_t esize = 4;
     void *f[2] = {nullptr, nullptr};
     int cur = 0;
@@ -140,6 +142,7 @@ void free_all(lbe_ctx *c)
     cudaFree(c->ll.ent);
     cudaFree(c->ll.count);
     if (c->L.err) cudaFree(c->L.err);
+    cudaFree(c->L.status);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
@@ -189,7 +192,7 @@ void enqueue_step(lbe_ctx *c)
     if (two_pass)
         launch_collide_stream(st, L, fin, fout, c->psi, c->type, s);
     else
-        launch_fused(st, L, fin, fout, c->rho, c->psi, c->type, s, c->zc_tuned);
+        launch_fused(st, L, fin, fout, c->rho, c->psi, c->type, c->tma ? &c->tmap[c->cur] : nullptr, s, c->zc_tuned);
     if (c->profiling) {
         cudaEventRecord(c->ev[c->ev_used + 1], s);
         c->ev_used += 2;
@@ -275,6 +278,10 @@ lbe_status sync(lbe_ctx *c, const char *where)
 {
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, where);
+    unsigned status = 0;
+    if (c->L.status && cudaMemcpy(&status, c->L.status, sizeof status, cudaMemcpyDeviceToHost) == cudaSuccess &&
+        (status & 1u))
+        return fail(c, LBE_ETIMEOUT, std::string(where) + ": a plane copy of the fused kernel did not complete");
 #ifdef LBE_CHECK
     unsigned long long bad = 0;
     if (c->L.err && cudaMemcpy(&bad, c->L.err, sizeof bad, cudaMemcpyDeviceToHost) == cudaSuccess && bad) {
@@ -361,6 +368,9 @@ lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_c
     if ((e = dalloc(c, &c->mass_partials, (size_t)2 * mass_blocks() * sizeof(double))) != cudaSuccess)
         return bail(e, "cudaMalloc(mass)");
     if ((e = dalloc(c, &c->mass_out, 2 * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc(mass_out)");
+    if ((e = dalloc(c, &c->L.status, sizeof(unsigned))) != cudaSuccess) return bail(e, "cudaMalloc(status)");
+    cudaMemsetAsync(c->L.status, 0, sizeof(unsigned), c->stream);
+    c->tma = fused_plane_map(&c->tmap[0], c->f[0], L, d->storage) && fused_plane_map(&c->tmap[1], c->f[1], L, d->storage);
 #ifdef LBE_CHECK
     if ((e = cudaMalloc((void **)&c->L.err, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc(err)");
     cudaMemset(c->L.err, 0, sizeof(unsigned long long));
@@ -724,9 +734,12 @@ lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc)
     float best = 1e30f;
     int best_zc = fused_zchunk(L);
     for (int zc : cand) {
-        launch_fused(c->d.storage, L, fin, fout, c->rho, c->psi, c->type, c->stream, zc);  // warm-up
+        launch_fused(c->d.storage, L, fin, fout, c->rho, c->psi, c->type, c->tma ? &c->tmap[c->cur] : nullptr,
+                     c->stream, zc);  // warm-up
         cudaEventRecord(e0, c->stream);
-        for (int r = 0; r < 3; r++) launch_fused(c->d.storage, L, fin, fout, c->rho, c->psi, c->type, c->stream, zc);
+        for (int r = 0; r < 3; r++)
+            launch_fused(c->d.storage, L, fin, fout, c->rho, c->psi, c->type, c->tma ? &c->tmap[c->cur] : nullptr,
+                         c->stream, zc);
         cudaEventRecord(e1, c->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) break;
         float ms = 0.f;
@@ -858,6 +871,11 @@ lbe_status lbe_batch_create(lbe_ctx *const *members, int32_t n, lbe_batch **out)
         BoxDev &d = box[k];
         d.L = c->L;
         d.ofs = fused_offsets(c->L);
+        d.tma = c->tma ? 1 : 0;
+        if (c->tma) {
+            d.tmap[0] = c->tmap[0];
+            d.tmap[1] = c->tmap[1];
+        }
         d.f[0] = c->f[0];
         d.f[1] = c->f[1];
         d.rho = c->rho;

@@ -2,6 +2,7 @@
 // Method: §2 of Günther et al., arXiv:1109.3277 (two-component Shan–Chen
 // D3Q19 BGK lattice Boltzmann with rigid ellipsoids).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -94,6 +95,7 @@ struct Lat {
     float base[2][Q];      // w_i ρ_ref^c for the 16-bit modes, 0 for FP32
     double rho_ref[2];
     int np;                        // particles (bounds checks)
+    unsigned *status;              // bit 0: a TMA copy of the fused kernel never completed
     unsigned long long *err;       // bounds-check record (checked builds only)
 };
 
@@ -173,6 +175,8 @@ struct Pair {
 // Ping-pong parities live in a device array beside the table, so that a
 // captured step can be replayed whatever the parity.
 struct BoxDev {
+    CUtensorMap tmap[2];     // population planes of f[0], f[1] (when tma)
+    int tma;                 // the fused kernel stages planes by TMA
     Lat L;
     FusedOfs ofs;
     void *f[2];
@@ -229,8 +233,12 @@ void launch_flip_batch(const BatchIndex &B, cudaStream_t s);
 
 // ---- launchers (fused.cu) -------------------------------------------------
 void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *rho, const float *psi,
-                  const uint8_t *type, cudaStream_t s, int zc_override = 0);
+                  const uint8_t *type, const CUtensorMap *tmap, cudaStream_t s, int zc_override = 0);
 int fused_zchunk(const Lat &L);
+// Tensor map of one population buffer for the fused kernel's plane copies
+// (box 32 x 8 x 1 x 38 of the (x, y, z, slot) array); false if the lattice's
+// row pitch is not a multiple of 16 bytes or the driver lacks the call.
+bool fused_plane_map(CUtensorMap *map, void *f, const Lat &L, int storage);
 constexpr int FUSED_TX = 32, FUSED_TY = 8;
 
 // Box lookup: the box b with off[b] <= i < off[b+1] (binary search).

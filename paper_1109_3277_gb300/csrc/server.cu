@@ -108,6 +108,9 @@ void finish(lbe_server *s, Request *r, lbe_status err)
                     o[16 + k] = T[3 * p + k];
                 }
                 for (int k = 0; k < 4; k++) o[3 + k] = q[4 * p + k];
+                // a run that diverged is a failure, whatever stopped it
+                for (int k = 0; k < LBE_PARTICLE_OUT; k++)
+                    if (!std::isfinite(o[k])) err = LBE_ENUMERIC;
             }
         }
         lbe_destroy(r->ctx);

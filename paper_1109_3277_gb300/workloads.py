@@ -242,7 +242,10 @@ def adsorption_request(seed, index, edge_range=(32, 96), m_range=(0.25, 4.0), r_
         m = m_range[0] + (m_range[1] - m_range[0]) * row[1]
         r_par = m * r_perp
         rmax = max(r_par, r_perp)
-        if 2 * rmax + 6 <= edge:
+        # resampled: particles that do not fit between the walls, and discs
+        # thinner than 2 lattice units (r_par < 2), which the lattice cannot
+        # resolve (the method diverges on them, in FP64 too)
+        if 2 * rmax + 6 <= edge and r_par >= 2.0:
             break
     drho = drho_range[0] + (drho_range[1] - drho_range[0]) * row[2]
     tilt = 0.5 * np.pi * row[3]
