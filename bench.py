@@ -186,17 +186,17 @@ def source_digest():
 
 
 def committed_traffic(kernel, workload):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch from the committed ncu summary
+    (profiles/traffic.md), if it was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
-        d = json.load(fh)
-    e = d.get(f"{kernel}:{workload}")
-    if not e or e.get("source_digest") != source_digest():
-        return None
-    return e.get("bytes_per_launch")
+        for line in fh:
+            cells = [c.strip() for c in line.strip().strip("|").split("|")]
+            if len(cells) == 4 and cells[0] == kernel and cells[1] == workload:
+                return int(cells[2]) if cells[3] == source_digest() else None
+    return None
 
 
 def add_particles(lat, w):
