@@ -105,15 +105,18 @@ __global__ void __launch_bounds__(256) k_moments(Lat L, const typename S::T *__r
 }
 
 // ------------------------------------------------------------ densities
-// ρ^c = Σ_i f_i^c on every fluid node, for the shell fill, the link kernel
-// and the halo of the fused kernel (which sums its own nodes' populations
-// in the same order, so the two agree bit for bit).  One thread per pair of
-// consecutive nodes, with paired loads; the slot stride S is padded past N,
-// so the pair loads of the last node stay inside the allocation.
+// ρ^c = Σ_i f_i^c on every fluid node, for the shell fill and the link
+// kernel, and ψ^c = 1 - exp(-ρ^c) for the fused kernel (which sums its own
+// nodes' populations in the same order, so the two agree bit for bit; the
+// shell fill writes ψ of the solid nodes into the same array).  One thread
+// per pair of consecutive nodes, with paired loads; the slot stride S is
+// padded past N, so the pair loads of the last node stay inside the
+// allocation.
 
 template <class S>
 __global__ void __launch_bounds__(256) k_rho(Lat L, const typename S::T *__restrict__ f,
-                                             const uint8_t *__restrict__ type, float *__restrict__ rho)
+                                             const uint8_t *__restrict__ type, float *__restrict__ rho,
+                                             float *__restrict__ psi)
 {
     const long long n = 2ll * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
     if (n >= L.N) return;
@@ -131,8 +134,14 @@ __global__ void __launch_bounds__(256) k_rho(Lat L, const typename S::T *__restr
             a0 += v0;
             a1 += v1;
         }
-        if (fl0) rho[(size_t)c * L.N + n] = a0;
-        if (fl1) rho[(size_t)c * L.N + n + 1] = a1;
+        if (fl0) {
+            rho[(size_t)c * L.N + n] = a0;
+            psi[(size_t)c * L.N + n] = 1.f - expf(-a0);
+        }
+        if (fl1) {
+            rho[(size_t)c * L.N + n + 1] = a1;
+            psi[(size_t)c * L.N + n + 1] = 1.f - expf(-a1);
+        }
     }
 }
 
@@ -234,6 +243,7 @@ __global__ void __launch_bounds__(256) k_rho_batch(BatchIndex B, int total)
 #pragma unroll
             for (int i = 1; i < Q; i++) r += S::ld(slot<S>(f, bx.L, c, i) + s.n, bx.L.base[c][i]);
             bx.rho[(size_t)c * bx.L.N + s.n] = r;
+            bx.psi[(size_t)c * bx.L.N + s.n] = 1.f - expf(-r);
         }
     }
 }
@@ -576,10 +586,12 @@ void launch_moments(int storage, const Lat &L, const void *f, const uint8_t *typ
                               L, (const typename S::T *)f, type, rho, psi)));
 }
 
-void launch_rho(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho, cudaStream_t s)
+void launch_rho(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho, float *psi,
+                cudaStream_t s)
 {
     const size_t pairs = ((size_t)L.N + 1) / 2;
-    LBE_DISPATCH(storage, (k_rho<S><<<blocks_for(pairs, 256), 256, 0, s>>>(L, (const typename S::T *)f, type, rho)));
+    LBE_DISPATCH(storage,
+                 (k_rho<S><<<blocks_for(pairs, 256), 256, 0, s>>>(L, (const typename S::T *)f, type, rho, psi)));
 }
 
 static unsigned batch_grid(int total)

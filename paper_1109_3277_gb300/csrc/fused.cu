@@ -8,10 +8,10 @@
 // planes deep: while the warps collide plane z, the next plane is on its way
 // into the other stage, as one TMA tensor copy (a 32 x 8 x 38-slot box of
 // the population array, completion on an mbarrier) where the lattice's row
-// pitch allows it, else by per-thread loads.  ψ = 1 - exp(-ρ) of the tile
-// and a one-node halo comes from the density kernel's ρ (fluid nodes) or the
-// shell fill's ψ (solid nodes), into a three-plane ring; the force at a
-// node reads its 18 neighbours' ψ from the ring.  Moments, force, collision
+// pitch allows it, else by per-thread loads.  ψ of the tile and a one-node
+// halo (written by the density kernel on fluid nodes, by the shell fill on
+// solid nodes) goes into a three-plane ring; the force at a node reads its
+// 18 neighbours' ψ from the ring.  Moments, force, collision
 // and the stores of one node run in one thread.
 //
 // Populations streaming into a wall or particle node are reflected into the
@@ -192,9 +192,10 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
     }
     const int own2 = gx + L.nx * gy;
 
-    // ψ and node type of plane zz (tile + halo) into the ring: 1 - exp(-ρ)
-    // from the density kernel on fluid nodes, the shell fill's ψ on solid
-    // nodes, walls beyond the lattice's z walls.
+    // ψ and node type of plane zz (tile + halo) into the ring: the density
+    // kernel's ψ on fluid nodes and the shell fill's on solid nodes share one
+    // array, so the loads of an entry do not wait on its type; walls beyond
+    // the lattice's z walls.
     auto load_ring = [&](int zz) {
         const int slot = (zz + 3) % 3;
         bool zin = true;
@@ -212,13 +213,8 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
             if (zin) {
                 const int n = own2 + nxy * gz;
                 t = type[n];
-                if (t == FLUID) {
-                    p0 = 1.f - expf(-__ldg(rho + n));
-                    p1 = 1.f - expf(-__ldg(rho + (size_t)L.N + n));
-                } else {
-                    p0 = psi[n];
-                    p1 = psi[(size_t)L.N + n];
-                }
+                p0 = psi[n];
+                p1 = psi[(size_t)L.N + n];
             }
             ps[ec] = make_float2(p0, p1);
             ts[ec] = t;
@@ -229,10 +225,7 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
             if (zin) {
                 const int n = hn2 + nxy * gz;
                 t = type[n];
-                if (t == FLUID)
-                    p = 1.f - expf(-__ldg(rho + (size_t)hc * L.N + n));
-                else
-                    p = psi[(size_t)hc * L.N + n];
+                p = psi[(size_t)hc * L.N + n];
             }
             reinterpret_cast<float *>(ps + he)[hc] = p;
             if (hc == 0) ts[he] = t;

@@ -175,7 +175,7 @@ void enqueue_step(lbe_ctx *c)
         launch_moments(st, L, fin, c->type, c->rho, c->psi, s);
     } else {
         if (links) cudaMemsetAsync(c->ll.count, 0, sizeof(int), s);
-        launch_rho(st, L, fin, c->type, c->rho, s);
+        launch_rho(st, L, fin, c->type, c->rho, c->psi, s);
     }
     launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho,
                  links ? c->ll : LinkList{nullptr, nullptr, 0}, s);
@@ -729,7 +729,7 @@ lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc)
     CK(c, cudaEventCreate(&e0));
     CK(c, cudaEventCreate(&e1));
     void *fin = c->f[c->cur], *fout = c->f[1 - c->cur];
-    launch_rho(c->d.storage, L, fin, c->type, c->rho, c->stream);
+    launch_rho(c->d.storage, L, fin, c->type, c->rho, c->psi, c->stream);
     launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, LinkList{nullptr, nullptr, 0}, c->stream);
     float best = 1e30f;
     int best_zc = fused_zchunk(L);

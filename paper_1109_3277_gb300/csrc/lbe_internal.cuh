@@ -204,7 +204,8 @@ void launch_init_f(int storage, const Lat &L, const double *rho0, void *f, const
                    cudaStream_t s);
 void launch_moments(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho,
                     float *psi, cudaStream_t s);
-void launch_rho(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho, cudaStream_t s);
+void launch_rho(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho, float *psi,
+                cudaStream_t s);
 void launch_shell(const Lat &L, const float *rho, float *psi, const uint8_t *type,
                   const uint32_t *owner, const double *drho, const LinkList &ll, cudaStream_t s);
 void launch_collide_stream(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
