@@ -41,9 +41,9 @@ template <class S>
 struct Smem {
     static constexpr size_t plane = 2 * Q * NT * sizeof(typename S::T);  // one staged plane
     static constexpr size_t stage = 0;                                   // T [2][2Q][NT]
-    static constexpr size_t sps = stage + 2 * plane;                     // float2 [3][HN] (ψ_r, ψ_b)
-    static constexpr size_t sty = sps + 3 * HN * sizeof(float2);         // uint8 [3][HN]
-    static constexpr size_t bar = (sty + 3 * HN + 15) / 16 * 16;          // uint64 [2] mbarriers
+    static constexpr size_t sps = stage + 2 * plane;                     // float2 [4][HN] (ψ_r, ψ_b)
+    static constexpr size_t sty = sps + 4 * HN * sizeof(float2);         // uint8 [4][HN]
+    static constexpr size_t bar = (sty + 4 * HN + 15) / 16 * 16;          // uint64 [2] mbarriers
     static constexpr size_t bytes = bar + 2 * sizeof(unsigned long long) + 128;  // + alignment slack
 };
 
@@ -192,12 +192,17 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
     }
     const int own2 = gx + L.nx * gy;
 
-    // ψ and node type of plane zz (tile + halo) into the ring: the density
+    // ψ and node type of plane zz (tile + halo) for the ring: the density
     // kernel's ψ on fluid nodes and the shell fill's on solid nodes share one
     // array, so the loads of an entry do not wait on its type; walls beyond
-    // the lattice's z walls.
-    auto load_ring = [&](int zz) {
-        const int slot = (zz + 3) % 3;
+    // the lattice's z walls.  Loaded one plane ahead into registers, stored
+    // into ring slot zz % 4 after the collision of plane zz - 2.
+    struct RingVals {
+        float p0, p1, ph;
+        uint8_t t, th;
+    };
+    auto ring_load = [&](int zz) {
+        RingVals v{0.f, 0.f, 0.f, WALL, WALL};
         bool zin = true;
         int gz = zz;
         if (L.walls) {
@@ -205,30 +210,28 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
         } else {
             gz = zz < 0 ? zz + L.nz : (zz >= L.nz ? zz - L.nz : zz);
         }
+        if (zin) {
+            const int n = own2 + nxy * gz;
+            v.t = type[n];
+            v.p0 = psi[n];
+            v.p1 = psi[(size_t)L.N + n];
+            if (h < NHALO) {
+                const int nh = hn2 + nxy * gz;
+                v.th = type[nh];
+                v.ph = psi[(size_t)hc * L.N + nh];
+            }
+        }
+        return v;
+    };
+    auto ring_store = [&](int zz, const RingVals &v) {
+        const int slot = (zz + 4) & 3;
         float2 *ps = sps + slot * HN;
         uint8_t *ts = sty + slot * HN;
-        {
-            float p0 = 0.f, p1 = 0.f;
-            uint8_t t = WALL;
-            if (zin) {
-                const int n = own2 + nxy * gz;
-                t = type[n];
-                p0 = psi[n];
-                p1 = psi[(size_t)L.N + n];
-            }
-            ps[ec] = make_float2(p0, p1);
-            ts[ec] = t;
-        }
+        ps[ec] = make_float2(v.p0, v.p1);
+        ts[ec] = v.t;
         if (h < NHALO) {
-            float p = 0.f;
-            uint8_t t = WALL;
-            if (zin) {
-                const int n = hn2 + nxy * gz;
-                t = type[n];
-                p = psi[(size_t)hc * L.N + n];
-            }
-            reinterpret_cast<float *>(ps + he)[hc] = p;
-            if (hc == 0) ts[he] = t;
+            reinterpret_cast<float *>(ps + he)[hc] = v.ph;
+            if (hc == 0) ts[he] = v.th;
         }
     };
 
@@ -261,13 +264,16 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
         __syncthreads();
     }
     fill(zb);
-    load_ring(zb - 1);
-    load_ring(zb);
+    ring_store(zb - 1, ring_load(zb - 1));
+    ring_store(zb, ring_load(zb));
+    ring_store(zb + 1, ring_load(zb + 1));
     const bool xy_inner = gx >= 1 && gx <= L.nx - 2 && gy >= 1 && gy <= L.ny - 2;
     bool ok = true;
     for (int z = zb; z < ze; z++) {
         if (z + 1 < ze) fill(z + 1);
-        load_ring(z + 1);
+        // the ring of plane z+2 is needed by the next collision: its loads
+        // are in flight during this one
+        const RingVals next = ring_load(z + 2);
         bool late = false;
         if (TMA) late = !mbar_wait(&bar[z & 1], ((z - zb) >> 1) & 1);
         if (__syncthreads_or(late)) {
@@ -275,8 +281,8 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
             break;
         }
         // ring slots of planes z-1, z, z+1
-        const float2 *pl[3] = {sps + ((z + 2) % 3) * HN, sps + (z % 3) * HN, sps + ((z + 1) % 3) * HN};
-        const uint8_t *tl[3] = {sty + ((z + 2) % 3) * HN, sty + (z % 3) * HN, sty + ((z + 1) % 3) * HN};
+        const float2 *pl[3] = {sps + ((z + 3) & 3) * HN, sps + (z & 3) * HN, sps + ((z + 1) & 3) * HN};
+        const uint8_t *tl[3] = {sty + ((z + 3) & 3) * HN, sty + (z & 3) * HN, sty + ((z + 1) & 3) * HN};
         if (active && tl[1][ec] == FLUID) {
             const int n = own2 + nxy * z;
             const bool inner = xy_inner && z >= 1 && z <= L.nz - 2;
@@ -390,6 +396,7 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
 #pragma unroll
             for (int ci = 0; ci < 2 * Q; ci++) d0[ofs.pop[ci]] = S::enc(0.f, 0.f);
         }
+        ring_store(z + 2, next);  // slot (z+2) % 4: not one the collision read
         __syncthreads();
     }
     if (TMA) {
