@@ -175,23 +175,6 @@ __device__ __forceinline__ int site_nb(const Lat &L, const Site &s, int i)
     return nidx(L, b, i);
 }
 
-// Append (n, m) for the lanes with m != 0 to the list: one atomic per warp.
-// Called by all 32 lanes.
-__device__ __forceinline__ void append_links(const LinkList &ll, int n, uint32_t m)
-{
-    const unsigned want = __ballot_sync(0xffffffffu, m != 0);
-    if (!want) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(want) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(ll.count, __popc(want));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (m) {
-        const int k = base + __popc(want & ((1u << lane) - 1u));
-        if (k < ll.cap) ll.ent[k] = make_uint2((unsigned)n, m);
-    }
-}
-
 // Batched form: lanes may belong to different boxes (key: the box, or -1
 // for a lane without a node); lanes of the same box share one atomic on the
 // box's counter.  Called by all 32 lanes.
@@ -259,34 +242,14 @@ __device__ __forceinline__ uint32_t shell_node(const Lat &L, const float *__rest
                                                const uint8_t *__restrict__ type, const uint32_t *__restrict__ owner,
                                                const double *__restrict__ drho, const Site &s)
 {
-    const int n = s.n;
-    uint8_t t = type[n];
+    const uint8_t t = type[s.n];
     if (t == FLUID) return 0;
-    float s0 = 0.f, s1 = 0.f;
-    int cnt = 0;
-    uint32_t fm = 0;
-#pragma unroll
-    for (int i = 1; i < Q; i++) {
-        int m = site_nb(L, s, i);
-        if (m < 0 || type[m] != FLUID) continue;
-        s0 += rho[m];
-        s1 += rho[(size_t)L.N + m];
-        cnt++;
-        fm |= 1u << i;
-    }
-    if (cnt == 0) return 0;  // interior: never read by a fluid node
-    float r0 = s0 / (float)cnt, r1 = s1 / (float)cnt;
     float dr = 0.f;
     if (t == PART) {
-        uint32_t o = owner[n];
+        uint32_t o = owner[s.n];
         if (idx_ok(L, o, L.np, 1)) dr = (float)drho[o];
     }
-    if (dr > 0.f)
-        r0 += dr;
-    else
-        r1 += fabsf(dr);
-    psi[n] = 1.f - expf(-r0);
-    psi[(size_t)L.N + n] = 1.f - expf(-r1);
+    const uint32_t fm = shell_fill(L, rho, psi, type, s.n, dr, [&](int i) { return site_nb(L, s, i); });
     return t == PART ? fm : 0u;
 }
 

@@ -34,6 +34,7 @@ struct lbe_ctx {
     double *pbuf = nullptr;
     float4 *x32 = nullptr;
     double *ppart = nullptr;
+    void *geo = nullptr;   // coverage geometry records (cap of them)
     Parts P{};
     Cells cells{};   // pair-force cell list (with the particles)
     size_t cells_bytes = 0;
@@ -117,6 +118,7 @@ void bind_parts(lbe_ctx *c)
     P.X32 = c->x32;
     P.K32 = c->x32 ? c->x32 + c->cap : nullptr;
     P.ppart = c->ppart;
+    P.geo = c->geo;
     P.nsplit = 1;
 }
 
@@ -137,6 +139,7 @@ void free_all(lbe_ctx *c)
     cudaFree(c->pbuf);
     cudaFree(c->x32);
     cudaFree(c->ppart);
+    cudaFree(c->geo);
     cudaFree(c->cells.count);
     cudaFree(c->cells.idx);
     cudaFree(c->ll.ent);
@@ -177,8 +180,17 @@ void enqueue_step(lbe_ctx *c)
         if (links) cudaMemsetAsync(c->ll.count, 0, sizeof(int), s);
         launch_rho(st, L, fin, c->type, c->rho, c->psi, s);
     }
-    launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho,
-                 links ? c->ll : LinkList{nullptr, nullptr, 0}, s);
+    if (two_pass) {
+        launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, LinkList{nullptr, nullptr, 0}, s);
+    } else {
+        // the solid nodes a fluid node can see: the particles' own nodes and
+        // the wall planes (none for a periodic lattice without particles)
+        if (c->np > 0) {
+            c->P.n = c->np;
+            launch_shell_particles(L, c->P, c->rho, c->psi, c->type, c->owner[c->ocur], c->ll, s);
+        }
+        launch_shell_walls(L, c->rho, c->psi, c->type, s);
+    }
     if (c->profiling) {
         if (c->ev_used + 2 > c->ev.size()) {
             for (int k = 0; k < 256; k++) {
@@ -210,6 +222,7 @@ void enqueue_step(lbe_ctx *c)
         launch_integrate(L, c->P, c->d.particle_mode, s);
         if (c->d.particle_mode != LBE_PARTICLES_STATIC) {
             uint32_t *oo = c->owner[c->ocur], *on = c->owner[1 - c->ocur];
+            launch_geom(L, c->P, s);
             launch_claim(L, c->P, 0, on, s);
             launch_transition(st, L, c->P, fout, c->type, oo, on, 0, s);
             launch_reset(L, c->P, 1, oo, s);
@@ -475,24 +488,30 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
         double *nb = nullptr;
         float4 *nx32 = nullptr;
         double *npp = nullptr;
+        void *ngeo = nullptr;
         CK(c, cudaMalloc((void **)&nb, blk.size() * sizeof(double)));
         cudaError_t e = cudaMalloc((void **)&nx32, x32.size() * sizeof(float4));
         if (e == cudaSuccess) e = cudaMalloc((void **)&npp, (size_t)6 * ncap * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc(&ngeo, (size_t)ncap * geom_bytes_per_particle());
         if (e != cudaSuccess) {
             cudaFree(nb);
             cudaFree(nx32);
+            cudaFree(npp);
             return cuda_fail(c, e, "add_particles: cudaMalloc");
         }
-        const size_t per_cap = PSTRIDE * sizeof(double) + 3 * sizeof(float4) + 6 * sizeof(double);
+        const size_t per_cap = PSTRIDE * sizeof(double) + 3 * sizeof(float4) + 6 * sizeof(double) +
+                               geom_bytes_per_particle();
         if (c->pbuf) {
             cudaFree(c->pbuf);
             cudaFree(c->x32);
             cudaFree(c->ppart);
+            cudaFree(c->geo);
             c->bytes -= (size_t)cap * per_cap;
         }
         c->pbuf = nb;
         c->x32 = nx32;
         c->ppart = npp;
+        c->geo = ngeo;
         c->cap = ncap;
         c->bytes += (size_t)ncap * per_cap;
     }
@@ -513,6 +532,7 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
     drop_graphs(c);
     cudaStream_t s = c->stream;
     uint32_t *oo = c->owner[c->ocur], *on = c->owner[1 - c->ocur];
+    launch_geom(c->L, c->P, s);
     launch_claim(c->L, c->P, 0, on, s);
     launch_transition(c->d.storage, c->L, c->P, c->f[c->cur], c->type, oo, on, 1, s);
     launch_reset(c->L, c->P, 1, oo, s);
@@ -667,10 +687,17 @@ lbe_status lbe_profile_read(lbe_ctx *c, double *ms_total, int64_t *launches)
 int32_t lbe_kernels_per_step(const lbe_ctx *c)
 {
     if (!c) return 0;
-    int k = 3;  // densities (boundary or all), shell fill, fused fluid (or collide+stream)
+    const bool two_pass = (c->d.flags & LBE_FLAG_TWO_PASS) != 0;
+    // densities, fused fluid (or collide + stream), shell fill: one sweep
+    // (two-pass), else per particle and over the wall planes
+    int k = 2;
+    if (two_pass)
+        k += 1;
+    else
+        k += (c->np > 0 ? 1 : 0) + (c->d.walls_z ? 1 : 0);
     if (c->np > 0) {
         k += 6;  // links, pair cells (count, prefix, fill), pairs, integrate
-        if (c->d.particle_mode != LBE_PARTICLES_STATIC) k += 3;  // claim, transition, reset
+        if (c->d.particle_mode != LBE_PARTICLES_STATIC) k += 4;  // geometry, claim, transition, reset
     }
     return k;
 }
@@ -690,7 +717,8 @@ size_t lbe_footprint(const lbe_lattice_desc *d, int32_t nparticles)
     b += 2 * N * sizeof(double);                                  // initial densities (transient)
     if (nparticles > 0) {
         const size_t cap = nparticles < 64 ? 64 : (size_t)nparticles + nparticles / 4;
-        b += cap * (PSTRIDE * sizeof(double) + 3 * sizeof(float4) + 6 * sizeof(double) + 2 * sizeof(int));
+        b += cap * (PSTRIDE * sizeof(double) + 3 * sizeof(float4) + 6 * sizeof(double) + 2 * sizeof(int) +
+                    geom_bytes_per_particle());
         b += (3 * (N / 8) + 1) * sizeof(int);  // cells (at least 2 nodes a side)
         b += N * sizeof(uint2) + sizeof(int);  // link list
     }
@@ -791,6 +819,7 @@ void batch_enqueue_step(lbe_batch *b)
         launch_link_batch(b->storage, b->idx, s);
         launch_pairs_batch(b->idx, b->total_parts, s);
         launch_integrate_batch(b->idx, b->total_parts, s);
+        launch_geom_batch(b->idx, b->total_parts, s);
         launch_claim_batch(b->idx, b->total_parts, s);
         launch_transition_batch(b->storage, b->idx, b->total_parts, s);
         launch_reset_batch(b->idx, b->total_parts, s);
@@ -1025,7 +1054,7 @@ lbe_status lbe_batch_first_quat(lbe_batch *b, double *quat_out)
 int32_t lbe_batch_kernels_per_step(const lbe_batch *b)
 {
     if (!b) return 0;
-    return b->total_parts > 0 ? 10 : 4;
+    return b->total_parts > 0 ? 11 : 4;
 }
 
 void lbe_batch_destroy(lbe_batch *b)

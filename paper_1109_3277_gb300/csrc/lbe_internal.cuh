@@ -129,6 +129,7 @@ struct Parts {
     double *ppart;                  // [nsplit][6][n] pair-force partial sums
     float4 *X32;                    // FP32 (x, y, z, max radius) for the pair prefilter
     float4 *K32;                    // FP32 velocity [2p] and ω [2p+1] for the fused links
+    void *geo;                      // per particle: coverage geometry of the last and the current update
 };
 
 // Particle nodes next to fluid nodes, collected each step by the shell-fill
@@ -142,6 +143,55 @@ struct LinkList {
 };
 
 constexpr double FIXED_UNIT = 1.0 / 1099511627776.0;  // 2^-40
+
+// Shell fill of solid node n (Eq. 10 and the colour rule): the mean ρ^c of
+// its fluid neighbours, the colour Δρ added to red if positive, else |Δρ| to
+// blue, then ψ^c = 1 - exp(-ρ^c).  Nothing for a node without a fluid
+// neighbour (never read by a fluid node).  nb(i) is the neighbour index
+// along c_i, -1 beyond a wall.  Returns the mask of fluid neighbours.
+template <class NB>
+__device__ __forceinline__ uint32_t shell_fill(const Lat &L, const float *__restrict__ rho, float *__restrict__ psi,
+                                               const uint8_t *__restrict__ type, int n, float dr, NB nb)
+{
+    float s0 = 0.f, s1 = 0.f;
+    int cnt = 0;
+    uint32_t fm = 0;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        const int m = nb(i);
+        if (m < 0 || type[m] != FLUID) continue;
+        s0 += rho[m];
+        s1 += rho[(size_t)L.N + m];
+        cnt++;
+        fm |= 1u << i;
+    }
+    if (cnt == 0) return 0;
+    float r0 = s0 / (float)cnt, r1 = s1 / (float)cnt;
+    if (dr > 0.f)
+        r0 += dr;
+    else
+        r1 += fabsf(dr);
+    psi[n] = 1.f - expf(-r0);
+    psi[(size_t)L.N + n] = 1.f - expf(-r1);
+    return fm;
+}
+
+// Append (n, m) for the lanes with m != 0 to a link list: one atomic per
+// warp.  Called by all 32 lanes.
+__device__ __forceinline__ void append_links(const LinkList &ll, int n, uint32_t m)
+{
+    const unsigned want = __ballot_sync(0xffffffffu, m != 0);
+    if (!want) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(want) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(ll.count, __popc(want));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (m) {
+        const int k = base + __popc(want & ((1u << lane) - 1u));
+        if (k < ll.cap) ll.ent[k] = make_uint2((unsigned)n, m);
+    }
+}
 
 // Cell list of the particles for the pair forces: cubic-ish cells of edge
 // >= the largest pair reach, so a particle's partners lie in its own cell
@@ -208,6 +258,12 @@ void launch_rho(int storage, const Lat &L, const void *f, const uint8_t *type, f
                 cudaStream_t s);
 void launch_shell(const Lat &L, const float *rho, float *psi, const uint8_t *type,
                   const uint32_t *owner, const double *drho, const LinkList &ll, cudaStream_t s);
+// Shell fill of the particles' own nodes (one CTA per particle over its
+// candidate rows) and of the wall planes: the solid nodes a fluid node can
+// see, without a sweep of the lattice.
+void launch_shell_particles(const Lat &L, const Parts &P, const float *rho, float *psi, const uint8_t *type,
+                            const uint32_t *owner, const LinkList &ll, cudaStream_t s);
+void launch_shell_walls(const Lat &L, const float *rho, float *psi, const uint8_t *type, cudaStream_t s);
 void launch_collide_stream(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
                            const uint8_t *type, cudaStream_t s);
 void launch_fields(int storage, const Lat &L, const void *f, const float *psi, const uint8_t *type,
@@ -225,6 +281,7 @@ void launch_fused_batch(int storage, const BatchIndex &B, int total_tiles, int c
 int fused_batch_ctas_per_sm(int storage);
 void launch_pairs_batch(const BatchIndex &B, int total_parts, cudaStream_t s);
 void launch_integrate_batch(const BatchIndex &B, int total_parts, cudaStream_t s);
+void launch_geom_batch(const BatchIndex &B, int total_parts, cudaStream_t s);
 void launch_claim_batch(const BatchIndex &B, int total_parts, cudaStream_t s);
 void launch_transition_batch(int storage, const BatchIndex &B, int total_parts, cudaStream_t s);
 void launch_reset_batch(const BatchIndex &B, int total_parts, cudaStream_t s);
@@ -263,6 +320,10 @@ void launch_link(int storage, const Lat &L, const LinkList &ll, const float *rho
                  const Parts &P, void *fout, cudaStream_t s);
 void launch_pairs(const Lat &L, const Parts &P, const Pair &pp, const Cells &C, cudaStream_t s);
 void launch_integrate(const Lat &L, const Parts &P, int mode, cudaStream_t s);
+// Coverage geometry of the particles (old and current), once per update;
+// geom_bytes_per_particle() is the size of one particle's record.
+void launch_geom(const Lat &L, const Parts &P, cudaStream_t s);
+size_t geom_bytes_per_particle();
 void launch_claim(const Lat &L, const Parts &P, int first, uint32_t *owner_new, cudaStream_t s);
 void launch_transition(int storage, const Lat &L, const Parts &P, void *f, uint8_t *type,
                        const uint32_t *owner_old, const uint32_t *owner_new, int placement,

@@ -195,6 +195,199 @@ __device__ __forceinline__ double box_disp(const Lat &L, const Box &b, int k, in
 
 __device__ __forceinline__ bool is_wall_z(const Lat &L, int z) { return L.walls && (z == 0 || z == L.nz - 1); }
 
+// ---- candidate rows -------------------------------------------------------
+// Along a row of the box (fixed unwrapped y, z) the nodes the inside test
+// can accept lie in one x interval: where the quadric of the ellipsoid is
+// at most 1.  The interval of the quadric at most QSPAN, widened by a node
+// on each side, holds all of them whatever the FP32 rounding of its
+// computation (relative errors ~1e-6 against a margin of ~1% of the radii),
+// so only those candidates are tested.  Boxes that span a whole period use
+// the plain box loop.
+constexpr float QSPAN = 1.02f;
+
+// x interval [xa, xb] (unwrapped, clamped to the box) of row (u1, u2) for
+// the ellipsoid g at X; xa > xb when the row misses it.
+__device__ __forceinline__ void row_span(const Geo &g, const double X[3], const Box &b, int u1, int u2, int &xa,
+                                         int &xb)
+{
+    const float dy = (float)((double)u1 - X[1]), dz = (float)((double)u2 - X[2]);
+    const float w[3] = {g.ip2f, g.io2f, g.io2f};
+    float A = 0.f, B = 0.f, C = -QSPAN;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float r0 = g.R32[0][k], ck = __fmaf_rn(g.R32[1][k], dy, __fmul_rn(g.R32[2][k], dz));
+        A = __fmaf_rn(w[k] * r0, r0, A);
+        B = __fmaf_rn(2.f * w[k] * r0, ck, B);
+        C = __fmaf_rn(w[k] * ck, ck, C);
+    }
+    const float D = __fmaf_rn(B, B, -4.f * A * C);
+    xa = 1;
+    xb = 0;
+    if (!(D >= 0.f) || !(A > 0.f)) return;
+    const float sq = sqrtf(D), ia = 0.5f / A;
+    const double lo = X[0] + (double)((-B - sq) * ia), hi = X[0] + (double)((-B + sq) * ia);
+    if (!(lo >= -2e9 && hi <= 2e9)) return;
+    xa = max((int)floor(lo) - 1, b.lo[0]);
+    xb = min((int)ceil(hi) + 1, b.lo[0] + b.ext[0] - 1);
+}
+
+__device__ __forceinline__ bool box_full(const Box &b) { return b.full[0] || b.full[1] || b.full[2]; }
+
+// Every candidate node of a particle's box, each visited once.  Each warp
+// takes chunks of 32 rows: lane l computes the NSEG disjoint segments
+// [xs[j], xe[j]] of row l of the chunk (spans(u1, u2, xs, xe), empty when
+// xs > xe, clamped to the box); a warp prefix over the rows' candidate
+// counts flattens them, and the lanes take consecutive candidates.  No
+// barrier: the warps of a CTA work on their own rows.  node(ux, u1, u2,
+// valid) is called by all 32 lanes of a warp in whole passes (valid =
+// false past the end), so it may use warp votes.  A box that spans a whole
+// period visits all its nodes.
+template <int NSEG, class SP, class F>
+__device__ __forceinline__ void for_segments(const Box &b, SP spans, F node)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (box_full(b)) {
+        for (int k0 = warp * 32; k0 < b.count; k0 += nw * 32) {
+            const int k = k0 + lane;
+            const bool valid = k < b.count;
+            const int kk = valid ? k : 0;
+            const int t = kk / b.ext[0];
+            node(b.lo[0] + kk % b.ext[0], b.lo[1] + t % b.ext[1], b.lo[2] + t / b.ext[1], valid);
+        }
+        return;
+    }
+    const int rows = b.ext[1] * b.ext[2];
+    for (int r0 = warp * 32; r0 < rows; r0 += nw * 32) {
+        const int r = r0 + lane;
+        int xs[NSEG], len[NSEG];
+        int tot = 0;
+        if (r < rows) {
+            int xe[NSEG];
+            spans(b.lo[1] + r % b.ext[1], b.lo[2] + r / b.ext[1], xs, xe);
+#pragma unroll
+            for (int j = 0; j < NSEG; j++) {
+                len[j] = max(0, xe[j] - xs[j] + 1);
+                tot += len[j];
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < NSEG; j++) {
+                xs[j] = 0;
+                len[j] = 0;
+            }
+        }
+        int incl = tot;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(full, incl, off);
+            if (lane >= off) incl += v;
+        }
+        const int excl = incl - tot;
+        const int total = __shfl_sync(full, incl, 31);
+        for (int k0 = 0; k0 < total; k0 += 32) {
+            const int k = k0 + lane;
+            const bool valid = k < total;
+            // the row (lane) holding candidate k: last lane with excl <= k
+            int src = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int e = __shfl_sync(full, excl, src + step);
+                if (e <= k) src += step;
+            }
+            int rem = k - __shfl_sync(full, excl, src);
+            int ux = 0;
+            bool found = false;
+#pragma unroll
+            for (int j = 0; j < NSEG; j++) {
+                const int xj = __shfl_sync(full, xs[j], src), lj = __shfl_sync(full, len[j], src);
+                if (!found && rem < lj) {
+                    ux = xj + rem;
+                    found = true;
+                } else if (!found) {
+                    rem -= lj;
+                }
+            }
+            const int rr = r0 + src;
+            node(ux, b.lo[1] + rr % b.ext[1], b.lo[2] + rr / b.ext[1], valid);
+        }
+    }
+}
+
+// The candidates of one ellipsoid (g at X) in box b.
+template <class F>
+__device__ __forceinline__ void for_candidates(const Box &b, const Geo &g, const double X[3], F node)
+{
+    for_segments<1>(b, [&](int u1, int u2, int *xs, int *xe) { row_span(g, X, b, u1, u2, xs[0], xe[0]); }, node);
+}
+
+// ---- coverage geometry ----------------------------------------------------
+// The geometry the coverage kernels need of a particle, computed once per
+// step by one thread per particle (k_geom) instead of by every CTA: the
+// rotation and inverse squared radii, the centre the box was formed around
+// with its integer and FP32 parts, and the box.
+struct PGeom {
+    Geo g;
+    double X[3];
+    int Xi[3];
+    float Xf[3];
+    Box box;
+};
+
+// Old geometry (the last coverage update's) and new geometry, and for the
+// transition the new centre unwrapped next to the old one and the union of
+// the two boxes.
+struct PGeom2 {
+    PGeom old_, now;
+    double Xu[3];
+    Box uni;
+};
+
+__device__ void pgeom_of(const Lat &L, const double *X, const double *q, double rp, double ro, PGeom &o)
+{
+    geo_of(q, rp, ro, o.g);
+    double lo[3], hi[3];
+    box_of(L, X, o.g.R, rp, ro, lo, hi);
+    finish_box(L, lo, hi, o.box);
+    for (int k = 0; k < 3; k++) {
+        o.X[k] = X[k];
+        // X = Xi + Xf, Xi integral: the FP32 displacement (u - Xi) - Xf
+        // carries no large cancellation (box_of bounds |X| < 1e9)
+        const double fl = floor(X[k]);
+        o.Xi[k] = o.box.count ? (int)fl : 0;
+        o.Xf[k] = (float)(X[k] - fl);
+    }
+}
+
+__device__ __forceinline__ void geom_body(const Lat &L, const Parts &P, int p)
+{
+    PGeom2 &G = reinterpret_cast<PGeom2 *>(P.geo)[p];
+    pgeom_of(L, P.Xold + 3 * p, P.qold + 4 * p, P.rp[p], P.ro[p], G.old_);
+    pgeom_of(L, P.X + 3 * p, P.q + 4 * p, P.rp[p], P.ro[p], G.now);
+    double lo[3], hi[3], lo2[3], hi2[3];
+    for (int k = 0; k < 3; k++) G.Xu[k] = P.Xold[3 * p + k] + pair_disp(L, k, P.Xold[3 * p + k], P.X[3 * p + k]);
+    box_of(L, P.Xold + 3 * p, G.old_.g.R, P.rp[p], P.ro[p], lo, hi);
+    box_of(L, G.Xu, G.now.g.R, P.rp[p], P.ro[p], lo2, hi2);
+    if (box_empty(lo, hi)) {
+        for (int k = 0; k < 3; k++) {
+            lo[k] = lo2[k];
+            hi[k] = hi2[k];
+        }
+    } else if (!box_empty(lo2, hi2)) {
+        for (int k = 0; k < 3; k++) {
+            lo[k] = fmin(lo[k], lo2[k]);
+            hi[k] = fmax(hi[k], hi2[k]);
+        }
+    }
+    finish_box(L, lo, hi, G.uni);
+}
+
+__global__ void k_geom(Lat L, Parts P)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < P.n) geom_body(L, P, p);
+}
+
 // Fixed-order block reduction of K doubles (PT threads).
 template <int K>
 __device__ void block_sum(double (&v)[K], double (*sh)[PT / 32])
@@ -843,45 +1036,28 @@ __global__ void k_integrate(Lat L, Parts P, int mode)
 
 __device__ __forceinline__ void claim_body(const Lat &L, const Parts &P, int p, uint32_t *__restrict__ owner_new)
 {
-    __shared__ Box box;
-    __shared__ Geo geo;
-    __shared__ double sX[3];
-    __shared__ int sXi[3];
-    __shared__ float sXf[3];
-    if (threadIdx.x == 0) {
-        geo_of(P.q + 4 * p, P.rp[p], P.ro[p], geo);
-        double lo[3], hi[3];
-        box_of(L, P.X + 3 * p, geo.R, P.rp[p], P.ro[p], lo, hi);
-        finish_box(L, lo, hi, box);
-        for (int k = 0; k < 3; k++) {
-            sX[k] = P.X[3 * p + k];
-            // X = Xi + Xf, Xi integral: the FP32 displacement (u - Xi) - Xf
-            // carries no large cancellation (box_of bounds |X| < 1e9)
-            double fl = floor(sX[k]);
-            sXi[k] = box.count ? (int)fl : 0;
-            sXf[k] = (float)(sX[k] - fl);
-        }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < box.count; k += PT) {
-        int x, y, z, u[3];
-        box_node(L, box, k, u, x, y, z);
-        if (is_wall_z(L, z)) continue;
+    const PGeom &G = reinterpret_cast<const PGeom2 *>(P.geo)[p].now;
+    const Box &box = G.box;
+    for_candidates(box, G.g, G.X, [&](int ux, int u1, int u2, bool valid) {
+        if (!valid) return;
+        const int u[3] = {ux, u1, u2};
+        const int x = wrapi(ux, L.nx), y = wrapi(u1, L.ny), z = wrapi(u2, L.nz);
+        if (is_wall_z(L, z)) return;
         float d32[3];
 #pragma unroll
         for (int a = 0; a < 3; a++)
-            d32[a] = box.full[a] ? (float)node_disp(L, a, a == 0 ? x : (a == 1 ? y : z), sX[a])
-                                 : (float)(u[a] - sXi[a]) - sXf[a];
+            d32[a] = box.full[a] ? (float)node_disp(L, a, a == 0 ? x : (a == 1 ? y : z), G.X[a])
+                                 : (float)(u[a] - G.Xi[a]) - G.Xf[a];
         float q32;
-        bool in = inside_q32(geo, d32, q32);
+        bool in = inside_q32(G.g, d32, q32);
         if (!in && q32 <= 1.001f) {
-            double dx[3] = {box_disp(L, box, 0, u[0], x, sX[0]), box_disp(L, box, 1, u[1], y, sX[1]),
-                            box_disp(L, box, 2, u[2], z, sX[2])};
-            in = inside_exact(geo, dx);
+            double dx[3] = {box_disp(L, box, 0, u[0], x, G.X[0]), box_disp(L, box, 1, u[1], y, G.X[1]),
+                            box_disp(L, box, 2, u[2], z, G.X[2])};
+            in = inside_exact(G.g, dx);
         }
         int n = x + L.nx * (y + L.ny * z);
         if (in && idx_ok(L, n, L.N, 4)) atomicMin(owner_new + n, (uint32_t)p);
-    }
+    });
 }
 
 __global__ void __launch_bounds__(PT) k_claim(Lat L, Parts P, uint32_t *__restrict__ owner_new)
@@ -903,53 +1079,27 @@ __device__ __forceinline__ void transition_body(const Lat &L, const Parts &P, in
                                                 uint8_t *__restrict__ type, const uint32_t *__restrict__ own_old,
                                                 const uint32_t *__restrict__ own_new, int placement)
 {
-    __shared__ Box box;
-    __shared__ double sX[3], sV[3], sW[3];
     __shared__ double red[6][PT / 32];
-    if (threadIdx.x == 0) {
-        double Ro[3][3], Rn[3][3];
-        rotmat(P.qold + 4 * p, Ro);
-        rotmat(P.q + 4 * p, Rn);
-        double Xo[3], Xu[3];
-        for (int k = 0; k < 3; k++) {
-            Xo[k] = P.Xold[3 * p + k];
-            Xu[k] = Xo[k] + pair_disp(L, k, Xo[k], P.X[3 * p + k]);
-        }
-        // union of the old and new boxes (either may be empty)
-        double lo[3], hi[3], lo2[3], hi2[3];
-        box_of(L, Xo, Ro, P.rp[p], P.ro[p], lo, hi);
-        box_of(L, Xu, Rn, P.rp[p], P.ro[p], lo2, hi2);
-        if (box_empty(lo, hi)) {
-            for (int k = 0; k < 3; k++) {
-                lo[k] = lo2[k];
-                hi[k] = hi2[k];
-            }
-        } else if (!box_empty(lo2, hi2)) {
-            for (int k = 0; k < 3; k++) {
-                lo[k] = fmin(lo[k], lo2[k]);
-                hi[k] = fmax(hi[k], hi2[k]);
-            }
-        }
-        finish_box(L, lo, hi, box);
-        for (int k = 0; k < 3; k++) {
-            sX[k] = P.X[3 * p + k];
-            sV[k] = P.V[3 * p + k];
-            sW[k] = P.W[3 * p + k];
-        }
-    }
-    __syncthreads();
+    const PGeom2 &G2 = reinterpret_cast<const PGeom2 *>(P.geo)[p];
+    const Box &box = G2.uni;
+    const Geo &gold = G2.old_.g, &gnew = G2.now.g;
+    const double *sXo = G2.old_.X, *sXu = G2.Xu;
+    const double sX[3] = {P.X[3 * p], P.X[3 * p + 1], P.X[3 * p + 2]};
+    const double sV[3] = {P.V[3 * p], P.V[3 * p + 1], P.V[3 * p + 2]};
+    const double sW[3] = {P.W[3 * p], P.W[3 * p + 1], P.W[3 * p + 2]};
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int k = threadIdx.x; k < box.count; k += PT) {
-        int x, y, z, u[3];
-        box_node(L, box, k, u, x, y, z);
+    // a node whose owner changed lies in the old or the new ellipsoid of the
+    // lower of its owners: the candidates of the old, then those of the new
+    // not already visited
+    auto visit = [&](int x, int y, int z) {
         int n = x + L.nx * (y + L.ny * z);
-        if (!idx_ok(L, n, L.N, 5)) continue;
+        if (!idx_ok(L, n, L.N, 5)) return;
         uint32_t o = own_old[n], w = own_new[n];
-        if (o == w) continue;
-        if (min(o, w) != (uint32_t)p) continue;
+        if (o == w) return;
+        if (min(o, w) != (uint32_t)p) return;
         if (o == NONE) {
             type[n] = PART;
-            if (placement) continue;
+            if (placement) return;
             double mom[3] = {0, 0, 0};
 #pragma unroll
             for (int c = 0; c < 2; c++)
@@ -969,7 +1119,7 @@ __device__ __forceinline__ void transition_body(const Lat &L, const Parts &P, in
             }
         } else if (w == NONE) {
             type[n] = FLUID;
-            if (placement) continue;
+            if (placement) return;
             float sr0 = 0.f, sr1 = 0.f;
             int cnt = 0;
             for (int i = 1; i < Q; i++) {
@@ -1015,7 +1165,24 @@ __device__ __forceinline__ void transition_body(const Lat &L, const Parts &P, in
                 acc[3 + k2] -= t[k2];
             }
         }
-    }
+    };
+    // per row: the old span, then the new span's parts left and right of it
+    for_segments<3>(
+        box,
+        [&](int u1, int u2, int *xs, int *xe) {
+            int a0, b0, a1, b1;
+            row_span(gold, sXo, box, u1, u2, a0, b0);
+            row_span(gnew, sXu, box, u1, u2, a1, b1);
+            xs[0] = a0;
+            xe[0] = b0;
+            xs[1] = a1;
+            xe[1] = a0 <= b0 ? min(b1, a0 - 1) : b1;
+            xs[2] = a0 <= b0 ? max(a1, b0 + 1) : 1;
+            xe[2] = a0 <= b0 ? b1 : 0;
+        },
+        [&](int ux, int u1, int u2, bool valid) {
+            if (valid) visit(wrapi(ux, L.nx), wrapi(u1, L.ny), wrapi(u2, L.nz));
+        });
     if (placement) return;
     block_sum<6>(acc, red);
     if (threadIdx.x == 0) {
@@ -1043,28 +1210,63 @@ __global__ void __launch_bounds__(PT) k_transition(Lat L, Parts P, typename S::T
 __device__ __forceinline__ void reset_body(const Lat &L, const Parts &P, int p, int use_old,
                                            uint32_t *__restrict__ owner)
 {
-    __shared__ Box box;
-    if (threadIdx.x == 0) {
-        const double *q = use_old ? P.qold + 4 * p : P.q + 4 * p;
-        const double *X = use_old ? P.Xold + 3 * p : P.X + 3 * p;
-        double R[3][3];
-        rotmat(q, R);
-        double lo[3], hi[3];
-        box_of(L, X, R, P.rp[p], P.ro[p], lo, hi);
-        finish_box(L, lo, hi, box);
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < box.count; k += PT) {
-        int x, y, z, u[3];
-        box_node(L, box, k, u, x, y, z);
-        int n = x + L.nx * (y + L.ny * z);
+    // The map holds, over this particle's box, only nodes inside its
+    // ellipsoid (its own) or inside other particles' (cleared by them), so
+    // clearing its own candidates empties the map.
+    const PGeom2 &G2 = reinterpret_cast<const PGeom2 *>(P.geo)[p];
+    const PGeom &G = use_old ? G2.old_ : G2.now;
+    for_candidates(G.box, G.g, G.X, [&](int ux, int u1, int u2, bool valid) {
+        if (!valid) return;
+        int n = wrapi(ux, L.nx) + L.nx * (wrapi(u1, L.ny) + L.ny * wrapi(u2, L.nz));
         if (idx_ok(L, n, L.N, 7)) owner[n] = NONE;
-    }
+    });
 }
 
 __global__ void __launch_bounds__(PT) k_reset(Lat L, Parts P, int use_old, uint32_t *__restrict__ owner)
 {
     reset_body(L, P, blockIdx.x, use_old, owner);
+}
+
+// ---------------------------------------------------------------- shell
+// Shell fill (Eq. 10 and the colour rule) of the nodes particle p owns,
+// over its candidate rows; its nodes with fluid neighbours enter the link
+// list.  With the wall planes these are all the solid nodes a fluid node
+// can see.
+__global__ void __launch_bounds__(PT) k_shell_particles(Lat L, Parts P, const float *__restrict__ rho,
+                                                        float *__restrict__ psi, const uint8_t *__restrict__ type,
+                                                        const uint32_t *__restrict__ owner, LinkList ll)
+{
+    const int p = blockIdx.x;
+    const PGeom &G = reinterpret_cast<const PGeom2 *>(P.geo)[p].now;
+    const Box &box = G.box;
+    const Geo &geo = G.g;
+    const double *sX = G.X;
+    const float dr = (float)P.drho[p];
+    for_candidates(box, geo, sX, [&](int ux, int u1, int u2, bool valid) {
+        int n = 0;
+        uint32_t fm = 0;
+        if (valid) {
+            const int x = wrapi(ux, L.nx), y = wrapi(u1, L.ny), z = wrapi(u2, L.nz);
+            n = x + L.nx * (y + L.ny * z);
+            if (owner[n] == (uint32_t)p)
+                fm = shell_fill(L, rho, psi, type, n, dr, [&](int i) { return nbr_node(L, x, y, z, i); });
+        }
+        if (ll.ent) append_links(ll, n, fm);
+    });
+}
+
+// Shell fill of the wall planes z = 0 and nz - 1 (Δρ = 0).
+__global__ void k_shell_walls(Lat L, const float *__restrict__ rho, float *__restrict__ psi,
+                              const uint8_t *__restrict__ type)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nxy = L.nx * L.ny;
+    if (k >= 2 * nxy) return;
+    const int z = k < nxy ? 0 : L.nz - 1, r = k < nxy ? k : k - nxy;
+    const int x = r % L.nx, y = r / L.nx;
+    const int n = x + L.nx * (y + L.ny * z);
+    if (type[n] != WALL) return;
+    shell_fill(L, rho, psi, type, n, 0.f, [&](int i) { return nbr_node(L, x, y, z, i); });
 }
 
 // ------------------------------------------------------------- batched
@@ -1099,6 +1301,16 @@ __global__ void __launch_bounds__(PT) k_reset_batch(BatchIndex B, int total)
     const BoxDev &bx = B.box[b];
     if (bx.mode == LBE_PARTICLES_STATIC) return;
     reset_body(bx.L, bx.P, g - B.part0[b], 1, bx.owner[B.par[2 * b + 1]]);
+}
+
+__global__ void k_geom_batch(BatchIndex B, int total)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int b = find_box(B.part0, B.nbox, g);
+    const BoxDev &bx = B.box[b];
+    if (bx.mode == LBE_PARTICLES_STATIC) return;
+    geom_body(bx.L, bx.P, g - B.part0[b]);
 }
 
 __global__ void k_integrate_batch(BatchIndex B, int total)
@@ -1184,6 +1396,11 @@ void launch_integrate_batch(const BatchIndex &B, int total, cudaStream_t s)
     if (total > 0) k_integrate_batch<<<(total + 127) / 128, 128, 0, s>>>(B, total);
 }
 
+void launch_geom_batch(const BatchIndex &B, int total, cudaStream_t s)
+{
+    if (total > 0) k_geom_batch<<<(total + 127) / 128, 128, 0, s>>>(B, total);
+}
+
 void launch_claim_batch(const BatchIndex &B, int total, cudaStream_t s)
 {
     if (total > 0) k_claim_batch<<<total, PT, 0, s>>>(B, total);
@@ -1238,6 +1455,14 @@ void launch_pairs(const Lat &L, const Parts &P, const Pair &pp, const Cells &C, 
     k_pairs<<<b, 128, 0, s>>>(L, P, pp, C);
 }
 
+void launch_geom(const Lat &L, const Parts &P, cudaStream_t s)
+{
+    if (P.n == 0) return;
+    k_geom<<<(P.n + 127) / 128, 128, 0, s>>>(L, P);
+}
+
+size_t geom_bytes_per_particle() { return sizeof(PGeom2); }
+
 void launch_integrate(const Lat &L, const Parts &P, int mode, cudaStream_t s)
 {
     if (P.n == 0) return;
@@ -1278,6 +1503,20 @@ void launch_link_batch(int storage, const BatchIndex &B, cudaStream_t s)
 {
     dim3 grid(LINK_BATCH_CTAS, B.nbox);
     LBE_DISPATCH(storage, (k_link_batch<S><<<grid, 256, 0, s>>>(B)));
+}
+
+void launch_shell_particles(const Lat &L, const Parts &P, const float *rho, float *psi, const uint8_t *type,
+                            const uint32_t *owner, const LinkList &ll, cudaStream_t s)
+{
+    if (P.n == 0) return;
+    k_shell_particles<<<P.n, PT, 0, s>>>(L, P, rho, psi, type, owner, ll);
+}
+
+void launch_shell_walls(const Lat &L, const float *rho, float *psi, const uint8_t *type, cudaStream_t s)
+{
+    if (!L.walls) return;
+    const int n = 2 * L.nx * L.ny;
+    k_shell_walls<<<(n + 255) / 256, 256, 0, s>>>(L, rho, psi, type);
 }
 
 void launch_reset(const Lat &L, const Parts &P, int use_old, uint32_t *owner, cudaStream_t s)

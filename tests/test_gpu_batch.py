@@ -92,7 +92,7 @@ def test_batch_matches_members_stepped_alone(storage):
     alone = [m(storage) for m in MAKERS]
     mixed = [m(storage) for m in MAKERS]
     batch = lbe.Batch(mixed)
-    assert batch.kernels_per_step() == 10
+    assert batch.kernels_per_step() == 11
     for g in alone:
         g.step(30)
     batch.step(30)
@@ -111,7 +111,7 @@ def test_member_alone_or_in_a_mix_is_identical():
     b1.step(25)
     b2.step(25)
     assert _equal(_state(solo), _state(mix[MAKERS.index(_pair)]))
-    assert b1.kernels_per_step() == 10
+    assert b1.kernels_per_step() == 11
 
 
 def test_odd_steps_and_interleaving_with_member_steps():
