@@ -482,11 +482,12 @@ __global__ void __launch_bounds__(NT, 3) k_fused_batch(BatchIndex B, int total)
 
 int fused_zchunk(const Lat &L)
 {
-    // enough CTAs to fill the GPU several times over, each chunk long enough
-    // that its two extra halo planes cost little
+    // About 16 waves of CTAs (three per SM on 152 SMs), so the last wave's
+    // idle SMs cost little, each chunk long enough (>= 16 planes where the
+    // lattice allows) that its extra halo planes cost little.
     long long cols = (long long)((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY);
     int zc = L.nz;
-    while (zc > 16 && cols * ((L.nz + zc - 1) / zc) < 8 * 152) zc = (zc + 1) / 2;
+    while (zc > 16 && cols * ((L.nz + zc - 1) / zc) < 48 * 152) zc = (zc + 1) / 2;
     return zc;
 }
 
