@@ -51,6 +51,8 @@ def parse(argv=None):
     ap.add_argument("--rate", type=float, default=50.0, help="serving: Poisson arrival rate (1/s)")
     ap.add_argument("--n", type=int, default=None, help="lattice edge (default: the workload's)")
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default=None)
+    ap.add_argument("--zchunk", type=int, default=0,
+                    help="fused-kernel z chunk in planes (default 0: the library's autotuner picks it)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args(argv)
@@ -251,7 +253,11 @@ def run_ours(args):
                       **w.params)
     add_particles(lat, w)
     lat.step(args.warmup)
-    zc = lat.autotune()  # the library's z-chunk autotuner (CUDA events, state unchanged)
+    if args.zchunk > 0:
+        lat.set_zchunk(args.zchunk)
+        zc = args.zchunk
+    else:
+        zc = lat.autotune()  # the library's z-chunk autotuner (CUDA events, state unchanged)
     torch.cuda.synchronize()
     lat.profile_enable(True)
     clocks = Clocks(dist.local)

@@ -187,6 +187,12 @@ LBE_API lbe_status lbe_mass_noalloc(const void *f, int32_t storage, const uint8_
  * later steps use the fastest.  *chosen_zc (may be NULL) receives it. */
 LBE_API lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc);
 
+/* Set the fused kernel's z-chunk length (planes per CTA; 0 restores the
+ * default, sized for about 16 waves of CTAs).  A chunk longer than the
+ * lattice is clipped.  Only the order in which tiles run depends on it,
+ * never a result.  LBE_EINVAL for a negative length. */
+LBE_API lbe_status lbe_set_zchunk(lbe_ctx *c, int32_t zc);
+
 /* Batches: several lattices stepped together, every kernel of the step
  * covering all of them in one launch (the fused fluid kernel as a persistent
  * kernel taking tiles of all boxes from one queue), replayed as a captured

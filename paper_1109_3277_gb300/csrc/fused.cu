@@ -208,7 +208,9 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
         if (L.walls) {
             zin = zz >= 0 && zz < L.nz;
         } else {
-            gz = zz < 0 ? zz + L.nz : (zz >= L.nz ? zz - L.nz : zz);
+            // planes -1 .. nz+1: two wraps when nz = 1
+            gz = zz < 0 ? zz + L.nz : zz;
+            while (gz >= L.nz) gz -= L.nz;
         }
         if (zin) {
             const int n = own2 + nxy * gz;

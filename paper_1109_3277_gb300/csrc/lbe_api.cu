@@ -785,6 +785,14 @@ lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc)
     return sync(c, "autotune");
 }
 
+lbe_status lbe_set_zchunk(lbe_ctx *c, int32_t zc)
+{
+    if (!c || zc < 0) return LBE_EINVAL;
+    c->zc_tuned = zc < c->L.nz ? zc : c->L.nz;
+    drop_graphs(c);
+    return LBE_OK;
+}
+
 }  // extern "C"
 
 // ----------------------------------------------------------------- batches

@@ -66,6 +66,7 @@ SIGNATURES = {
     "lbe_mass_noalloc": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_int64, _D,
                                          ctypes.c_int32, _P, _P]),
     "lbe_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "lbe_set_zchunk": (ctypes.c_int, [_P, ctypes.c_int32]),
     "lbe_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_P)]),
     "lbe_batch_step": (ctypes.c_int, [_P, ctypes.c_int32]),
     "lbe_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
@@ -227,6 +228,10 @@ class Lattice:
         zc = ctypes.c_int32()
         self._check(load().lbe_autotune(self._ptr, ctypes.byref(zc)), "autotune")
         return zc.value
+
+    def set_zchunk(self, zc):
+        """Fix the fused kernel's z chunk (0: default); results do not depend on it."""
+        self._check(load().lbe_set_zchunk(self._ptr, int(zc)), "set_zchunk")
 
     def device_bytes(self):
         return int(load().lbe_device_bytes(self._ptr))

@@ -152,6 +152,13 @@ def test_autotuners_keep_results_bit_identical():
     a.step(20)
     b.step(20)
     assert _equal(_state(a), _state(b))
+    for z in (1, 5, 10 ** 6, 0):
+        a.set_zchunk(z)
+        a.step(4)
+        b.step(4)
+        assert _equal(_state(a), _state(b)), z
+    with pytest.raises(lbe.LbeError):
+        a.set_zchunk(-1)
     m1 = [m() for m in MAKERS]
     m2 = [m() for m in MAKERS]
     b1, b2 = lbe.Batch(m1), lbe.Batch(m2)

@@ -36,11 +36,15 @@ def _add(g, r, **p):
 @pytest.mark.parametrize("shape,walls,tau", [((8, 8, 8), False, (1.0, 1.0)),
                                              ((13, 7, 5), True, (0.8, 1.3)),
                                              ((33, 17, 9), False, (1.0, 0.7)),
-                                             ((70, 35, 40), True, (1.0, 1.0))])
+                                             ((70, 35, 40), True, (1.0, 1.0)),
+                                             ((1, 1, 1), False, (1.0, 1.0)),
+                                             ((3, 2, 1), False, (0.9, 1.1)),
+                                             ((2, 1, 3), True, (1.0, 1.0))])
 def test_one_step_populations(shape, walls, tau, flags):
-    """Several tiles plus a ragged tail (the fused kernel's tiles are 32x16
+    """Several tiles plus a ragged tail (the fused kernel's tiles are 32x8
     and walk z in chunks), walls or not, τ ≠ 1; fused and two-pass fluid
-    kernels."""
+    kernels.  Degenerate lattices: one node (every neighbour is the node
+    itself), a single periodic plane, and one fluid plane between walls."""
     nx, ny, nz = shape
     f0 = W.random_populations(shape, seed=21)
     g = lbe.Lattice(shape, np.full((2, nz, ny, nx), 0.5), walls_z=walls, tau=tau, g_br=0.1,
