@@ -107,8 +107,9 @@ __global__ void __launch_bounds__(256) k_moments(Lat L, const typename S::T *__r
 // ------------------------------------------------------------ densities
 // ρ^c = Σ_i f_i^c on every fluid node, for the shell fill and the link
 // kernel, and ψ^c = 1 - exp(-ρ^c) for the fused kernel (which sums its own
-// nodes' populations in the same order, so the two agree bit for bit; the
-// shell fill writes ψ of the solid nodes into the same array).  One thread
+// nodes' stored populations in the same order and adds ρ_ref the same way,
+// so the two agree bit for bit; the shell fill writes ψ of the solid nodes
+// into the same array).  One thread
 // per pair of consecutive nodes, with paired loads; the slot stride S is
 // padded past N, so the pair loads of the last node stay inside the
 // allocation.
@@ -125,15 +126,19 @@ __global__ void __launch_bounds__(256) k_rho(Lat L, const typename S::T *__restr
     if (!fl0 && !fl1) return;
 #pragma unroll
     for (int c = 0; c < 2; c++) {
+        // Σ_i of the stored quantities (δf_i, or f_i in FP32) in index
+        // order, plus ρ_ref (0 in FP32)
         float a0, a1;
-        S::ld2(slot<S>(f, L, c, 0) + n, L.base[c][0], a0, a1);
+        S::ld2(slot<S>(f, L, c, 0) + n, 0.f, a0, a1);
 #pragma unroll
         for (int i = 1; i < Q; i++) {
             float v0, v1;
-            S::ld2(slot<S>(f, L, c, i) + n, L.base[c][i], v0, v1);
-            a0 += v0;
-            a1 += v1;
+            S::ld2(slot<S>(f, L, c, i) + n, 0.f, v0, v1);
+            a0 = __fadd_rn(a0, v0);
+            a1 = __fadd_rn(a1, v1);
         }
+        a0 = __fadd_rn(L.rref[c], a0);
+        a1 = __fadd_rn(L.rref[c], a1);
         if (fl0) {
             rho[(size_t)c * L.N + n] = a0;
             psi[(size_t)c * L.N + n] = 1.f - expf(-a0);
@@ -222,9 +227,10 @@ __global__ void __launch_bounds__(256) k_rho_batch(BatchIndex B, int total)
         const typename S::T *f = (const typename S::T *)bx.f[B.par[2 * b]];
 #pragma unroll
         for (int c = 0; c < 2; c++) {
-            float r = S::ld(slot<S>(f, bx.L, c, 0) + s.n, bx.L.base[c][0]);
+            float r = S::ld(slot<S>(f, bx.L, c, 0) + s.n, 0.f);
 #pragma unroll
-            for (int i = 1; i < Q; i++) r += S::ld(slot<S>(f, bx.L, c, i) + s.n, bx.L.base[c][i]);
+            for (int i = 1; i < Q; i++) r = __fadd_rn(r, S::ld(slot<S>(f, bx.L, c, i) + s.n, 0.f));
+            r = __fadd_rn(bx.L.rref[c], r);
             bx.rho[(size_t)c * bx.L.N + s.n] = r;
             bx.psi[(size_t)c * bx.L.N + s.n] = 1.f - expf(-r);
         }

@@ -21,6 +21,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <type_traits>
+
 #include "lbe_internal.cuh"
 
 namespace lbe {
@@ -120,24 +122,27 @@ __device__ __forceinline__ void tma_plane(void *dst, const CUtensorMap *map, int
 // (components 0 or ±1) are exact and stay plain.
 
 // Equilibrium velocity of component c, u' + (τ_c/ρ_c) F^c with the
-// Shan–Chen force F^c = -g ψ^c s^c + ρ^c g_body (Eq. 3), and 1 - 1.5 u·u.
+// Shan–Chen force F^c = -g ψ^c s^c + ρ^c g_body (Eq. 3), and -1.5 u·u.
 __device__ __forceinline__ void eq_velocity(const Lat &L, int c, float r, float pc, const float s[3],
-                                            const float up[3], float ue[3], float &uu15)
+                                            const float up[3], float ue[3], float &um15)
 {
     const float ir = r > 0.f ? __fdiv_rn(L.tau[c], r) : 0.f;
     const float gp = __fmul_rn(-L.g, pc);
 #pragma unroll
     for (int k = 0; k < 3; k++) ue[k] = __fmaf_rn(ir, __fmaf_rn(gp, s[k], __fmul_rn(r, L.body[k])), up[k]);
     const float uu = __fmaf_rn(ue[0], ue[0], __fmaf_rn(ue[1], ue[1], __fmul_rn(ue[2], ue[2])));
-    uu15 = __fmaf_rn(-1.5f, uu, 1.f);
+    um15 = __fmul_rn(-1.5f, uu);
 }
 
-// Even and odd parts of f^eq_i = w_i ρ (1 + 3 c·u + 4.5 (c·u)^2 - 1.5 u·u).
-__device__ __forceinline__ void feq_parts(float w, float r, float cu, float uu15, float &even, float &odd)
+// f^eq_i = w_i ρ (1 + 3 c·u + 4.5 (c·u)^2 - 1.5 u·u) relative to the stored
+// quantity's base w_i ρ_ref: even part w_i (ρ (4.5 (c·u)^2 - 1.5 u·u) + Δρ)
+// with Δρ = ρ - ρ_ref (for FP32 storage ρ_ref = 0, Δρ = ρ), odd part
+// 3 w_i ρ c·u (w3r = 3 w_i ρ comes per weight).
+__device__ __forceinline__ void feq_parts(float w, float r, float dr, float w3r, float cu, float um15,
+                                          float &even, float &odd)
 {
-    const float wr = __fmul_rn(w, r);
-    even = __fmul_rn(wr, __fmaf_rn(__fmul_rn(4.5f, cu), cu, uu15));
-    odd = __fmul_rn(__fmul_rn(3.f, wr), cu);
+    even = __fmul_rn(w, __fmaf_rn(r, __fmaf_rn(__fmul_rn(4.5f, cu), cu, um15), dr));
+    odd = __fmul_rn(w3r, cu);
 }
 
 // BGK relaxation f + (f^eq - f)/τ.
@@ -289,27 +294,30 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
             const int n = own2 + nxy * z;
             const bool inner = xy_inner && z >= 1 && z <= L.nz - 2;
             const T *fb = stage + (z & 1) * 2 * Q * NT + tid;
-            // moments: ρ^c (the density kernel's sum, same order), j^c, and
-            // the shifted velocity u' = Σ_c j^c/τ_c / Σ_c ρ^c/τ_c
-            float rho_[2], jj[2][3];
+            // moments from the stored quantities d_i (δf_i in the 16-bit
+            // modes, f_i in FP32): Δρ^c = Σ_i d_i, ρ^c = ρ_ref + Δρ^c, and
+            // j^c = Σ_i c_i d_i (the bases cancel: Σ_i w_i c_i = 0); the
+            // shifted velocity u' = Σ_c j^c/τ_c / Σ_c ρ^c/τ_c
+            float drho[2], rho_[2], jj[2][3];
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                // one pass over opposite pairs (i, i+1), c_{i+1} = -c_i; ρ
-                // accumulates in index order
-                float a = S::cvt(fb[(c * Q) * NT], L.base[c][0]);
+                // one pass over opposite pairs (i, i+1), c_{i+1} = -c_i; the
+                // sum accumulates in index order
+                float a = S::raw(fb[(c * Q) * NT]);
                 float jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
                 for (int i = 1; i < Q; i += 2) {
-                    const float va = S::cvt(fb[(c * Q + i) * NT], L.base[c][i]);
-                    const float vb = S::cvt(fb[(c * Q + i + 1) * NT], L.base[c][i + 1]);
-                    a += va;
-                    a += vb;
-                    const float d = va - vb;
-                    if (cx(i)) jx += cx(i) * d;
-                    if (cy(i)) jy += cy(i) * d;
-                    if (cz(i)) jz += cz(i) * d;
+                    const float va = S::raw(fb[(c * Q + i) * NT]);
+                    const float vb = S::raw(fb[(c * Q + i + 1) * NT]);
+                    a = __fadd_rn(a, va);
+                    a = __fadd_rn(a, vb);
+                    const float d = __fsub_rn(va, vb);
+                    if (cx(i)) jx = __fadd_rn(jx, cx(i) * d);
+                    if (cy(i)) jy = __fadd_rn(jy, cy(i) * d);
+                    if (cz(i)) jz = __fadd_rn(jz, cz(i) * d);
                 }
-                rho_[c] = a;
+                drho[c] = a;
+                rho_[c] = __fadd_rn(L.rref[c], a);
                 jj[c][0] = jx;
                 jj[c][1] = jy;
                 jj[c][2] = jz;
@@ -339,56 +347,75 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
             const float2 pcc = pl[1][ec];
             const float pc[2] = {pcc.x, pcc.y};
             T *dst = fout + n;
-            // Push offsets of nodes on the lattice boundary wrap around the
-            // periodic axes: corrections for c = +1 ([0]) and c = -1 ([1]).
-            int wx[2] = {0, 0}, wy[2] = {0, 0}, wz[2] = {0, 0};
-            if (!inner) {
-                wx[0] = gx == L.nx - 1 ? -L.nx : 0;
-                wx[1] = gx == 0 ? L.nx : 0;
-                wy[0] = gy == L.ny - 1 ? -nxy : 0;
-                wy[1] = gy == 0 ? nxy : 0;
-                if (!L.walls) {  // with walls z = 0 and nz-1 are wall nodes
-                    wz[0] = z == L.nz - 1 ? -L.N : 0;
-                    wz[1] = z == 0 ? L.N : 0;
+            // A warp whose nodes are all off the lattice boundary and have
+            // no solid neighbour pushes every population to its fixed
+            // offset; the others select, per population, between the push
+            // (with the periodic wrap of boundary nodes) and the reflection.
+            const bool clean = __all_sync(__activemask(), inner && solid == 0u);
+            auto collide = [&](auto clean_tag) {
+                constexpr bool CLEAN = decltype(clean_tag)::value;
+                // Push offsets of nodes on the lattice boundary wrap around
+                // the periodic axes: corrections for c = +1 ([0]) and c = -1 ([1]).
+                int wx[2] = {0, 0}, wy[2] = {0, 0}, wz[2] = {0, 0};
+                if (!CLEAN && !inner) {
+                    wx[0] = gx == L.nx - 1 ? -L.nx : 0;
+                    wx[1] = gx == 0 ? L.nx : 0;
+                    wy[0] = gy == L.ny - 1 ? -nxy : 0;
+                    wy[1] = gy == 0 ? nxy : 0;
+                    if (!L.walls) {  // with walls z = 0 and nz-1 are wall nodes
+                        wz[0] = z == L.nz - 1 ? -L.N : 0;
+                        wz[1] = z == 0 ? L.N : 0;
+                    }
                 }
-            }
-            // store of the post-collision population fs of direction i:
-            // pushed to the neighbour, or reflected into slot opp(i) of this
-            // node (walls and particle nodes; the link kernel adds the
-            // moving-boundary term for the latter).  Both slots have the
-            // same weight, hence the same storage offset; the address is a
-            // select, not a branch.
-            auto put = [&](int c, int i, float fs) {
-                const int corr = (cx(i) > 0 ? wx[0] : (cx(i) < 0 ? wx[1] : 0)) +
-                                 (cy(i) > 0 ? wy[0] : (cy(i) < 0 ? wy[1] : 0)) +
-                                 (cz(i) > 0 ? wz[0] : (cz(i) < 0 ? wz[1] : 0));
-                const long long o = ((solid >> i) & 1u) ? ofs.pop[c * Q + opp(i)] : ofs.push[c * Q + i] + corr;
-                S::st(dst + o, fs, L.base[c][i]);
+                // store of the post-collision population fs of direction i:
+                // pushed to the neighbour, or reflected into slot opp(i) of
+                // this node (walls and particle nodes; the link kernel adds
+                // the moving-boundary term for the latter).  Both slots have
+                // the same weight, hence the same storage offset; the
+                // address is a select, not a branch.
+                auto put = [&](int c, int i, float fs) {
+                    if (CLEAN) {
+                        S::st_raw(dst + ofs.push[c * Q + i], fs);
+                    } else {
+                        const int corr = (cx(i) > 0 ? wx[0] : (cx(i) < 0 ? wx[1] : 0)) +
+                                         (cy(i) > 0 ? wy[0] : (cy(i) < 0 ? wy[1] : 0)) +
+                                         (cz(i) > 0 ? wz[0] : (cz(i) < 0 ? wz[1] : 0));
+                        const long long o =
+                            ((solid >> i) & 1u) ? ofs.pop[c * Q + opp(i)] : ofs.push[c * Q + i] + corr;
+                        S::st_raw(dst + o, fs);
+                    }
+                };
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const float r = rho_[c], dr = drho[c];
+                    float ue[3], um15;
+                    eq_velocity(L, c, r, pc[c], s[c], up, ue, um15);
+                    const float it = L.itau[c];
+                    // 3 w ρ per weight (axis 1/18, diagonal 1/36)
+                    const float w3r_a = __fmul_rn(3.f * wgt(1), r), w3r_d = __fmul_rn(3.f * wgt(7), r);
+                    float seq = 0.f;
+                    // opposite pairs share the even part of the equilibrium
+#pragma unroll
+                    for (int i = 1; i < Q; i += 2) {
+                        const float cu = cx(i) * ue[0] + cy(i) * ue[1] + cz(i) * ue[2];
+                        float even, odd;
+                        feq_parts(wgt(i), r, dr, i < 7 ? w3r_a : w3r_d, cu, um15, even, odd);
+                        const float fa = S::raw(fb[(c * Q + i) * NT]);
+                        const float fbv = S::raw(fb[(c * Q + i + 1) * NT]);
+                        seq = __fadd_rn(seq, 2.f * even);
+                        put(c, i, relax(fa, __fadd_rn(even, odd), it));
+                        put(c, i + 1, relax(fbv, __fsub_rn(even, odd), it));
+                    }
+                    // rest population: equilibrium Δρ - Σ_{i>0} f^eq_i in the
+                    // stored quantity (exact mass)
+                    const float f0 = S::raw(fb[(c * Q) * NT]);
+                    S::st_raw(dst + ofs.pop[c * Q], relax(f0, __fsub_rn(dr, seq), it));
+                }
             };
-#pragma unroll
-            for (int c = 0; c < 2; c++) {
-                const float r = rho_[c];
-                float ue[3], uu15;
-                eq_velocity(L, c, r, pc[c], s[c], up, ue, uu15);
-                const float it = L.itau[c];
-
-                float seq = 0.f;
-                // opposite pairs share the even part of the equilibrium
-#pragma unroll
-                for (int i = 1; i < Q; i += 2) {
-                    const float cu = cx(i) * ue[0] + cy(i) * ue[1] + cz(i) * ue[2];
-                    float even, odd;
-                    feq_parts(wgt(i), r, cu, uu15, even, odd);
-                    const float fa = S::cvt(fb[(c * Q + i) * NT], L.base[c][i]);
-                    const float fbv = S::cvt(fb[(c * Q + i + 1) * NT], L.base[c][i + 1]);
-                    seq = __fadd_rn(seq, 2.f * even);
-                    put(c, i, relax(fa, __fadd_rn(even, odd), it));
-                    put(c, i + 1, relax(fbv, __fsub_rn(even, odd), it));
-                }
-                // rest population: equilibrium ρ - Σ_{i>0} f^eq_i (exact mass)
-                const float f0 = S::cvt(fb[(c * Q) * NT], L.base[c][0]);
-                S::st(dst + ofs.pop[c * Q], relax(f0, __fsub_rn(r, seq), it), L.base[c][0]);
-            }
+            if (clean)
+                collide(std::true_type{});
+            else
+                collide(std::false_type{});
         } else if (active) {
             // A solid node's populations are never read (a node that a
             // particle uncovers gets f^eq in all slots), but writing them

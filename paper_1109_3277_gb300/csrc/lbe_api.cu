@@ -345,6 +345,7 @@ lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_c
         L.tau[k] = (float)d->tau[k];
         L.itau[k] = (float)(1.0 / d->tau[k]);
         L.rho_ref[k] = d->rho_ref[k];
+        L.rref[k] = d->storage == LBE_STORE_F32 ? 0.f : (float)d->rho_ref[k];
         for (int i = 0; i < Q; i++)
             L.base[k][i] = d->storage == LBE_STORE_F32 ? 0.f : (float)(wgtd(i) * d->rho_ref[k]);
     }

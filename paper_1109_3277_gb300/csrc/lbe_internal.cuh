@@ -39,8 +39,12 @@ __host__ __device__ constexpr double wgtd(int i) { return i == 0 ? 1.0 / 3.0 : (
 
 // Population storage.  FP32 stores f itself; the 16-bit modes store
 // δf = f - w_i ρ_ref^c (the offset from the rest equilibrium at ρ_ref).
+// raw/st_raw read and write the stored quantity (δf, or f for FP32) in
+// FP32; ld/ldc/st/cvt/enc convert to and from f with the slot's base.
 struct StF32 {
     using T = float;
+    static __device__ __forceinline__ float raw(T v) { return v; }
+    static __device__ __forceinline__ void st_raw(T *p, float v) { *p = v; }
     static __device__ __forceinline__ float ld(const T *p, float) { return __ldg(p); }
     static __device__ __forceinline__ float ldc(const T *p, float) { return *p; }
     static __device__ __forceinline__ void st(T *p, float v, float) { *p = v; }
@@ -56,6 +60,8 @@ struct StF32 {
 };
 struct StF16 {
     using T = __half;
+    static __device__ __forceinline__ float raw(T v) { return __half2float(v); }
+    static __device__ __forceinline__ void st_raw(T *p, float v) { *p = __float2half_rn(v); }
     static __device__ __forceinline__ float ld(const T *p, float b) { return b + __half2float(__ldg(p)); }
     static __device__ __forceinline__ float ldc(const T *p, float b) { return b + __half2float(*p); }
     static __device__ __forceinline__ void st(T *p, float v, float b) { *p = __float2half_rn(v - b); }
@@ -70,6 +76,8 @@ struct StF16 {
 };
 struct StBF16 {
     using T = __nv_bfloat16;
+    static __device__ __forceinline__ float raw(T v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ void st_raw(T *p, float v) { *p = __float2bfloat16_rn(v); }
     static __device__ __forceinline__ float ld(const T *p, float b) { return b + __bfloat162float(__ldg(p)); }
     static __device__ __forceinline__ float ldc(const T *p, float b) { return b + __bfloat162float(*p); }
     static __device__ __forceinline__ void st(T *p, float v, float b) { *p = __float2bfloat16_rn(v - b); }
@@ -93,6 +101,7 @@ struct Lat {
     float g;
     float body[3];
     float base[2][Q];      // w_i ρ_ref^c for the 16-bit modes, 0 for FP32
+    float rref[2];         // ρ_ref^c for the 16-bit modes, 0 for FP32
     double rho_ref[2];
     int np;                        // particles (bounds checks)
     unsigned *status;              // bit 0: a TMA copy of the fused kernel never completed
