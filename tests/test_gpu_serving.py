@@ -130,3 +130,13 @@ def test_batch_first_quat_in_member_order():
     q = b.first_quat()
     for k, g in enumerate(lats):
         assert np.array_equal(q[k], g.read_particles()["quat"][0])
+
+
+def test_idle_server_starts_and_stops():
+    """A server that never gets a request runs no chunk and shuts down cleanly."""
+    import time
+    srv = lbe.Server(1 * GB, 2, "f32")
+    time.sleep(0.2)
+    st = srv.stats()
+    srv.close()
+    assert st == {"completed": 0, "node_steps": 0, "max_running": 0, "chunks": 0}
