@@ -131,8 +131,9 @@ LBE_API lbe_status lbe_read_fields(lbe_ctx *c, double *rho, double *vel, uint8_t
 LBE_API lbe_status lbe_read_particles(lbe_ctx *c, double *pos, double *quat, double *vel, double *omega,
                               double *force, double *torque);
 
-/* Per-component fluid mass Σ_x Σ_i f_i^c over fluid nodes, summed in FP64
- * in a fixed order (synchronises). */
+/* Per-component fluid mass Σ_x Σ_i f_i^c over fluid nodes (synchronises).
+ * Each node's 19 FP32 populations are summed error-free (TwoSum) and the
+ * node sums are added in FP64 in a fixed order. */
 LBE_API lbe_status lbe_mass(lbe_ctx *c, double out[2]);
 
 /* Raw populations f[2][19][N] as doubles (synchronises / uploads).  Solid

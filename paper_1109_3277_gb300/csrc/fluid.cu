@@ -447,6 +447,26 @@ __global__ void k_fields(Lat L, const typename S::T *__restrict__ f, const float
 constexpr int MASS_BLOCKS = 1024;
 constexpr int MASS_THREADS = 256;
 
+// Σ_i f_i^c of node n.  The 19 FP32 values are added with Knuth's
+// error-free TwoSum: s collects the rounded sum and e the rounding errors,
+// so s + e is the exact sum up to the rounding of the small term e (about
+// 1e-15 of the node's mass), and only two FP64 additions per node and
+// component remain (FP64 arithmetic is slow on this part).
+template <class S>
+__device__ __forceinline__ double node_mass(const Lat &L, const typename S::T *__restrict__ f, int c, int n)
+{
+    float s = S::ld(slot<S>(f, L, c, 0) + n, L.base[c][0]), e = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        const float v = S::ld(slot<S>(f, L, c, i) + n, L.base[c][i]);
+        const float t = __fadd_rn(s, v);
+        const float vb = __fsub_rn(t, s);
+        e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(t, vb)), __fsub_rn(v, vb)));
+        s = t;
+    }
+    return (double)s + (double)e;
+}
+
 template <class S>
 __global__ void __launch_bounds__(MASS_THREADS) k_mass(Lat L, const typename S::T *__restrict__ f,
                                                        const uint8_t *__restrict__ type,
@@ -455,11 +475,8 @@ __global__ void __launch_bounds__(MASS_THREADS) k_mass(Lat L, const typename S::
     double a0 = 0.0, a1 = 0.0;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < L.N; n += gridDim.x * blockDim.x) {
         if (type[n] != FLUID) continue;
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            a0 += (double)S::ld(slot<S>(f, L, 0, i) + n, L.base[0][i]);
-            a1 += (double)S::ld(slot<S>(f, L, 1, i) + n, L.base[1][i]);
-        }
+        a0 += node_mass<S>(L, f, 0, n);
+        a1 += node_mass<S>(L, f, 1, n);
     }
     __shared__ double sh[2][MASS_THREADS];
     sh[0][threadIdx.x] = a0;

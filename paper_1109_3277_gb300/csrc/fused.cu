@@ -41,6 +41,9 @@ __device__ __forceinline__ int wrapc(int v, int n)
 // Dynamic shared memory layout (bytes from a 128-byte aligned base).
 template <class S>
 struct Smem {
+    // CTAs per SM the kernels are compiled for: three at 16 bit (51 KB of
+    // shared memory each, 80 registers per thread), two in FP32 (90 KB each)
+    static constexpr int CTAS = sizeof(typename S::T) == 2 ? 3 : 2;
     static constexpr size_t plane = 2 * Q * NT * sizeof(typename S::T);  // one staged plane
     static constexpr size_t stage = 0;                                   // T [2][2Q][NT]
     static constexpr size_t sps = stage + 2 * plane;                     // float2 [4][HN] (ψ_r, ψ_b)
@@ -322,9 +325,11 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
                 jj[c][1] = jy;
                 jj[c][2] = jz;
             }
-            // the collision re-reads the stage: keeping the converted
-            // populations live in registers instead would spill
-            asm volatile("" ::: "memory");
+            // 16-bit storage: the collision re-reads the stage, since keeping
+            // the converted populations live in registers would spill under
+            // the three-CTA register budget.  FP32 storage runs two CTAs
+            // per SM (shared memory) and keeps them in registers.
+            if constexpr (sizeof(T) == 2) asm volatile("" ::: "memory");
             const float den = __fmaf_rn(rho_[1], L.itau[1], __fmul_rn(rho_[0], L.itau[0]));
             const float iden = den > 0.f ? 1.f / den : 0.f;
             float up[3];
@@ -448,7 +453,7 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
 }
 
 template <class S, bool TMA>
-__global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__restrict__ fin,
+__global__ void __launch_bounds__(NT, Smem<S>::CTAS) k_fused(Lat L, const typename S::T *__restrict__ fin,
                                               typename S::T *__restrict__ fout, const float *__restrict__ rho,
                                               const float *__restrict__ psi,
                                               const uint8_t *__restrict__ type, int zc, FusedOfs ofs,
@@ -462,7 +467,7 @@ __global__ void __launch_bounds__(NT, 3) k_fused(Lat L, const typename S::T *__r
 // Persistent multi-lattice variant: CTAs take tiles of all boxes of a batch
 // from one queue (largest boxes first in the queue order set by the host).
 template <class S>
-__global__ void __launch_bounds__(NT, 3) k_fused_batch(BatchIndex B, int total)
+__global__ void __launch_bounds__(NT, Smem<S>::CTAS) k_fused_batch(BatchIndex B, int total)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = align128(smem_raw);
