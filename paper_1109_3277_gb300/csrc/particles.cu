@@ -1193,8 +1193,11 @@ __device__ __forceinline__ void transition_body(const Lat &L, const Parts &P, in
     }
 }
 
+// Compiled for eight CTAs per SM (64 registers): most candidates only
+// compare two owner words, and the occupancy hides their latency; the
+// rare fill and empty spill a few registers.
 template <class S>
-__global__ void __launch_bounds__(PT) k_transition(Lat L, Parts P, typename S::T *__restrict__ f,
+__global__ void __launch_bounds__(PT, 8) k_transition(Lat L, Parts P, typename S::T *__restrict__ f,
                                                    uint8_t *__restrict__ type,
                                                    const uint32_t *__restrict__ own_old,
                                                    const uint32_t *__restrict__ own_new,
