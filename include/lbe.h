@@ -86,7 +86,7 @@ typedef struct {
     double  lub_rho;         /* density in μ = ν ρ of the lubrication correction */
     void   *cuda_stream;     /* cudaStream_t to enqueue on (of the chosen device), or NULL */
     int32_t device;          /* CUDA device ordinal; -1 = the library's current device */
-    int32_t flags;           /* 0, or LBE_FLAG_TWO_PASS */
+    int32_t flags;           /* 0, or LBE_FLAG_TWO_PASS | LBE_FLAG_WIDE_OFFSETS */
 } lbe_lattice_desc;
 
 /* Run the fluid update as two passes (densities and ψ of every node to
@@ -94,6 +94,12 @@ typedef struct {
  * results up to FP32 rounding; kept as the comparison point of the fused
  * kernel. */
 #define LBE_FLAG_TWO_PASS 1
+
+/* The fused kernel addresses its stores with 32-bit offsets from the node's
+ * component where they fit (19 x the slot stride + 2 N < 2^32, lattices up
+ * to about 214 M nodes) and with 64-bit offsets otherwise.  This flag takes
+ * the 64-bit form on any lattice: same results, bit for bit (for tests). */
+#define LBE_FLAG_WIDE_OFFSETS 2
 
 /* Create a lattice on the current CUDA device with populations at the rest
  * equilibrium f_i^c = w_i rho0^c (Eq. 2 at u = 0).

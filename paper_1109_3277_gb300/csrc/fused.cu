@@ -155,7 +155,7 @@ __device__ __forceinline__ float relax(float f, float feq, float it) { return __
 // arrive as tensor copies described by *tmap; otherwise each thread loads
 // its node's populations.  Returns false if a copy never completed (the
 // lattice's status word records it).
-template <class S, bool TMA>
+template <class S, bool TMA, bool R32>
 __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__restrict__ fin,
                                            typename S::T *__restrict__ fout, const float *__restrict__ rho,
                                            const float *__restrict__ psi, const uint8_t *__restrict__ type, int zc,
@@ -352,6 +352,9 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
             const float2 pcc = pl[1][ec];
             const float pc[2] = {pcc.x, pcc.y};
             T *dst = fout + n;
+            // R32: stores address the node's component c from dc[c] with
+            // 32-bit offsets (one wide multiply-add per address)
+            T *const dc[2] = {dst, dst + (size_t)Q * (size_t)L.S};
             // A warp whose nodes are all off the lattice boundary and have
             // no solid neighbour pushes every population to its fixed
             // offset; the others select, per population, between the push
@@ -380,14 +383,23 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
                 // address is a select, not a branch.
                 auto put = [&](int c, int i, float fs) {
                     if (CLEAN) {
-                        S::st_raw(dst + ofs.push[c * Q + i], fs);
+                        if constexpr (R32)
+                            S::st_raw(dc[c] + ofs.push32[c * Q + i], fs);
+                        else
+                            S::st_raw(dst + ofs.push[c * Q + i], fs);
                     } else {
                         const int corr = (cx(i) > 0 ? wx[0] : (cx(i) < 0 ? wx[1] : 0)) +
                                          (cy(i) > 0 ? wy[0] : (cy(i) < 0 ? wy[1] : 0)) +
                                          (cz(i) > 0 ? wz[0] : (cz(i) < 0 ? wz[1] : 0));
-                        const long long o =
-                            ((solid >> i) & 1u) ? ofs.pop[c * Q + opp(i)] : ofs.push[c * Q + i] + corr;
-                        S::st_raw(dst + o, fs);
+                        if constexpr (R32) {
+                            const unsigned o = ((solid >> i) & 1u) ? ofs.pop32[c * Q + opp(i)]
+                                                                   : ofs.push32[c * Q + i] + (unsigned)corr;
+                            S::st_raw(dc[c] + o, fs);
+                        } else {
+                            const long long o =
+                                ((solid >> i) & 1u) ? ofs.pop[c * Q + opp(i)] : ofs.push[c * Q + i] + corr;
+                            S::st_raw(dst + o, fs);
+                        }
                     }
                 };
 #pragma unroll
@@ -414,7 +426,7 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
                     // rest population: equilibrium Δρ - Σ_{i>0} f^eq_i in the
                     // stored quantity (exact mass)
                     const float f0 = S::raw(fb[(c * Q) * NT]);
-                    S::st_raw(dst + ofs.pop[c * Q], relax(f0, __fsub_rn(dr, seq), it));
+                    S::st_raw(R32 ? dc[c] : dst + ofs.pop[c * Q], relax(f0, __fsub_rn(dr, seq), it));
                 }
             };
             if (clean)
@@ -452,7 +464,7 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
     return ok;
 }
 
-template <class S, bool TMA>
+template <class S, bool TMA, bool R32>
 __global__ void __launch_bounds__(NT, Smem<S>::CTAS) k_fused(Lat L, const typename S::T *__restrict__ fin,
                                               typename S::T *__restrict__ fout, const float *__restrict__ rho,
                                               const float *__restrict__ psi,
@@ -460,8 +472,8 @@ __global__ void __launch_bounds__(NT, Smem<S>::CTAS) k_fused(Lat L, const typena
                                               const __grid_constant__ CUtensorMap tmap)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    fused_tile<S, TMA>(L, fin, fout, rho, psi, type, zc, ofs, &tmap, blockIdx.x, blockIdx.y, blockIdx.z,
-                       align128(smem_raw));
+    fused_tile<S, TMA, R32>(L, fin, fout, rho, psi, type, zc, ofs, &tmap, blockIdx.x, blockIdx.y, blockIdx.z,
+                            align128(smem_raw));
 }
 
 // Persistent multi-lattice variant: CTAs take tiles of all boxes of a batch
@@ -494,10 +506,10 @@ __global__ void __launch_bounds__(NT, Smem<S>::CTAS) k_fused_batch(BatchIndex B,
         const CUtensorMap *tm = &B.box[s_box].tmap[cur];
         bool ok;
         if (sb.tma)
-            ok = fused_tile<S, true>(sb.L, (const typename S::T *)sb.f[cur], (typename S::T *)sb.f[1 - cur], sb.rho,
+            ok = fused_tile<S, true, false>(sb.L, (const typename S::T *)sb.f[cur], (typename S::T *)sb.f[1 - cur], sb.rho,
                                      sb.psi, sb.type, sb.zc, sb.ofs, tm, bx, by, bz, smem);
         else
-            ok = fused_tile<S, false>(sb.L, (const typename S::T *)sb.f[cur], (typename S::T *)sb.f[1 - cur], sb.rho,
+            ok = fused_tile<S, false, false>(sb.L, (const typename S::T *)sb.f[cur], (typename S::T *)sb.f[1 - cur], sb.rho,
                                       sb.psi, sb.type, sb.zc, sb.ofs, tm, bx, by, bz, smem);
         if (!ok) break;
     }
@@ -555,11 +567,23 @@ FusedOfs fused_offsets(const Lat &L)
     FusedOfs ofs;
     for (int c = 0; c < 2; c++)
         for (int i = 0; i < Q; i++) {
-            long long o = (long long)(c * Q + i) * L.S;
+            const long long o = (long long)(c * Q + i) * L.S, r = (long long)i * L.S;
+            const long long d = cx(i) + (long long)cy(i) * L.nx + (long long)cz(i) * L.nx * L.ny;
             ofs.pop[c * Q + i] = o;
-            ofs.push[c * Q + i] = o + cx(i) + (long long)cy(i) * L.nx + (long long)cz(i) * L.nx * L.ny;
+            ofs.push[c * Q + i] = o + d;
+            // slot 0 never pushes; the others lie at least S - nx*ny - nx - 1 > 0
+            // above the component base
+            ofs.pop32[c * Q + i] = (unsigned)r;
+            ofs.push32[c * Q + i] = (unsigned)(r + d);
         }
     return ofs;
+}
+
+// The 32-bit offsets hold every store of a component: the highest is slot
+// 18 of the pushed neighbour plus a periodic wrap of N.
+bool fused_rel32(const Lat &L)
+{
+    return !L.wide && (long long)Q * L.S + 2LL * L.N + (long long)L.nx * L.ny + L.nx + 1 < (1LL << 32);
 }
 
 template <class S>
@@ -568,22 +592,27 @@ static void launch_fused_t(const Lat &L, const void *fin, void *fout, const floa
 {
     static bool configured = false;  // the attribute is per function and process
     if (!configured) {
-        cudaFuncSetAttribute(k_fused<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem<S>::bytes);
-        cudaFuncSetAttribute(k_fused<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem<S>::bytes);
+        const int b = (int)Smem<S>::bytes;
+        cudaFuncSetAttribute(k_fused<S, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        cudaFuncSetAttribute(k_fused<S, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        cudaFuncSetAttribute(k_fused<S, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        cudaFuncSetAttribute(k_fused<S, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
         configured = true;
     }
     const int zc = zc_override > 0 ? zc_override : fused_zchunk(L);
     dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
     FusedOfs ofs = fused_offsets(L);
     using T = typename S::T;
-    if (tmap) {
-        k_fused<S, true><<<grid, NT, Smem<S>::bytes, s>>>(L, (const T *)fin, (T *)fout, rho, psi, type, zc, ofs,
-                                                          *tmap);
-    } else {
-        const CUtensorMap none{};
-        k_fused<S, false><<<grid, NT, Smem<S>::bytes, s>>>(L, (const T *)fin, (T *)fout, rho, psi, type, zc, ofs,
-                                                           none);
-    }
+    const CUtensorMap none{};
+    const CUtensorMap &tm = tmap ? *tmap : none;
+    const bool r32 = fused_rel32(L);
+    auto go = [&](auto kernel) {
+        kernel<<<grid, NT, Smem<S>::bytes, s>>>(L, (const T *)fin, (T *)fout, rho, psi, type, zc, ofs, tm);
+    };
+    if (tmap)
+        r32 ? go(k_fused<S, true, true>) : go(k_fused<S, true, false>);
+    else
+        r32 ? go(k_fused<S, false, true>) : go(k_fused<S, false, false>);
 }
 
 void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *rho, const float *psi,

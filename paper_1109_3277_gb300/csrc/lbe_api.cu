@@ -320,7 +320,7 @@ lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_c
     if (!(d->tau[0] > 0.5) || !(d->tau[1] > 0.5)) return LBE_EINVAL;
     if (d->storage < LBE_STORE_F32 || d->storage > LBE_STORE_F16_OFS) return LBE_EINVAL;
     if (d->particle_mode < 0 || d->particle_mode > 2) return LBE_EINVAL;
-    if (d->flags & ~LBE_FLAG_TWO_PASS) return LBE_EINVAL;
+    if (d->flags & ~(LBE_FLAG_TWO_PASS | LBE_FLAG_WIDE_OFFSETS)) return LBE_EINVAL;
     long long N = (long long)d->nx * d->ny * d->nz;
     if (N > 0x7fffffffLL) return LBE_EINVAL;
     if (d->ny > 65535 || d->nz > 65535) return LBE_EINVAL;  // launch-grid rows and planes
@@ -341,6 +341,7 @@ lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_c
     L.walls = d->walls_z ? 1 : 0;
     L.N = (int)N;
     L.S = ((N + 127) / 128) * 128 + 384;
+    L.wide = (d->flags & LBE_FLAG_WIDE_OFFSETS) ? 1 : 0;
     for (int k = 0; k < 2; k++) {
         L.tau[k] = (float)d->tau[k];
         L.itau[k] = (float)(1.0 / d->tau[k]);

@@ -104,6 +104,7 @@ struct Lat {
     float rref[2];         // ρ_ref^c for the 16-bit modes, 0 for FP32
     double rho_ref[2];
     int np;                        // particles (bounds checks)
+    int wide;                      // 1: the fused kernel takes 64-bit store offsets
     unsigned *status;              // bit 0: a TMA copy of the fused kernel never completed
     unsigned long long *err;       // bounds-check record (checked builds only)
 };
@@ -219,11 +220,18 @@ struct Cells {
 // Offsets of the population arrays of a lattice: pop[c*Q+i] = (c*Q+i)*S and
 // push[c*Q+i] = pop[c*Q+i] + (cx + cy*nx + cz*nx*ny), so the address of a
 // load or of an interior push is one add.
+// Element offsets of the fused kernel's loads and stores from a node: its
+// own slot (pop) and the neighbour's it pushes to (push), from the base of
+// the population array; and the same from the base of the node's component
+// as 32-bit words (pop32, push32), used where they fit (fused_rel32).
 struct FusedOfs {
     long long pop[2 * Q];
     long long push[2 * Q];
+    unsigned pop32[2 * Q];
+    unsigned push32[2 * Q];
 };
 FusedOfs fused_offsets(const Lat &L);
+bool fused_rel32(const Lat &L);
 
 struct Pair {
     double k_hertz, lub_cut, mu;

@@ -15,6 +15,7 @@ Q = 19
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 MODES = {"free": 0, "static": 1, "prescribed": 2}
 FLAG_TWO_PASS = 1
+FLAG_WIDE_OFFSETS = 2
 PARTICLE_IN = 16   # pos[3], quat[4], vel[3], omega[3], r_par, r_perp, delta_rho
 PARTICLE_OUT = 19  # pos[3], quat[4], vel[3], omega[3], force[3], torque[3]
 
