@@ -45,7 +45,8 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["pickering", "spinodal", "bijel", "adsorption", "serving"],
+    ap.add_argument("--workload", choices=["pickering", "spinodal", "bijel", "adsorption", "serving",
+                                           "contact_angle"],
                     default="pickering")
     ap.add_argument("--requests", type=int, default=32, help="serving: number of adsorption requests")
     ap.add_argument("--rate", type=float, default=50.0, help="serving: Poisson arrival rate (1/s)")
@@ -418,6 +419,38 @@ def run_serving(args):
         print(json.dumps(line), flush=True)
 
 
+def run_contact_angle(args):
+    """Contact-angle calibration Θ(Δρ) (§2, the particle colour): one sphere
+    of radius 5 per colour in a 48 x 48 x 40 box with walls and a flat
+    interface, all boxes stepped as one batch for 8,000 steps; Θ from the
+    sphere's height above the far interface, and the line Θ = a Δρ + b over
+    the spheres still at the interface.  The paper's own fit (243.2° per unit
+    Δρ, its parameters) is context, not a target."""
+    import torch
+    from paper_1109_3277_gb300 import build as lbe_build
+    from paper_1109_3277_gb300 import contact_angle as CA
+
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    lbe_build.build()
+    drhos = [-0.06, -0.04, -0.02, 0.0, 0.02, 0.04, 0.06]
+    storage = args.storage or "f32"
+    res = CA.calibrate(drhos, steps=8000, chunk=1000, storage=storage)
+    if rank == 0:
+        line = {"metric": "contact angle calibration: dΘ/dΔρ", "value": round(res["slope_deg"], 2),
+                "unit": "deg per unit Δρ", "n_gpus": world, "higher_is_better": None, "scaling": "weak",
+                "vs_baseline": None, "dtype": f"f32 arithmetic, {storage} storage",
+                "data": "synthetic (seeded flat interface)",
+                "config": {"workload": "contact-angle-48x48x40-R5", "delta_rho": res["delta_rho"],
+                           "steps": res["steps"], "boxes_at_once": len(drhos)},
+                "theta_deg": [round(t, 2) for t in res["theta_deg"]],
+                "height": [round(h, 3) for h in res["height"]], "attached": res["attached"],
+                "intercept_deg": round(res["intercept_deg"], 2), "batch_mlups": round(res["mlups"], 1),
+                "seconds": round(res["seconds"], 2),
+                "paper_fit_context": "Θ = 243.2° Δρ + 90° for the paper's parameters"}
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The oracle as it stands, timed on the host cores on a bounded sample
     of the same workload; rank 0 only."""
@@ -456,6 +489,8 @@ def main(argv=None):
         run_reference(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.workload == "contact_angle":
+        run_contact_angle(args)
     else:
         run_ours(args)
 

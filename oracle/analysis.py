@@ -71,3 +71,36 @@ def tilt(quat, normal=(0.0, 0.0, 1.0)):
     axis = np.stack([1 - 2 * (y * y + z * z), 2 * (x * y + w * z), 2 * (x * z - w * y)], axis=1)
     c = np.abs(axis @ np.asarray(normal, dtype=np.float64))
     return np.arccos(np.clip(c, 0.0, 1.0))
+
+
+def interface_z(rho, col, walls=True):
+    """Height of the φ = ρ_r − ρ_b = 0 crossing on lattice column col = (x,
+    y): the zero of the straight line through the two nodes where φ changes
+    sign (the crossing nearest mid-height if there are several), over the
+    fluid planes (1 .. nz−2 between walls).  NaN without a crossing."""
+    x, y = col
+    phi = np.asarray(rho[0], dtype=np.float64)[:, y, x] - np.asarray(rho[1], dtype=np.float64)[:, y, x]
+    nz = phi.size
+    lo, hi = (1, nz - 2) if walls else (0, nz - 1)
+    zs = []
+    for z in range(lo, hi):
+        if phi[z] == 0.0:
+            zs.append(float(z))
+        elif phi[z] * phi[z + 1] < 0.0:
+            zs.append(z + phi[z] / (phi[z] - phi[z + 1]))
+    if not zs:
+        return float("nan")
+    zs = np.asarray(zs)
+    return float(zs[np.argmin(np.abs(zs - 0.5 * (lo + hi)))])
+
+
+def sphere_contact_angle(z_centre, z_interface, radius):
+    """Contact angle (degrees, through the lower, red phase) of a sphere whose
+    centre is z_centre − z_interface above a flat interface.  The interface
+    cuts the sphere in the circle at polar angle β from the upward axis,
+    cos β = (z_interface − z_centre) / radius.  There the sphere's outward
+    normal makes the angle β with the interface normal, so the angle between
+    the two surfaces measured through the lower phase is Θ = β (a sphere
+    below the interface, fully wetted by red, has Θ = 0)."""
+    c = (z_interface - z_centre) / radius
+    return float(np.degrees(np.arccos(min(1.0, max(-1.0, c)))))

@@ -258,3 +258,18 @@ def adsorption_request(seed, index, edge_range=(32, 96), m_range=(0.25, 4.0), r_
                     dict(walls_z=True, tau=(1.0, 1.0), g_br=0.1, rho_ref=(0.37, 0.37)),
                     rho0, 20000,
                     _particles([[edge / 2.0 + 0.25, edge / 2.0 + 0.25, zc]], [q], r_par, r_perp, drho))
+
+
+def contact_angle_box(delta_rho, seed=1115, shape=(48, 48, 40), radius=5.0, steps=6000):
+    """Contact-angle calibration (§2, the particle colour): a box with walls
+    in z and a flat interface at mid-height (red-rich below, 0.7 / 0.04 with
+    1e-3 noise), one sphere of radius ``radius`` and colour ``delta_rho``
+    centred on the interface, τ = 1, g = 0.1.  The sphere settles at the
+    height where the interface meets it at its contact angle."""
+    nx, ny, nz = shape
+    rho0 = flat_interface(shape, nz // 2, 0.7, 0.04, 1e-3, seed)
+    return Workload(f"contact-angle-{nx}x{ny}x{nz}-R{radius:g}-drho{delta_rho:+.3f}", shape,
+                    dict(walls_z=True, tau=(1.0, 1.0), g_br=0.1, rho_ref=(0.37, 0.37)),
+                    rho0, steps,
+                    _particles([[nx / 2.0, ny / 2.0, nz / 2.0]], [[1.0, 0.0, 0.0, 0.0]], radius, radius,
+                               delta_rho))

@@ -51,3 +51,53 @@ def test_tilt_closed_forms():
         assert abs(analysis.tilt(q)[0] - t) < 1e-12
     # a symmetry axis pointing down is the same tilt as pointing up
     assert abs(analysis.tilt(W.axis_tilt_quaternion(np.pi - 0.4, 1.0))[0] - 0.4) < 1e-12
+
+
+def _column_field(phi_z, nx=4, ny=3):
+    """rho [2, nz, ny, nx] whose φ = ρ_r − ρ_b is phi_z on every column."""
+    phi_z = np.asarray(phi_z, dtype=np.float64)
+    r = 0.5 + 0.5 * phi_z
+    b = 0.5 - 0.5 * phi_z
+    return np.stack([np.broadcast_to(r[:, None, None], (phi_z.size, ny, nx)),
+                     np.broadcast_to(b[:, None, None], (phi_z.size, ny, nx))])
+
+
+def test_interface_height_closed_forms():
+    z = np.arange(40, dtype=np.float64)
+    # a linear profile crosses exactly where the line does
+    assert analysis.interface_z(_column_field(0.03 * (17.3 - z)), (1, 2)) == pytest.approx(17.3, abs=1e-12)
+    # a profile odd about a midpoint between nodes crosses at the midpoint
+    assert analysis.interface_z(_column_field(np.tanh((20.5 - z) / 2.0)), (0, 0)) == pytest.approx(20.5, abs=1e-12)
+    # no crossing between the walls
+    assert np.isnan(analysis.interface_z(_column_field(np.ones(40)), (0, 0)))
+    # a slab has two crossings: the one nearest mid-height
+    slab = np.where((z > 8) & (z < 25), 1.0, -1.0)
+    assert analysis.interface_z(_column_field(slab), (0, 0)) == pytest.approx(24.5, abs=1e-12)
+
+
+@pytest.mark.parametrize("theta", [0.0, 30.0, 90.0, 131.0, 180.0])
+def test_sphere_contact_angle_against_wetted_area(theta):
+    """The fraction of a sphere's surface below a plane through the contact
+    circle is (1 + cos Θ)/2 (Archimedes); a seeded uniform sample of the
+    surface recovers Θ from the centre height through that fraction."""
+    R, zi = 5.0, 19.5
+    zc = zi - R * np.cos(np.radians(theta))
+    assert analysis.sphere_contact_angle(zc, zi, R) == pytest.approx(theta, abs=1e-9)
+    u = W.uniform(7, (200000,), stream=9, lo=-1.0, hi=1.0)  # z of uniform points on the unit sphere
+    below = np.mean(zc + R * u < zi)
+    est = np.degrees(np.arccos(np.clip(2 * below - 1, -1, 1)))
+    assert est == pytest.approx(theta, abs=1.0)
+
+
+def test_package_contact_angle_analysis_matches_the_oracle():
+    """The library's host analysis (used by the calibration and the bench)
+    and the oracle's give the same heights and angles on the same fields."""
+    from paper_1109_3277_gb300 import contact_angle as CA
+    z = np.arange(36, dtype=np.float64)
+    for z0, w in ((17.3, 1.5), (20.0, 2.0), (12.75, 3.0)):
+        rho = _column_field(np.tanh((z0 - z) / w))
+        a = CA.interface_height(rho, 2, 1)
+        b = analysis.interface_z(rho, (2, 1))
+        assert a == pytest.approx(b, abs=1e-12)
+        for zc in (z0 - 4.0, z0, z0 + 2.5):
+            assert CA.contact_angle(zc, a, 5.0) == pytest.approx(analysis.sphere_contact_angle(zc, b, 5.0), abs=1e-9)
