@@ -46,7 +46,7 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["pickering", "spinodal", "bijel", "adsorption", "serving",
-                                           "contact_angle"],
+                                           "contact_angle", "adsorption_study"],
                     default="pickering")
     ap.add_argument("--requests", type=int, default=32, help="serving: number of adsorption requests")
     ap.add_argument("--rate", type=float, default=50.0, help="serving: Poisson arrival rate (1/s)")
@@ -451,6 +451,30 @@ def run_contact_angle(args):
         print(json.dumps(line), flush=True)
 
 
+def run_adsorption_study(args):
+    """Single-ellipsoid adsorption of §4: an ellipsoid of radii 12 and 6
+    (aspect ratio 2, Θ = 90°) in a 64^3 box with walls and two lamellae, for
+    seven starting tilts stepped as one batch for 10,000 steps; prints the
+    tilt and the centre-to-interface distance every 500 steps."""
+    import torch
+    from paper_1109_3277_gb300 import adsorption as AD
+    from paper_1109_3277_gb300 import build as lbe_build
+
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    lbe_build.build()
+    tilts = [0.0057, 10.0, 30.0, 45.0, 60.0, 80.0, 90.0]
+    res = AD.trajectories(tilts, steps=10000, chunk=500, storage=args.storage or "f32")
+    if rank == 0:
+        line = {"metric": "single-ellipsoid adsorption: tilt and distance trajectories", "value": None,
+                "unit": None, "n_gpus": world, "higher_is_better": None, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32 arithmetic", "data": "synthetic (seeded lamellae)",
+                "config": {"workload": "adsorption-study-64-m2", "tilt0_deg": tilts, "steps": 10000},
+                "step": res["step"], "phi_deg": [[round(v, 2) for v in p] for p in res["phi_deg"]],
+                "z": [[round(v, 3) for v in z] for z in res["z"]], "batch_mlups": round(res["mlups"], 1)}
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The oracle as it stands, timed on the host cores on a bounded sample
     of the same workload; rank 0 only."""
@@ -491,6 +515,8 @@ def main(argv=None):
         run_serving(args)
     elif args.workload == "contact_angle":
         run_contact_angle(args)
+    elif args.workload == "adsorption_study":
+        run_adsorption_study(args)
     else:
         run_ours(args)
 

@@ -273,3 +273,23 @@ def contact_angle_box(delta_rho, seed=1115, shape=(48, 48, 40), radius=5.0, step
                     rho0, steps,
                     _particles([[nx / 2.0, ny / 2.0, nz / 2.0]], [[1.0, 0.0, 0.0, 0.0]], radius, radius,
                                delta_rho))
+
+
+def adsorption_study_box(tilt_deg, seed=1116, edge=64, r_par=12.0, r_perp=6.0, delta_rho=0.0, gap=2.0):
+    """Single-ellipsoid adsorption of §4: a cube of edge 64 with walls at
+    z = 0 and 63 and two lamellae (red-rich below z = 32, blue-rich above,
+    0.7 / 0.04 with 1e-3 noise), g = 0.1, τ = 1, one ellipsoid of radii
+    r_par = 12, r_perp = 6 (aspect ratio 2) and colour Δρ = 0 (Θ = 90°) whose
+    axis makes the angle ``tilt_deg`` with the interface normal.  Its centre
+    starts above the interface by its half-extent along z minus ``gap``, so
+    that its lowest point dips ``gap`` nodes into the interface."""
+    shape = (edge, edge, edge)
+    t = np.radians(tilt_deg)
+    half = np.sqrt((r_par * np.cos(t)) ** 2 + (r_perp * np.sin(t)) ** 2)
+    zc = edge / 2.0 + half - gap
+    rho0 = flat_interface(shape, edge // 2, 0.7, 0.04, 1e-3, seed)
+    return Workload(f"adsorption-study-{edge}-m{r_par / r_perp:g}-tilt{tilt_deg:g}", shape,
+                    dict(walls_z=True, tau=(1.0, 1.0), g_br=0.1, rho_ref=(0.37, 0.37)),
+                    rho0, 10000,
+                    _particles([[edge / 2.0 + 0.25, edge / 2.0 + 0.25, zc]], [axis_tilt_quaternion(t)],
+                               r_par, r_perp, delta_rho))

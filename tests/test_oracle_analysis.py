@@ -101,3 +101,14 @@ def test_package_contact_angle_analysis_matches_the_oracle():
         assert a == pytest.approx(b, abs=1e-12)
         for zc in (z0 - 4.0, z0, z0 + 2.5):
             assert CA.contact_angle(zc, a, 5.0) == pytest.approx(analysis.sphere_contact_angle(zc, b, 5.0), abs=1e-9)
+
+
+def test_package_tilt_matches_the_oracle():
+    """The adsorption driver's tilt and the oracle's agree on seeded random
+    orientations and on the axis-tilt construction."""
+    from paper_1109_3277_gb300 import adsorption as AD
+    q = W.random_quaternions(5, 64)
+    for k in range(64):
+        assert AD.tilt_deg(q[k]) == pytest.approx(np.degrees(analysis.tilt(q[k])[0]), abs=1e-9)
+    for t in (0.0, 0.0057, 10.0, 45.0, 89.0, 90.0):
+        assert AD.tilt_deg(W.axis_tilt_quaternion(np.radians(t))) == pytest.approx(t, abs=1e-7)
