@@ -197,7 +197,8 @@ LBE_API lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc);
 /* Set the fused kernel's z-chunk length (planes per CTA; 0 restores the
  * default, sized for about 16 waves of CTAs).  A chunk longer than the
  * lattice is clipped.  Only the order in which tiles run depends on it,
- * never a result.  LBE_EINVAL for a negative length. */
+ * never a result.  Synchronises first (and returns a pending error of
+ * earlier steps).  LBE_EINVAL for a negative length. */
 LBE_API lbe_status lbe_set_zchunk(lbe_ctx *c, int32_t zc);
 
 /* Batches: several lattices stepped together, every kernel of the step

@@ -790,6 +790,9 @@ lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc)
 lbe_status lbe_set_zchunk(lbe_ctx *c, int32_t zc)
 {
     if (!c || zc < 0) return LBE_EINVAL;
+    cudaSetDevice(c->device);
+    lbe_status st = sync(c, "set_zchunk");  // no captured step in flight when its graph goes
+    if (st != LBE_OK) return st;
     c->zc_tuned = zc < c->L.nz ? zc : c->L.nz;
     drop_graphs(c);
     return LBE_OK;
