@@ -274,3 +274,41 @@ def test_fill_empty_mass_bookkeeping():
                            atol=1e-12 * m.sum())
         m = m1
     assert events > 10
+
+
+def test_co_moving_fluid_is_left_at_equilibrium_exactly():
+    """Eq. 4 with C = 6 w_i ρ (u_surf·c_i) (readings c5, c6): a sphere centred
+    on a node (its links come in inversion pairs) that moves with the
+    uniform fluid.  The bounced population plus C is then exactly the
+    equilibrium of the moving fluid, so after one step every fluid node is
+    still at f^eq(ρ, U), to rounding, and the net force and torque vanish: in
+    (2 f*_ī + C) c_ī the terms odd in c cancel, and the even ones sum to zero
+    over each inversion pair.  A wrong sign or factor in C leaves the odd
+    terms, which do not cancel."""
+    n = 16
+    U = np.array([0.02, -0.01, 0.005])
+    rho0 = np.zeros((2, n, n, n))
+    rho0[0] = 1.0
+    L = lbref.Lattice((n, n, n), rho0, g_br=0.0, particle_mode=1)
+    # radius 4.3: no node lies within 0.05 of the surface
+    L.add_particles([[8.0, 8.0, 8.0]], [[1.0, 0, 0, 0]], 4.3, 4.3, 0.0, vel=[U])
+    f = L.get_populations()
+    _, _, typ = L.read_fields()
+    feq = lbref.feq(1.0, U)
+    fluid = typ == 0
+    f[0] = np.where(fluid[None], feq[:, None, None, None], 0.0)
+    f[1] = 0.0
+    L.set_populations(f)
+    L.step(1)
+    f1 = L.get_populations()
+    assert np.max(np.abs(f1[0][:, fluid] - feq[:, None])) < 1e-14
+    p = L.read_particles()
+    assert np.max(np.abs(p["force"][0])) < 1e-12
+    assert np.max(np.abs(p["torque"][0])) < 1e-12
+    # the same sphere at rest in that flow feels a drag along U
+    L2 = lbref.Lattice((n, n, n), rho0, g_br=0.0, particle_mode=1)
+    L2.add_particles([[8.0, 8.0, 8.0]], [[1.0, 0, 0, 0]], 4.3, 4.3, 0.0)
+    L2.set_populations(f)
+    L2.step(1)
+    F = L2.read_particles()["force"][0]
+    assert F @ U > 0 and np.linalg.norm(F) > 1e-3
