@@ -46,7 +46,7 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["pickering", "spinodal", "bijel", "adsorption", "serving",
-                                           "contact_angle", "adsorption_study"],
+                                           "contact_angle", "adsorption_study", "domain_size"],
                     default="pickering")
     ap.add_argument("--requests", type=int, default=32, help="serving: number of adsorption requests")
     ap.add_argument("--rate", type=float, default=50.0, help="serving: Poisson arrival rate (1/s)")
@@ -479,6 +479,33 @@ def run_adsorption_study(args):
         print(json.dumps(line), flush=True)
 
 
+def run_domain_size(args):
+    """Domain size against particle concentration (§4): 256^3 bijels with
+    prolate ellipsoids (aspect ratio 2, Θ = 90°) at C = 0.08 ... 0.24, each
+    run for 20,000 steps with L(t) every 5,000; prints L(C) and the fit
+    L = a / C + b (the paper's, for its parameters: a ≈ 2.20, b ≈ 11.08)."""
+    import torch
+    from paper_1109_3277_gb300 import build as lbe_build
+    from paper_1109_3277_gb300 import domain as D
+
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    lbe_build.build()
+    Cs = [0.08, 0.12, 0.16, 0.20, 0.24]
+    res = D.study(Cs, n=args.n or 256, steps=20000, checkpoint=5000, storage=args.storage or "f16")
+    if rank == 0:
+        line = {"metric": "bijel domain size against particle concentration", "value": round(res["a"], 3),
+                "unit": "a of L = a/C + b", "n_gpus": world, "higher_is_better": None, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32 arithmetic, f16-offset storage",
+                "data": "synthetic (seeded random phases, RSA placement)",
+                "config": {"workload": f"bijel-study-{args.n or 256}^3-m2", "C": res["C"],
+                           "particles": res["particles"], "steps": 20000},
+                "b": round(res["b"], 3), "step": res["step"], "L": [[round(v, 3) for v in s_] for s_ in res["L"]],
+                "mlups": round(res["mlups"], 1), "seconds": round(res["seconds"], 1),
+                "paper_fit_context": "a = 2.20, b = 11.08 for m = 2 at the paper's parameters"}
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The oracle as it stands, timed on the host cores on a bounded sample
     of the same workload; rank 0 only."""
@@ -521,6 +548,8 @@ def main(argv=None):
         run_contact_angle(args)
     elif args.workload == "adsorption_study":
         run_adsorption_study(args)
+    elif args.workload == "domain_size":
+        run_domain_size(args)
     else:
         run_ours(args)
 

@@ -293,3 +293,19 @@ def adsorption_study_box(tilt_deg, seed=1116, edge=64, r_par=12.0, r_perp=6.0, d
                     rho0, 10000,
                     _particles([[edge / 2.0 + 0.25, edge / 2.0 + 0.25, zc]], [axis_tilt_quaternion(t)],
                                r_par, r_perp, delta_rho))
+
+
+def bijel_study_box(concentration, seed=1117, n=256, r_par=8.0, r_perp=4.0, g_br=0.08, steps=20000):
+    """Domain size against particle concentration (§4): an n^3 periodic box
+    of random red- or blue-rich nodes (fluid ratio 1:1), g = 0.08, and
+    prolate ellipsoids of aspect ratio r_par / r_perp = 2 with Δρ = 0
+    (Θ = 90°) placed by random sequential addition to the volume fraction
+    ``concentration``."""
+    shape = (n, n, n)
+    vol = 4.0 / 3.0 * np.pi * r_par * r_perp * r_perp
+    count = int(round(concentration * n ** 3 / vol))
+    pos, quat = place_ellipsoids(shape, count, r_par, r_perp, seed)
+    return Workload(f"bijel-study-{n}^3-C{concentration:g}-{len(pos)}prolate", shape,
+                    dict(walls_z=False, tau=(1.0, 1.0), g_br=g_br, rho_ref=(0.37, 0.37)),
+                    random_phases(shape, 0.5, seed=seed), steps,
+                    _particles(pos, quat, r_par, r_perp, 0.0), storage="f16")

@@ -112,3 +112,25 @@ def test_package_tilt_matches_the_oracle():
         assert AD.tilt_deg(q[k]) == pytest.approx(np.degrees(analysis.tilt(q[k])[0]), abs=1e-9)
     for t in (0.0, 0.0057, 10.0, 45.0, 89.0, 90.0):
         assert AD.tilt_deg(W.axis_tilt_quaternion(np.radians(t))) == pytest.approx(t, abs=1e-7)
+
+
+def test_package_domain_size_matches_the_oracle():
+    """The study's real-FFT domain size and the oracle's full-FFT one agree
+    on seeded fields with and without solid nodes, and give the wavelength
+    of a single mode."""
+    from paper_1109_3277_gb300 import domain as D
+    shape = (24, 20, 16)
+    nx, ny, nz = shape
+    rho = W.uniform(3, (2, nz, ny, nx), stream=11, lo=0.0, hi=1.0)
+    fluid = W.uniform(3, (nz, ny, nx), stream=12) > 0.2
+    for fl in (None, fluid):
+        a = D.domain_size(rho, fl)
+        b = analysis.domain_size(rho, fl)
+        assert a[0] == pytest.approx(b[0], rel=1e-12)
+        assert np.allclose(a[1], b[1], rtol=1e-12)
+    x = np.arange(nx)
+    phi = np.broadcast_to(np.sin(2 * np.pi * x / 8.0)[None, None, :], (nz, ny, nx))
+    L, (lx, _, _) = D.domain_size(np.stack([0.5 + 0.5 * phi, 0.5 - 0.5 * phi]))
+    assert lx == pytest.approx(8.0, rel=1e-12)
+    assert D.fit_inverse([0.1, 0.2, 0.25], [2.2 / 0.1 + 11.08, 2.2 / 0.2 + 11.08, 2.2 / 0.25 + 11.08]) == \
+        pytest.approx((2.2, 11.08), rel=1e-12)
