@@ -499,6 +499,7 @@ def run_domain_size(args):
                 "vs_baseline": None, "dtype": "f32 arithmetic, f16-offset storage",
                 "data": "synthetic (seeded random phases, RSA placement)",
                 "config": {"workload": f"bijel-study-{args.n or 256}^3-m2", "C": res["C"],
+                           "C_placed": [round(c, 4) for c in res["C_placed"]],
                            "particles": res["particles"], "steps": 20000},
                 "b": round(res["b"], 3), "step": res["step"], "L": [[round(v, 3) for v in s_] for s_ in res["L"]],
                 "mlups": round(res["mlups"], 1), "seconds": round(res["seconds"], 1),
