@@ -1,6 +1,7 @@
 """The seeded input generators: SplitMix64 against its published test
 sequence, determinism, placement without overlap."""
 import numpy as np
+import pytest
 
 from paper_1109_3277_gb300 import workloads as W
 
@@ -52,3 +53,26 @@ def test_workload_recipes():
     rmax = max(r.particles["r_par"][0], r.particles["r_perp"][0])
     assert 2 * rmax + 6 <= e
     assert r.particles["pos"][0, 2] + rmax < e - 1
+
+
+def test_study_recipes():
+    """The calibration and study boxes: shapes, walls, the interface, and
+    particles placed as stated."""
+    c = W.contact_angle_box(0.04)
+    assert c.shape == (48, 48, 40) and c.params["walls_z"]
+    assert np.allclose(c.particles["pos"][0], [24.0, 24.0, 20.0])
+    assert c.particles["r_par"][0] == c.particles["r_perp"][0] == 5.0 and c.particles["delta_rho"][0] == 0.04
+    assert abs(c.rho0[0, 10].mean() - 0.7) < 1e-3 and abs(c.rho0[1, 30].mean() - 0.7) < 1e-3
+    for tilt in (0.0057, 45.0, 90.0):
+        a = W.adsorption_study_box(tilt)
+        q = a.particles["quat"][0]
+        axis_z = 2 * (q[1] * q[3] - q[0] * q[2])
+        assert np.degrees(np.arccos(min(1.0, abs(axis_z)))) == pytest.approx(tilt, abs=1e-6)
+        # the lowest point dips 2 nodes below the interface plane z = 32
+        t = np.radians(tilt)
+        half = np.hypot(12.0 * np.cos(t), 6.0 * np.sin(t))
+        assert a.particles["pos"][0, 2] - half == pytest.approx(30.0, abs=1e-12)
+    b = W.bijel_study_box(0.2, n=64)
+    vol = 4.0 / 3.0 * np.pi * 8.0 * 4.0 * 4.0
+    assert len(b.particles["pos"]) == int(round(0.2 * 64 ** 3 / vol))
+    assert b.params["g_br"] == 0.08 and not b.params["walls_z"]
