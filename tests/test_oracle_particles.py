@@ -312,3 +312,33 @@ def test_co_moving_fluid_is_left_at_equilibrium_exactly():
     L2.step(1)
     F = L2.read_particles()["force"][0]
     assert F @ U > 0 and np.linalg.norm(F) > 1e-3
+
+
+@pytest.mark.parametrize("gap", [0.1, 0.4, 0.6])
+def test_lubrication_sphere_limit(gap):
+    """Eq. 9 for two spheres of radius R approaching at relative speed v
+    with a gap h = r - 2R below the cut-off Δc = 2/3: the correction is
+    (3π μ R^2 / 2) v (1/h - 1/Δc) along the line of centres, pushing them
+    apart, with μ = ρ̄ ν and ν = (τ - 1/2)/3 (reading c10).  It is isolated
+    as the difference between runs with and without the cut-off; the Hertz
+    term is zero at a positive gap."""
+    R, tau, rho_bar, cut = 4.0, 0.8, 1.4, 2.0 / 3.0
+    n = (32, 16, 16)
+    rho0 = np.zeros((2, 16, 16, 32))
+    rho0[0] = 1.0
+    v = 0.01
+    xa = 10.0
+    xb = xa + 2 * R + gap
+    F = []
+    for c in (cut, 0.0):
+        L = lbref.Lattice(n, rho0, g_br=0.0, tau=(tau, tau), particle_mode=1, lub_cut=c, lub_rho=rho_bar)
+        L.add_particles([[xa, 8.0, 8.0], [xb, 8.0, 8.0]], [[1.0, 0, 0, 0]] * 2, R, R, 0.0,
+                        vel=[[v, 0, 0], [-v, 0, 0]])
+        L.step(1)
+        F.append(L.read_particles()["force"])
+    dF = F[0] - F[1]
+    mu = rho_bar * (tau - 0.5) / 3.0
+    want = 1.5 * np.pi * mu * R * R * (2 * v) * (1.0 / gap - 1.0 / cut)
+    assert dF[0, 0] == pytest.approx(-want, rel=1e-10)
+    assert dF[1, 0] == pytest.approx(want, rel=1e-10)
+    assert np.allclose(dF[:, 1:], 0.0, atol=1e-14)
