@@ -124,32 +124,43 @@ __device__ __forceinline__ void tma_plane(void *dst, const CUtensorMap *map, int
 // fused kernels agree exactly.  Products with the lattice velocities c_i
 // (components 0 or ±1) are exact and stay plain.
 
-// Equilibrium velocity of component c, u' + (τ_c/ρ_c) F^c with the
+// The two components go through the same node arithmetic, so it is done on
+// (red, blue) pairs with the paired FP32 instructions (add, multiply and
+// fused multiply-add on two lanes, each rounded to nearest like its scalar
+// form): every component's result has the bits of the scalar sequence.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Equilibrium velocities of both components, u' + (τ_c/ρ_c) F^c with the
 // Shan–Chen force F^c = -g ψ^c s^c + ρ^c g_body (Eq. 3), and -1.5 u·u.
-__device__ __forceinline__ void eq_velocity(const Lat &L, int c, float r, float pc, const float s[3],
-                                            const float up[3], float ue[3], float &um15)
+__device__ __forceinline__ void eq_velocity(const Lat &L, float2 r, float2 pc, const float2 s[3], const float up[3],
+                                            float2 ue[3], float2 &um15)
 {
-    const float ir = r > 0.f ? __fdiv_rn(L.tau[c], r) : 0.f;
-    const float gp = __fmul_rn(-L.g, pc);
+    const float2 ir = make_float2(r.x > 0.f ? __fdiv_rn(L.tau[0], r.x) : 0.f,
+                                  r.y > 0.f ? __fdiv_rn(L.tau[1], r.y) : 0.f);
+    const float2 gp = mul2(dup2(-L.g), pc);
 #pragma unroll
-    for (int k = 0; k < 3; k++) ue[k] = __fmaf_rn(ir, __fmaf_rn(gp, s[k], __fmul_rn(r, L.body[k])), up[k]);
-    const float uu = __fmaf_rn(ue[0], ue[0], __fmaf_rn(ue[1], ue[1], __fmul_rn(ue[2], ue[2])));
-    um15 = __fmul_rn(-1.5f, uu);
+    for (int k = 0; k < 3; k++) ue[k] = fma2(ir, fma2(gp, s[k], mul2(r, dup2(L.body[k]))), dup2(up[k]));
+    const float2 uu = fma2(ue[0], ue[0], fma2(ue[1], ue[1], mul2(ue[2], ue[2])));
+    um15 = mul2(dup2(-1.5f), uu);
 }
 
 // f^eq_i = w_i ρ (1 + 3 c·u + 4.5 (c·u)^2 - 1.5 u·u) relative to the stored
 // quantity's base w_i ρ_ref: even part w_i (ρ (4.5 (c·u)^2 - 1.5 u·u) + Δρ)
 // with Δρ = ρ - ρ_ref (for FP32 storage ρ_ref = 0, Δρ = ρ), odd part
 // 3 w_i ρ c·u (w3r = 3 w_i ρ comes per weight).
-__device__ __forceinline__ void feq_parts(float w, float r, float dr, float w3r, float cu, float um15,
-                                          float &even, float &odd)
+__device__ __forceinline__ void feq_parts(float w, float2 r, float2 dr, float2 w3r, float2 cu, float2 um15,
+                                          float2 &even, float2 &odd)
 {
-    even = __fmul_rn(w, __fmaf_rn(r, __fmaf_rn(__fmul_rn(4.5f, cu), cu, um15), dr));
-    odd = __fmul_rn(w3r, cu);
+    even = mul2(dup2(w), fma2(r, fma2(mul2(dup2(4.5f), cu), cu, um15), dr));
+    odd = mul2(w3r, cu);
 }
 
 // BGK relaxation f + (f^eq - f)/τ.
-__device__ __forceinline__ float relax(float f, float feq, float it) { return __fmaf_rn(__fsub_rn(feq, f), it, f); }
+__device__ __forceinline__ float2 relax(float2 f, float2 feq, float2 it) { return fma2(sub2(feq, f), it, f); }
 
 // One tile (column bx, by, z chunk bz) of one lattice.  TMA: the planes
 // arrive as tensor copies described by *tmap; otherwise each thread loads
@@ -237,10 +248,10 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
         const int slot = (zz + 4) & 3;
         float2 *ps = sps + slot * HN;
         uint8_t *ts = sty + slot * HN;
-        ps[ec] = make_float2(v.p0, v.p1);
+        ps[ec] = make_float2(v.p1, v.p0);  // (ψ_b, ψ_r): the partner component first
         ts[ec] = v.t;
         if (h < NHALO) {
-            reinterpret_cast<float *>(ps + he)[hc] = v.ph;
+            reinterpret_cast<float *>(ps + he)[1 - hc] = v.ph;
             if (hc == 0) ts[he] = v.th;
         }
     };
@@ -301,56 +312,49 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
             // modes, f_i in FP32): Δρ^c = Σ_i d_i, ρ^c = ρ_ref + Δρ^c, and
             // j^c = Σ_i c_i d_i (the bases cancel: Σ_i w_i c_i = 0); the
             // shifted velocity u' = Σ_c j^c/τ_c / Σ_c ρ^c/τ_c
-            float drho[2], rho_[2], jj[2][3];
+            // (red, blue) pairs of the stored quantities of direction i
+            auto ld2 = [&](int i) { return make_float2(S::raw(fb[i * NT]), S::raw(fb[(Q + i) * NT])); };
+            float2 a = ld2(0), jj[3] = {dup2(0.f), dup2(0.f), dup2(0.f)};
 #pragma unroll
-            for (int c = 0; c < 2; c++) {
+            for (int i = 1; i < Q; i += 2) {
                 // one pass over opposite pairs (i, i+1), c_{i+1} = -c_i; the
                 // sum accumulates in index order
-                float a = S::raw(fb[(c * Q) * NT]);
-                float jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-                for (int i = 1; i < Q; i += 2) {
-                    const float va = S::raw(fb[(c * Q + i) * NT]);
-                    const float vb = S::raw(fb[(c * Q + i + 1) * NT]);
-                    a = __fadd_rn(a, va);
-                    a = __fadd_rn(a, vb);
-                    const float d = __fsub_rn(va, vb);
-                    if (cx(i)) jx = __fadd_rn(jx, cx(i) * d);
-                    if (cy(i)) jy = __fadd_rn(jy, cy(i) * d);
-                    if (cz(i)) jz = __fadd_rn(jz, cz(i) * d);
-                }
-                drho[c] = a;
-                rho_[c] = __fadd_rn(L.rref[c], a);
-                jj[c][0] = jx;
-                jj[c][1] = jy;
-                jj[c][2] = jz;
+                const float2 va = ld2(i), vb = ld2(i + 1);
+                a = add2(a, va);
+                a = add2(a, vb);
+                const float2 d = sub2(va, vb);
+                if (cx(i)) jj[0] = cx(i) > 0 ? add2(jj[0], d) : sub2(jj[0], d);
+                if (cy(i)) jj[1] = cy(i) > 0 ? add2(jj[1], d) : sub2(jj[1], d);
+                if (cz(i)) jj[2] = cz(i) > 0 ? add2(jj[2], d) : sub2(jj[2], d);
             }
+            const float2 drho = a, rho_ = add2(make_float2(L.rref[0], L.rref[1]), a);
             // 16-bit storage: the collision re-reads the stage, since keeping
             // the converted populations live in registers would spill under
             // the three-CTA register budget.  FP32 storage runs two CTAs
             // per SM (shared memory) and keeps them in registers.
             if constexpr (sizeof(T) == 2) asm volatile("" ::: "memory");
-            const float den = __fmaf_rn(rho_[1], L.itau[1], __fmul_rn(rho_[0], L.itau[0]));
+            const float den = __fmaf_rn(rho_.y, L.itau[1], __fmul_rn(rho_.x, L.itau[0]));
             const float iden = den > 0.f ? 1.f / den : 0.f;
             float up[3];
 #pragma unroll
             for (int k = 0; k < 3; k++)
-                up[k] = __fmul_rn(__fmaf_rn(jj[1][k], L.itau[1], __fmul_rn(jj[0][k], L.itau[0])), iden);
-            float s[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+                up[k] = __fmul_rn(__fmaf_rn(jj[k].y, L.itau[1], __fmul_rn(jj[k].x, L.itau[0])), iden);
+            // s^c = Σ_i c_i ψ^{c'}(x + c_i): the ring holds (ψ_b, ψ_r), the
+            // partner of (red, blue)
+            float2 s[3] = {dup2(0.f), dup2(0.f), dup2(0.f)};
             uint32_t solid = 0;  // bit i: neighbour i is not fluid
 #pragma unroll
             for (int i = 1; i < Q; i++) {
                 const int e = ec + cy(i) * HX + cx(i);
                 const float2 pp = pl[cz(i) + 1][e];
-                const float p0 = pp.x, p1 = pp.y;
                 const uint8_t tn = tl[cz(i) + 1][e];
                 solid |= (uint32_t)(tn != FLUID) << i;
-                if (cx(i)) { s[0][0] += cx(i) * p1; s[1][0] += cx(i) * p0; }
-                if (cy(i)) { s[0][1] += cy(i) * p1; s[1][1] += cy(i) * p0; }
-                if (cz(i)) { s[0][2] += cz(i) * p1; s[1][2] += cz(i) * p0; }
+                if (cx(i)) s[0] = cx(i) > 0 ? add2(s[0], pp) : sub2(s[0], pp);
+                if (cy(i)) s[1] = cy(i) > 0 ? add2(s[1], pp) : sub2(s[1], pp);
+                if (cz(i)) s[2] = cz(i) > 0 ? add2(s[2], pp) : sub2(s[2], pp);
             }
             const float2 pcc = pl[1][ec];
-            const float pc[2] = {pcc.x, pcc.y};
+            const float2 pc = make_float2(pcc.y, pcc.x);  // own (ψ_r, ψ_b)
             T *dst = fout + n;
             // R32: stores address the node's component c from dc[c] with
             // 32-bit offsets (one wide multiply-add per address)
@@ -402,32 +406,42 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
                         }
                     }
                 };
+                float2 ue[3], um15;
+                eq_velocity(L, rho_, pc, s, up, ue, um15);
+                const float2 it = make_float2(L.itau[0], L.itau[1]);
+                // 3 w ρ per weight (axis 1/18, diagonal 1/36)
+                const float2 w3r_a = mul2(dup2(3.f * wgt(1)), rho_), w3r_d = mul2(dup2(3.f * wgt(7)), rho_);
+                float2 seq = dup2(0.f);
+                // opposite pairs share the even part of the equilibrium
 #pragma unroll
-                for (int c = 0; c < 2; c++) {
-                    const float r = rho_[c], dr = drho[c];
-                    float ue[3], um15;
-                    eq_velocity(L, c, r, pc[c], s[c], up, ue, um15);
-                    const float it = L.itau[c];
-                    // 3 w ρ per weight (axis 1/18, diagonal 1/36)
-                    const float w3r_a = __fmul_rn(3.f * wgt(1), r), w3r_d = __fmul_rn(3.f * wgt(7), r);
-                    float seq = 0.f;
-                    // opposite pairs share the even part of the equilibrium
-#pragma unroll
-                    for (int i = 1; i < Q; i += 2) {
-                        const float cu = cx(i) * ue[0] + cy(i) * ue[1] + cz(i) * ue[2];
-                        float even, odd;
-                        feq_parts(wgt(i), r, dr, i < 7 ? w3r_a : w3r_d, cu, um15, even, odd);
-                        const float fa = S::raw(fb[(c * Q + i) * NT]);
-                        const float fbv = S::raw(fb[(c * Q + i + 1) * NT]);
-                        seq = __fadd_rn(seq, 2.f * even);
-                        put(c, i, relax(fa, __fadd_rn(even, odd), it));
-                        put(c, i + 1, relax(fbv, __fsub_rn(even, odd), it));
-                    }
-                    // rest population: equilibrium Δρ - Σ_{i>0} f^eq_i in the
-                    // stored quantity (exact mass)
-                    const float f0 = S::raw(fb[(c * Q) * NT]);
-                    S::st_raw(R32 ? dc[c] : dst + ofs.pop[c * Q], relax(f0, __fsub_rn(dr, seq), it));
+                for (int i = 1; i < Q; i += 2) {
+                    // c·u with c components in {-1, 0, 1}: sums in x, y, z order
+                    float2 cu = dup2(0.f);
+                    bool first = true;
+                    auto acc = [&](int ck, float2 v) {
+                        if (!ck) return;
+                        const float2 t = ck > 0 ? v : make_float2(-v.x, -v.y);
+                        cu = first ? t : add2(cu, t);
+                        first = false;
+                    };
+                    acc(cx(i), ue[0]);
+                    acc(cy(i), ue[1]);
+                    acc(cz(i), ue[2]);
+                    float2 even, odd;
+                    feq_parts(wgt(i), rho_, drho, i < 7 ? w3r_a : w3r_d, cu, um15, even, odd);
+                    seq = add2(seq, mul2(dup2(2.f), even));
+                    const float2 ra = relax(ld2(i), add2(even, odd), it);
+                    const float2 rb = relax(ld2(i + 1), sub2(even, odd), it);
+                    put(0, i, ra.x);
+                    put(1, i, ra.y);
+                    put(0, i + 1, rb.x);
+                    put(1, i + 1, rb.y);
                 }
+                // rest population: equilibrium Δρ - Σ_{i>0} f^eq_i in the
+                // stored quantity (exact mass)
+                const float2 r0 = relax(ld2(0), sub2(drho, seq), it);
+                S::st_raw(R32 ? dc[0] : dst + ofs.pop[0], r0.x);
+                S::st_raw(R32 ? dc[1] : dst + ofs.pop[Q], r0.y);
             };
             if (clean)
                 collide(std::true_type{});
