@@ -4,7 +4,6 @@ dipping into the interface, first moves across the interface without
 turning, then turns to the stable point φ ≈ 90°, as the paper's snapshot
 series shows; one started at 30° ends there too, and both centres end on
 the interface (z = 0 at Θ = 90°)."""
-import numpy as np
 import pytest
 
 from paper_1109_3277_gb300 import adsorption as AD

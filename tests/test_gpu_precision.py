@@ -8,7 +8,6 @@ tests/golden/make_spinodal_golden.py (oracle only)."""
 import json
 import os
 
-import numpy as np
 import pytest
 
 from oracle import analysis, lbref
