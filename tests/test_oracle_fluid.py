@@ -198,3 +198,21 @@ def test_demixing_sign_of_coupling(g, demix):
         assert s1 > 10 * s0
     else:
         assert s1 < s0
+
+
+def test_walls_leave_a_uniform_mixture_at_rest():
+    """Readings c11, c13: a wall node takes the mean ρ of its fluid
+    neighbours (Δρ = 0), so next to a flat wall a uniform mixture at rest
+    sees the same ψ on every side and no Shan–Chen force.  It stays uniform
+    and at rest to rounding over many steps.  Walls that kept ψ = 0 instead
+    would pull the fluid towards themselves at once."""
+    shape = (6, 5, 12)
+    nx, ny, nz = shape
+    rho0 = np.zeros((2, nz, ny, nx))
+    rho0[0], rho0[1] = 0.6, 0.3
+    L = _lattice(shape, rho0, walls_z=True, g_br=0.1, tau=(1.0, 0.8))
+    L.step(60)
+    rho, vel, typ = L.read_fields()
+    fl = typ == 0
+    assert np.max(np.abs(rho[0][fl] - 0.6)) < 1e-13 and np.max(np.abs(rho[1][fl] - 0.3)) < 1e-13
+    assert np.max(np.abs(vel[:, fl])) < 1e-14
