@@ -342,3 +342,27 @@ def test_lubrication_sphere_limit(gap):
     assert dF[0, 0] == pytest.approx(-want, rel=1e-10)
     assert dF[1, 0] == pytest.approx(want, rel=1e-10)
     assert np.allclose(dF[:, 1:], 0.0, atol=1e-14)
+
+
+@pytest.mark.parametrize("drho", [0.15, -0.15])
+def test_colour_rule_sign(drho):
+    """The colour rule of §2: Δρ > 0 adds red density to the particle's
+    shell, Δρ < 0 adds |Δρ| to blue.  The extra density repels the other
+    component (g > 0), so after some steps in a uniform mixture the fluid
+    next to the particle is richer in the colour's component than the bulk:
+    red for Δρ > 0, blue for Δρ < 0."""
+    n = 16
+    rho0 = np.full((2, n, n, n), 0.35)
+    L = lbref.Lattice((n, n, n), rho0, g_br=0.1, particle_mode=1)
+    L.add_particles([[8.0, 8.0, 8.0]], [[1.0, 0, 0, 0]], 3.3, 3.3, drho)
+    L.step(40)
+    rho, _, typ = L.read_fields()
+    fluid = typ == 0
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    r = np.sqrt((x - 8.0) ** 2 + (y - 8.0) ** 2 + (z - 8.0) ** 2)
+    near = fluid & (r < 5.0)
+    far = fluid & (r > 7.0)
+    phi_near = (rho[0] - rho[1])[near].mean()
+    phi_far = (rho[0] - rho[1])[far].mean()
+    assert np.sign(phi_near - phi_far) == np.sign(drho)
+    assert abs(phi_near - phi_far) > 1e-3
