@@ -57,10 +57,13 @@ _lib = None
 
 
 def lib():
+    """The oracle library: the in-tree build, or the file named by the
+    environment variable LBREF_LIB (the mutation tests load deliberately
+    broken builds of the oracle this way, in subprocesses)."""
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_LIB)
+        path = os.environ.get("LBREF_LIB") or build()
+        L = ctypes.CDLL(path)
         P = ctypes.c_void_p
         D = ctypes.POINTER(ctypes.c_double)
         L.lbref_init_lattice.argtypes = [ctypes.POINTER(LatticeDesc), D, ctypes.POINTER(P)]
