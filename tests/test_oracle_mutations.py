@@ -81,6 +81,28 @@ MUTANTS = {
     "rotation composed on the wrong side": (
         [("qmul(quat, dq, qn);", "qmul(dq, quat, qn);", 1)],
         [PART + "test_symmetric_top_free_precession"]),
+    "surface velocity without the rotation": (
+        [("cross(P->W, rb, wr);\n                for (int k = 0; k < 3; k++) us[k] = P->V[k] + wr[k];",
+          "cross(P->W, rb, wr);\n                for (int k = 0; k < 3; k++) us[k] = P->V[k];", 1)],
+        [FLUID + "test_bruteforce_one_step_static_particle"]),
+    "torque arm from the wrong centre": (
+        [("double rb[3] = {node_disp(c, 0, x0, P->X[0]) - 0.5 * CV[i][0],",
+          "double rb[3] = {node_disp(c, 0, x0, P->X[0] + 1.0) - 0.5 * CV[i][0],", 1)],
+        [FLUID + "test_bruteforce_one_step_static_particle"]),
+    "wall bounce-back into the incoming slot": (
+        [("fn[((long)cc * Q + i) * N + y] = c->fs[((long)cc * Q + io) * N + y];",
+          "fn[((long)cc * Q + i) * N + y] = c->fs[((long)cc * Q + i) * N + y];", 1)],
+        [FLUID + "test_bruteforce_one_step_fluid"]),
+    "shell fill divides by 18, not by the fluid neighbours": (
+        [("double rn[2] = {s[0] / cnt, s[1] / cnt};", "double rn[2] = {s[0] / 18.0, s[1] / 18.0};", 1)],
+        [FLUID + "test_walls_leave_a_uniform_mixture_at_rest"]),
+    "C with the other component's density": (
+        [("double C = 6.0 * WV[i] * c->rho[cc * N + y] * uc;",
+          "double C = 6.0 * WV[i] * c->rho[(1 - cc) * N + y] * uc;", 1)],
+        [FLUID + "test_bruteforce_one_step_static_particle"]),
+    "Shan-Chen sum over the own component": (
+        [("double ps = c->psi[co * N + m];", "double ps = c->psi[cc * N + m];", 1)],
+        [FLUID + "test_bruteforce_one_step_fluid"]),
     "gyroscopic term with the wrong sign": (
         [("cross(wb, L, wl);", "cross(L, wb, wl);", 1)],
         [PART + "test_symmetric_top_free_precession"]),
