@@ -103,6 +103,14 @@ MUTANTS = {
     "Shan-Chen sum over the own component": (
         [("double ps = c->psi[co * N + m];", "double ps = c->psi[cc * N + m];", 1)],
         [FLUID + "test_bruteforce_one_step_fluid"]),
+    "Hertz force applied with the same sign to both particles": (
+        [("B->Fpair[k] += fj[k];\n                A->Fpair[k] -= fj[k];",
+          "B->Fpair[k] += fj[k];\n                A->Fpair[k] += fj[k];", 1)],
+        [PART + "test_hertz_pair_force_applied_to_both_particles"]),
+    "Hertz torques of the two particles exchanged": (
+        [("A->Tpair[k] += ti[k];\n                B->Tpair[k] += tj[k];",
+          "A->Tpair[k] += tj[k];\n                B->Tpair[k] += ti[k];", 1)],
+        [PART + "test_hertz_pair_force_applied_to_both_particles"]),
     "gyroscopic term with the wrong sign": (
         [("cross(wb, L, wl);", "cross(L, wb, wl);", 1)],
         [PART + "test_symmetric_top_free_precession"]),

@@ -366,3 +366,30 @@ def test_colour_rule_sign(drho):
     phi_far = (rho[0] - rho[1])[far].mean()
     assert np.sign(phi_near - phi_far) == np.sign(drho)
     assert abs(phi_near - phi_far) > 1e-3
+
+
+def test_hertz_pair_force_applied_to_both_particles():
+    """The pair step applies the Berne–Pechukas Hertz interaction (Eq. 6-8)
+    of lbref_pair_hertz with r = X_B − X_A: +f_j on B, −f_j on A, and each
+    particle's own torque.  Isolated as the difference between runs with and
+    without the Hertz constant (no lubrication), two overlapping ellipsoids
+    held in place."""
+    n = (32, 24, 24)
+    rho0 = np.zeros((2, 24, 24, 32))
+    rho0[0] = 1.0
+    qa, qb = W.axis_tilt_quaternion(0.7, 0.2), W.axis_tilt_quaternion(1.2, -0.4)
+    xa, xb = np.array([13.0, 12.0, 12.0]), np.array([19.5, 12.8, 11.6])
+    out = []
+    for k in (100.0, 0.0):
+        L = lbref.Lattice(n, rho0, g_br=0.0, particle_mode=1, k_hertz=k, lub_cut=0.0)
+        L.add_particles([xa, xb], [qa, qb], 6.0, 3.0, 0.0)
+        L.step(1)
+        p = L.read_particles()
+        out.append((p["force"], p["torque"]))
+    dF, dT = out[0][0] - out[1][0], out[0][1] - out[1][1]
+    h = lbref.pair_hertz(100.0, 6.0, 3.0, xb - xa, _axis(qa), _axis(qb))
+    assert h["energy"] > 0  # they overlap
+    assert np.allclose(dF[1], h["f_j"], rtol=1e-12, atol=1e-14)
+    assert np.allclose(dF[0], -h["f_j"], rtol=1e-12, atol=1e-14)
+    assert np.allclose(dT[0], h["t_i"], rtol=1e-12, atol=1e-14)
+    assert np.allclose(dT[1], h["t_j"], rtol=1e-12, atol=1e-14)
