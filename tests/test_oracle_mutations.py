@@ -111,6 +111,14 @@ MUTANTS = {
         [("A->Tpair[k] += ti[k];\n                B->Tpair[k] += tj[k];",
           "A->Tpair[k] += tj[k];\n                B->Tpair[k] += ti[k];", 1)],
         [PART + "test_hertz_pair_force_applied_to_both_particles"]),
+    "inside test in the lab frame's transpose": (
+        [("d[k] = R[0][k] * dx[0] + R[1][k] * dx[1] + R[2][k] * dx[2];",
+          "d[k] = R[k][0] * dx[0] + R[k][1] * dx[1] + R[k][2] * dx[2];", 1)],
+        [PART + "test_coverage_matches_exact_rational_count", FLUID + "test_bruteforce_one_step_static_particle"]),
+    "inside test with the radii exchanged": (
+        [("double ip2 = 1.0 / (rp * rp), io2 = 1.0 / (ro * ro);",
+          "double ip2 = 1.0 / (ro * ro), io2 = 1.0 / (rp * rp);", 1)],
+        [PART + "test_coverage_matches_exact_rational_count"]),
     "gyroscopic term with the wrong sign": (
         [("cross(wb, L, wl);", "cross(L, wb, wl);", 1)],
         [PART + "test_symmetric_top_free_precession"]),
