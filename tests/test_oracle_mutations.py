@@ -119,6 +119,14 @@ MUTANTS = {
         [("double ip2 = 1.0 / (rp * rp), io2 = 1.0 / (ro * ro);",
           "double ip2 = 1.0 / (ro * ro), io2 = 1.0 / (rp * rp);", 1)],
         [PART + "test_coverage_matches_exact_rational_count"]),
+    "uncovered node at the particle's translation only": (
+        [("cross(P->W, r, wr);\n            for (int k = 0; k < 3; k++) us[k] = P->V[k] + wr[k];",
+          "cross(P->W, r, wr);\n            for (int k = 0; k < 3; k++) us[k] = P->V[k];", 1)],
+        [PART + "test_uncovered_node_gets_the_local_equilibrium"]),
+    "uncovered node's density over neighbours the particle now covers": (
+        [("if (m < 0 || c->type[m] != T_FLUID || c->nowner[m] >= 0) continue;",
+          "if (m < 0 || c->type[m] != T_FLUID) continue;", 1)],
+        [PART + "test_uncovered_node_gets_the_local_equilibrium"]),
     "gyroscopic term with the wrong sign": (
         [("cross(wb, L, wl);", "cross(L, wb, wl);", 1)],
         [PART + "test_symmetric_top_free_precession"]),
