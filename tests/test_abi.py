@@ -1,5 +1,6 @@
-"""The C-ABI library loads and exports every symbol include/lbe.h declares
-(no compute calls: this runs without a GPU)."""
+"""The C-ABI library loads and exports every symbol include/lbe.h declares,
+and its host-side checks and arithmetic behave as documented (no compute
+calls: this runs without a GPU)."""
 import ctypes
 import os
 import re
@@ -67,3 +68,39 @@ def test_library_fails_loudly_without_the_shared_object(tmp_path):
             lbe.load(str(tmp_path / "missing.so"))
         finally:
             lbe._lib = saved
+
+
+def test_invalid_descriptors_are_rejected_before_any_device_work():
+    """lbe_init_lattice checks its descriptor on the host and returns
+    LBE_EINVAL (-1) without touching a device (so this runs without one)."""
+    import numpy as np
+    from paper_1109_3277_gb300 import lbe
+    ok = dict(shape=(8, 8, 8))
+    bad = [dict(shape=(0, 8, 8)), dict(shape=(8, 8, 2), walls_z=True), dict(tau=(0.5, 1.0)),
+           dict(tau=(1.0, float("nan"))), dict(storage=7), dict(particle_mode=5), dict(flags=8),
+           dict(shape=(1, 70000, 1))]
+    for b in bad:
+        p = dict(ok, **b)
+        shape = p.pop("shape")
+        nx, ny, nz = shape
+        with pytest.raises(lbe.LbeError) as e:
+            lbe.Lattice(shape, np.full((2, nz, ny, nx), 0.5), **p)
+        assert e.value.status == -1, b
+
+
+def test_footprint_arithmetic():
+    """lbe_footprint is host arithmetic: the 16-bit modes save exactly half
+    of the two population buffers, particles add their arrays and the link
+    list, and an invalid descriptor gives 0."""
+    from paper_1109_3277_gb300 import lbe
+    shape = (40, 36, 30)
+    N = 40 * 36 * 30
+    S = ((N + 127) // 128) * 128 + 384
+    f32 = lbe.footprint(shape, storage="f32")
+    f16 = lbe.footprint(shape, storage="f16")
+    assert f32 - f16 == 2 * 2 * 19 * S * 2
+    assert lbe.footprint(shape, storage="bf16") == f16
+    with_p = lbe.footprint(shape, 10, storage="f16")
+    assert with_p - f16 >= N * 8
+    assert lbe.footprint((0, 36, 30)) == 0
+    assert lbe.footprint(shape, storage=9) == 0
