@@ -67,8 +67,14 @@ def far_column(shape, pos):
     return int(np.floor(pos[0] + nx / 2.0)) % nx, int(np.floor(pos[1] + ny / 2.0)) % ny
 
 
-def calibrate(delta_rhos, steps=6000, shape=(48, 48, 40), radius=5.0, storage="f32", chunk=500, seed=1115):
+def calibrate(delta_rhos, steps=6000, shape=(48, 48, 40), radius=5.0, storage="f32", chunk=500, seed=1115,
+              lattice=None):
     """Run one box per Δρ together and return the contact angles.
+
+    ``lattice`` replaces the library's lattice class (then the boxes step one
+    after the other instead of as a batch); any class with the constructor,
+    add_particles, step, read_particles, read_fields and close of
+    ``lbe.Lattice`` will do.
 
     Returns a dict: ``delta_rho``; ``theta_deg`` (per box, after ``steps``);
     ``height`` (sphere centre minus far interface height, per box); the
@@ -79,29 +85,34 @@ def calibrate(delta_rhos, steps=6000, shape=(48, 48, 40), radius=5.0, storage="f
              for d in delta_rhos]
     lats = []
     for w in boxes:
-        g = lbe.Lattice(w.shape, w.rho0, storage=storage, **w.params)
+        g = (lattice or lbe.Lattice)(w.shape, w.rho0, storage=storage, **w.params)
         p = w.particles
         g.add_particles(p["pos"], p["quat"], p["r_par"], p["r_perp"], p["delta_rho"])
         lats.append(g)
-    batch = lbe.Batch(lats)
+    batch = lbe.Batch(lats) if lattice is None else None
     trace = []
     done = 0
     t0 = time.perf_counter()
     while done < steps:
         n = min(chunk, steps - done)
-        batch.step(n)
+        if batch is not None:
+            batch.step(n)
+        else:
+            for g in lats:
+                g.step(n)
         done += n
         trace.append([float(g.read_particles()["pos"][0, 2]) for g in lats])
     dt = time.perf_counter() - t0
     thetas, heights = [], []
     for g in lats:
         pos = g.read_particles()["pos"][0]
-        rho, _, _ = g.read_fields(vel=False)
+        rho, _, _ = g.read_fields()
         x, y = far_column(shape, pos)
         zi = interface_height(rho, x, y)
         heights.append(float(pos[2] - zi))
         thetas.append(contact_angle(pos[2], zi, radius))
-    batch.close()
+    if batch is not None:
+        batch.close()
     for g in lats:
         g.close()
     d = np.asarray(delta_rhos, dtype=np.float64)

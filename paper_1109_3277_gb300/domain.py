@@ -54,15 +54,19 @@ def fit_inverse(concentrations, sizes):
     return float(a), float(b)
 
 
-def study(concentrations, n=256, steps=20000, checkpoint=5000, storage="f16", **box):
+def study(concentrations, n=256, steps=20000, checkpoint=5000, storage="f16", lattice=None, **box):
     """One lattice per concentration, run for ``steps`` with L recorded at
     every ``checkpoint``; returns the L(t) series, the final sizes, the fit
-    of L = a/C + b and the node updates per second of the stepping."""
+    of L = a/C + b and the node updates per second of the stepping.
+    ``lattice`` is the lattice class (default: the library's ``lbe.Lattice``;
+    any class with its constructor, add_particles, step, mass, read_fields
+    and close will do)."""
+    make = lattice or lbe.Lattice
     out = {"C": [], "C_placed": [], "particles": [], "step": [], "L": [], "L_final": []}
     busy, nodes = 0.0, 0
     for C in concentrations:
         w = W.bijel_study_box(float(C), n=n, steps=steps, **box)
-        g = lbe.Lattice(w.shape, w.rho0, storage=storage, **w.params)
+        g = make(w.shape, w.rho0, storage=storage, **w.params)
         p = w.particles
         g.add_particles(p["pos"], p["quat"], p["r_par"], p["r_perp"], p["delta_rho"])
         series, marks, done = [], [], 0
@@ -73,7 +77,7 @@ def study(concentrations, n=256, steps=20000, checkpoint=5000, storage="f16", **
             g.mass()  # synchronises
             busy += time.perf_counter() - t0
             done += k
-            rho, _, typ = g.read_fields(vel=False)
+            rho, _, typ = g.read_fields()
             series.append(domain_size(rho, typ == 0)[0])
             marks.append(done)
         g.close()

@@ -134,3 +134,24 @@ def test_package_domain_size_matches_the_oracle():
     assert lx == pytest.approx(8.0, rel=1e-12)
     assert D.fit_inverse([0.1, 0.2, 0.25], [2.2 / 0.1 + 11.08, 2.2 / 0.2 + 11.08, 2.2 / 0.25 + 11.08]) == \
         pytest.approx((2.2, 11.08), rel=1e-12)
+
+
+def test_study_drivers_run_on_the_oracle():
+    """The calibration and domain-size drivers, with the oracle's lattice
+    class standing in for the library's (tiny boxes, few steps): their
+    bookkeeping of chunks, heights, angles, concentrations and fits."""
+    from oracle import lbref
+    from paper_1109_3277_gb300 import contact_angle as CA
+    from paper_1109_3277_gb300 import domain as D
+    r = CA.calibrate([-0.05, 0.05], steps=30, shape=(16, 16, 16), radius=3.0, chunk=15,
+                     lattice=lbref.Lattice)
+    assert len(r["trace"]) == 2 and all(len(t) == 2 for t in r["trace"])
+    assert all(np.isfinite(r["theta_deg"])) and all(0.0 <= t <= 180.0 for t in r["theta_deg"])
+    for h, t in zip(r["height"], r["theta_deg"]):
+        assert t == pytest.approx(np.degrees(np.arccos(np.clip(-h / 3.0, -1, 1))), abs=1e-9)
+    d = D.study([0.1, 0.2], n=32, steps=20, checkpoint=10, lattice=lbref.Lattice)
+    assert d["step"] == [10, 20] and all(len(s) == 2 for s in d["L"])
+    assert all(np.isfinite(d["L_final"])) and all(L > 0 for L in d["L_final"])
+    vol = 4.0 / 3.0 * np.pi * 8.0 * 4.0 * 4.0
+    assert d["C_placed"] == pytest.approx([p * vol / 32 ** 3 for p in d["particles"]], rel=1e-12)
+    assert np.isfinite(d["a"]) and np.isfinite(d["b"])
