@@ -30,20 +30,22 @@ def tilt_deg(quat):
     return float(np.degrees(np.arccos(min(1.0, abs(az)))))
 
 
-def trajectories(tilts_deg, steps=8000, chunk=250, storage="f32", **box):
+def trajectories(tilts_deg, steps=8000, chunk=250, storage="f32", lattice=None, **box):
     """Run one box per starting angle together.
 
     Returns a dict with ``tilt0_deg`` and ``step`` (the chunk ends), and per
     box ``z`` (the centre minus the far interface height) and ``phi_deg``
-    (the tilt) at every chunk end, plus ``mlups`` and ``seconds``."""
+    (the tilt) at every chunk end, plus ``mlups`` and ``seconds``.
+    ``lattice`` replaces the library's lattice class (the boxes then step one
+    after the other instead of as a batch)."""
     works = [W.adsorption_study_box(float(t), **box) for t in tilts_deg]
     lats = []
     for w in works:
-        g = lbe.Lattice(w.shape, w.rho0, storage=storage, **w.params)
+        g = (lattice or lbe.Lattice)(w.shape, w.rho0, storage=storage, **w.params)
         p = w.particles
         g.add_particles(p["pos"], p["quat"], p["r_par"], p["r_perp"], p["delta_rho"])
         lats.append(g)
-    batch = lbe.Batch(lats)
+    batch = lbe.Batch(lats) if lattice is None else None
     z = [[] for _ in lats]
     phi = [[] for _ in lats]
     marks = []
@@ -51,19 +53,24 @@ def trajectories(tilts_deg, steps=8000, chunk=250, storage="f32", **box):
     while done < steps:
         n = min(chunk, steps - done)
         t0 = time.perf_counter()
-        batch.step(n)
+        if batch is not None:
+            batch.step(n)
+        else:
+            for g in lats:
+                g.step(n)
         for k, g in enumerate(lats):
             st = g.read_particles()
             pos = st["pos"][0]
             if k == 0:
                 busy += time.perf_counter() - t0
-            rho, _, _ = g.read_fields(vel=False)
+            rho, _, _ = g.read_fields()
             zi = CA.interface_height(rho, *CA.far_column(g.shape, pos))
             z[k].append(float(pos[2] - zi))
             phi[k].append(tilt_deg(st["quat"][0]))
         done += n
         marks.append(done)
-    batch.close()
+    if batch is not None:
+        batch.close()
     for g in lats:
         g.close()
     nodes = sum(int(np.prod(w.shape)) for w in works)

@@ -155,3 +155,12 @@ def test_study_drivers_run_on_the_oracle():
     vol = 4.0 / 3.0 * np.pi * 8.0 * 4.0 * 4.0
     assert d["C_placed"] == pytest.approx([p * vol / 32 ** 3 for p in d["particles"]], rel=1e-12)
     assert np.isfinite(d["a"]) and np.isfinite(d["b"])
+    from paper_1109_3277_gb300 import adsorption as AD
+    t = AD.trajectories([10.0, 80.0], steps=20, chunk=10, lattice=lbref.Lattice, edge=24, r_par=6.0,
+                        r_perp=3.0)
+    assert t["step"] == [10, 20] and all(len(z) == 2 for z in t["z"])
+    # after 10 of the first steps the ellipsoids have barely moved or turned
+    assert t["phi_deg"][0][0] == pytest.approx(10.0, abs=0.5) and t["phi_deg"][1][0] == pytest.approx(80.0, abs=0.5)
+    for k, tilt in enumerate((10.0, 80.0)):
+        half = np.hypot(6.0 * np.cos(np.radians(tilt)), 3.0 * np.sin(np.radians(tilt)))
+        assert t["z"][k][0] == pytest.approx(half - 2.0 + 0.5, abs=0.3)
