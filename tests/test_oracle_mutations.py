@@ -127,6 +127,10 @@ MUTANTS = {
         [("if (m < 0 || c->type[m] != T_FLUID || c->nowner[m] >= 0) continue;",
           "if (m < 0 || c->type[m] != T_FLUID) continue;", 1)],
         [PART + "test_uncovered_node_gets_the_local_equilibrium"]),
+    "prescribed rotation about the body-frame axis": (
+        [("for (int k = 0; k < 3; k++) wb[k] = R[0][k] * W[0] + R[1][k] * W[1] + R[2][k] * W[2];",
+          "for (int k = 0; k < 3; k++) wb[k] = W[k];", 1)],
+        [PART + "test_prescribed_motion_closed_form"]),
     "gyroscopic term with the wrong sign": (
         [("cross(wb, L, wl);", "cross(L, wb, wl);", 1)],
         [PART + "test_symmetric_top_free_precession"]),

@@ -440,3 +440,28 @@ def test_uncovered_node_gets_the_local_equilibrium(case):
             assert np.allclose(f[comp, :, z, y, x], lbref.feq(rbar[comp], us), rtol=0, atol=1e-14)
     if case == "spinning ellipsoid":
         assert bordering > 0
+
+
+def test_prescribed_motion_closed_form():
+    """Prescribed mode (the driven particles of the parity and serving
+    tests): the centre moves by V every step and the orientation turns about
+    the fixed lab-frame ω by |ω| per step, whatever the fluid does."""
+    n = 24
+    rho0 = W.uniform_mixture((n, n, n), 0.5, 0.05, seed=4)
+    V = np.array([0.03, -0.02, 0.01])
+    om = np.array([0.01, 0.02, -0.015])
+    q0 = W.axis_tilt_quaternion(0.4, 1.1)
+    L = lbref.Lattice((n, n, n), rho0, g_br=0.1, particle_mode=2)
+    L.add_particles([[11.0, 12.0, 12.5]], [q0], 5.0, 2.5, 0.05, vel=[V], omega=[om])
+    steps = 25
+    L.step(steps)
+    p = L.read_particles()
+    assert np.allclose(p["pos"][0], np.array([11.0, 12.0, 12.5]) + steps * V, atol=1e-12)
+    ang = np.linalg.norm(om) * steps
+    ax = om / np.linalg.norm(om)
+
+    def rot(v):  # Rodrigues: rotation by ang about ax
+        return v * np.cos(ang) + np.cross(ax, v) * np.sin(ang) + ax * (ax @ v) * (1 - np.cos(ang))
+
+    assert np.allclose(_axis(p["quat"][0]), rot(_axis(q0)), atol=1e-10)
+    assert np.allclose(p["vel"][0], V) and np.allclose(p["omega"][0], om)
