@@ -10,9 +10,9 @@
 // the population array, completion on an mbarrier) where the lattice's row
 // pitch allows it, else by per-thread loads.  ψ of the tile and a one-node
 // halo (written by the density kernel on fluid nodes, by the shell fill on
-// solid nodes) goes into a three-plane ring; the force at a node reads its
-// 18 neighbours' ψ from the ring.  Moments, force, collision
-// and the stores of one node run in one thread.
+// solid nodes) goes into a four-slot ring of planes; the force at a node
+// reads its 18 neighbours' ψ from the ring.  Moments, force, collision and
+// the stores of one node run in one thread, on (red, blue) pairs.
 //
 // Populations streaming into a wall or particle node are reflected into the
 // opposite slot of their own node (halfway bounce-back).  For particle
@@ -46,7 +46,7 @@ struct Smem {
     static constexpr int CTAS = sizeof(typename S::T) == 2 ? 3 : 2;
     static constexpr size_t plane = 2 * Q * NT * sizeof(typename S::T);  // one staged plane
     static constexpr size_t stage = 0;                                   // T [2][2Q][NT]
-    static constexpr size_t sps = stage + 2 * plane;                     // float2 [4][HN] (ψ_r, ψ_b)
+    static constexpr size_t sps = stage + 2 * plane;                     // float2 [4][HN] (ψ_b, ψ_r)
     static constexpr size_t sty = sps + 4 * HN * sizeof(float2);         // uint8 [4][HN]
     static constexpr size_t bar = (sty + 4 * HN + 15) / 16 * 16;          // uint64 [2] mbarriers
     static constexpr size_t bytes = bar + 2 * sizeof(unsigned long long) + 128;  // + alignment slack
