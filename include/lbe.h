@@ -169,29 +169,35 @@ LBE_API size_t lbe_device_bytes(const lbe_ctx *c);
  * allocates nothing: its per-block partial sums live in a fixed 16 KiB array
  * (2 x 1024 doubles) that the library keeps on every GPU that loads it until
  * the process exits.
- *  f:         device pointer, populations of component c and direction i at
- *             f + (c*19 + i) * slot_stride (elements of the storage type;
- *             the 16-bit modes hold f - w_i rho_ref[c]);
+ *  f:         device pointer, the library's population layout: the two
+ *             components of direction i at node n side by side, component c
+ *             at element 2 * (i * slot_stride + n) + c (elements of the
+ *             storage type; the 16-bit modes hold f - w_i rho_ref[c]);
  *  node_type: device pointer, [nodes] bytes, 0 = fluid (summed), others skipped;
  *  rho_ref:   host pointer to 2 doubles (ignored for LBE_STORE_F32);
  *  out:       device pointer to 2 doubles, written in stream order;
- *  device:    CUDA device ordinal, or -1 for the library's current device;
+ *  device:    CUDA device ordinal, or -1 for the caller's current device;
+ *             the caller's current device is the same on return;
  *  cuda_stream: the cudaStream_t to enqueue on (NULL = legacy default).
  * Returns LBE_EINVAL for a null pointer, nodes < 1 or nodes >
- * LBE_NOALLOC_MAX_NODES, slot_stride < nodes or an unknown storage mode;
- * LBE_ECUDA if a CUDA call fails.  The first call on a device looks up the
- * device address of the fixed array (cudaGetSymbolAddress): make that first
- * call before any stream capture.  All calls share the one array, so calls
- * that overlap on the GPU (other streams, other threads) race and must be
- * ordered by the caller. */
+ * LBE_NOALLOC_MAX_NODES, slot_stride < nodes, device < -1 or an unknown
+ * storage mode; LBE_ECUDA if a CUDA call fails.  The first call on a device
+ * looks up the device address of the fixed array (cudaGetSymbolAddress):
+ * make that first call before any stream capture.  The address stays cached
+ * for the life of the process and does not survive a cudaDeviceReset of
+ * that device.  All calls share the one array, so calls that overlap on the
+ * GPU (other streams, other threads) race and must be ordered by the
+ * caller. */
 #define LBE_NOALLOC_MAX_NODES 2147483647LL
 LBE_API lbe_status lbe_mass_noalloc(const void *f, int32_t storage, const uint8_t *node_type,
                                     int64_t nodes, int64_t slot_stride, const double rho_ref[2],
                                     int32_t device, void *cuda_stream, double *out);
 
-/* Pick the fused kernel's z-chunk length for this lattice by timing the
- * candidates with CUDA events on the current state (which is not changed);
- * later steps use the fastest.  *chosen_zc (may be NULL) receives it. */
+/* Pick the fused kernel's tile height and z-chunk length for this lattice
+ * by timing the candidates (heights 8 and, where built, 4, times chunks
+ * 4, 8, 16, ... and the full height) with CUDA events on the current state
+ * (which is not changed); later steps use the fastest.  *chosen_zc (may be
+ * NULL) receives the chunk; lbe_get_tile gives both. */
 LBE_API lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc);
 
 /* Set the fused kernel's z-chunk length (planes per CTA; 0 restores the
@@ -200,6 +206,27 @@ LBE_API lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc);
  * never a result.  Synchronises first (and returns a pending error of
  * earlier steps).  LBE_EINVAL for a negative length. */
 LBE_API lbe_status lbe_set_zchunk(lbe_ctx *c, int32_t zc);
+
+/* The fused kernel's tile: 32 nodes wide and rows = 4 or 8 rows high (4 is
+ * built for τ = 1 lattices with TMA copies; others take 8), walking a z
+ * chunk of zc planes (0: the default for the lattice).  lbe_autotune picks
+ * both; lbe_set_tile fixes them (synchronises first, LBE_EINVAL for other
+ * heights or a negative chunk) and lbe_get_tile reads the ones in use
+ * (0, 0 with LBE_FLAG_TWO_PASS).  Only the order in which nodes are
+ * visited depends on them, never a result. */
+LBE_API lbe_status lbe_set_tile(lbe_ctx *c, int32_t rows, int32_t zc);
+LBE_API lbe_status lbe_get_tile(const lbe_ctx *c, int32_t *rows, int32_t *zc);
+
+/* Failure detection of the fused kernel's copies: every wait for a plane's
+ * box copy gives up after a bounded number of tries (about 2^22 by
+ * default; each try may suspend the thread for a while).  The CTA then
+ * stops, waits with the default bound for its copies in flight, and sets
+ * the lattice's status word; the next synchronising call returns
+ * LBE_ETIMEOUT.  lbe_set_wait_limit sets the number of tries (0 restores
+ * the default) so that tests can make the wait run out; a run that timed
+ * out has left the populations of the step partly written.  Synchronises
+ * first; LBE_EINVAL for a negative count. */
+LBE_API lbe_status lbe_set_wait_limit(lbe_ctx *c, int32_t tries);
 
 /* Batches: several lattices stepped together, every kernel of the step
  * covering all of them in one launch (the fused fluid kernel as a persistent

@@ -55,53 +55,41 @@ __device__ __forceinline__ int nidx(const Lat &L, const Nbr &b, int i)
     return b.xs[cx(i) + 1] + L.nx * (b.ys[cy(i) + 1] + L.ny * z);
 }
 
-template <class S>
-__device__ __forceinline__ const typename S::T *slot(const typename S::T *f, const Lat &L, int c,
-                                                     int i)
-{
-    return f + (size_t)(c * Q + i) * (size_t)L.S;
-}
-template <class S>
-__device__ __forceinline__ typename S::T *slot(typename S::T *f, const Lat &L, int c, int i)
-{
-    return f + (size_t)(c * Q + i) * (size_t)L.S;
-}
-
 // ---------------------------------------------------------------- init
 
 template <class S>
-__global__ void k_init_f(Lat L, const double *__restrict__ rho0, typename S::T *__restrict__ f,
+__global__ void k_init_f(Lat L, const double *__restrict__ rho0, typename S::P *__restrict__ f,
                          const uint8_t *__restrict__ type)
 {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= L.N) return;
     bool fl = type[n] == FLUID;
+    const float r0 = fl ? (float)rho0[n] : 0.f, r1 = fl ? (float)rho0[(size_t)L.N + n] : 0.f;
 #pragma unroll
-    for (int c = 0; c < 2; c++) {
-        float r = fl ? (float)rho0[(size_t)c * L.N + n] : 0.f;
-#pragma unroll
-        for (int i = 0; i < Q; i++) S::st(slot<S>(f, L, c, i) + n, wgt(i) * r, L.base[c][i]);
-    }
+    for (int i = 0; i < Q; i++) st2f<S>(f, L, i, n, make_float2(wgt(i) * r0, wgt(i) * r1));
 }
 
 // ------------------------------------------------------------- moments
 // ρ^c = Σ_i f_i^c on fluid nodes and ψ^c = 1 - exp(-ρ^c) (Eq. 3's weight).
 
 template <class S>
-__global__ void __launch_bounds__(256) k_moments(Lat L, const typename S::T *__restrict__ f,
+__global__ void __launch_bounds__(256) k_moments(Lat L, const typename S::P *__restrict__ f,
                                                  const uint8_t *__restrict__ type,
                                                  float *__restrict__ rho, float *__restrict__ psi)
 {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= L.N || type[n] != FLUID) return;
+    float r0 = 0.f, r1 = 0.f;
 #pragma unroll
-    for (int c = 0; c < 2; c++) {
-        float r = 0.f;
-#pragma unroll
-        for (int i = 0; i < Q; i++) r += S::ld(slot<S>(f, L, c, i) + n, L.base[c][i]);
-        rho[(size_t)c * L.N + n] = r;
-        psi[(size_t)c * L.N + n] = 1.f - expf(-r);
+    for (int i = 0; i < Q; i++) {
+        const float2 v = ld2f<S>(f, L, i, n);
+        r0 += v.x;
+        r1 += v.y;
     }
+    rho[n] = r0;
+    rho[(size_t)L.N + n] = r1;
+    psi[n] = 1.f - expf(-r0);
+    psi[(size_t)L.N + n] = 1.f - expf(-r1);
 }
 
 // ------------------------------------------------------------ densities
@@ -109,45 +97,21 @@ __global__ void __launch_bounds__(256) k_moments(Lat L, const typename S::T *__r
 // kernel, and ψ^c = 1 - exp(-ρ^c) for the fused kernel (which sums its own
 // nodes' stored populations in the same order and adds ρ_ref the same way,
 // so the two agree bit for bit; the shell fill writes ψ of the solid nodes
-// into the same array).  One thread
-// per pair of consecutive nodes, with paired loads; the slot stride S is
-// padded past N, so the pair loads of the last node stay inside the
-// allocation.
+// into the same array).  One thread per node: each pair load brings both
+// components of a direction.
 
 template <class S>
-__global__ void __launch_bounds__(256) k_rho(Lat L, const typename S::T *__restrict__ f,
+__global__ void __launch_bounds__(256) k_rho(Lat L, const typename S::P *__restrict__ f,
                                              const uint8_t *__restrict__ type, float *__restrict__ rho,
                                              float *__restrict__ psi)
 {
-    const long long n = 2ll * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
-    if (n >= L.N) return;
-    const bool two = n + 1 < L.N;
-    const bool fl0 = type[n] == FLUID, fl1 = two && type[n + 1] == FLUID;
-    if (!fl0 && !fl1) return;
-#pragma unroll
-    for (int c = 0; c < 2; c++) {
-        // Σ_i of the stored quantities (δf_i, or f_i in FP32) in index
-        // order, plus ρ_ref (0 in FP32)
-        float a0, a1;
-        S::ld2(slot<S>(f, L, c, 0) + n, 0.f, a0, a1);
-#pragma unroll
-        for (int i = 1; i < Q; i++) {
-            float v0, v1;
-            S::ld2(slot<S>(f, L, c, i) + n, 0.f, v0, v1);
-            a0 = __fadd_rn(a0, v0);
-            a1 = __fadd_rn(a1, v1);
-        }
-        a0 = __fadd_rn(L.rref[c], a0);
-        a1 = __fadd_rn(L.rref[c], a1);
-        if (fl0) {
-            rho[(size_t)c * L.N + n] = a0;
-            psi[(size_t)c * L.N + n] = 1.f - expf(-a0);
-        }
-        if (fl1) {
-            rho[(size_t)c * L.N + n + 1] = a1;
-            psi[(size_t)c * L.N + n + 1] = 1.f - expf(-a1);
-        }
-    }
+    const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (n >= L.N || type[n] != FLUID) return;
+    const float2 r = node_rho2<S>(f, L, n);
+    rho[n] = r.x;
+    rho[(size_t)L.N + n] = r.y;
+    psi[n] = 1.f - expf(-r.x);
+    psi[(size_t)L.N + n] = 1.f - expf(-r.y);
 }
 
 // Neighbour indexing on a 3D grid (x per thread, one y row and z plane per
@@ -224,16 +188,12 @@ __global__ void __launch_bounds__(256) k_rho_batch(BatchIndex B, int total)
         const BoxDev &bx = batch_site(B, g, s);
         if (bx.type[s.n] != FLUID) continue;
         const int b = find_box(B.node0, B.nbox, g);
-        const typename S::T *f = (const typename S::T *)bx.f[B.par[2 * b]];
-#pragma unroll
-        for (int c = 0; c < 2; c++) {
-            float r = S::ld(slot<S>(f, bx.L, c, 0) + s.n, 0.f);
-#pragma unroll
-            for (int i = 1; i < Q; i++) r = __fadd_rn(r, S::ld(slot<S>(f, bx.L, c, i) + s.n, 0.f));
-            r = __fadd_rn(bx.L.rref[c], r);
-            bx.rho[(size_t)c * bx.L.N + s.n] = r;
-            bx.psi[(size_t)c * bx.L.N + s.n] = 1.f - expf(-r);
-        }
+        const typename S::P *f = (const typename S::P *)bx.f[B.par[2 * b]];
+        const float2 r = node_rho2<S>(f, bx.L, s.n);
+        bx.rho[s.n] = r.x;
+        bx.rho[(size_t)bx.L.N + s.n] = r.y;
+        bx.psi[s.n] = 1.f - expf(-r.x);
+        bx.psi[(size_t)bx.L.N + s.n] = 1.f - expf(-r.y);
     }
 }
 
@@ -301,8 +261,8 @@ __global__ void __launch_bounds__(256) k_shell_batch(BatchIndex B, int total)
 // whose target is solid is reflected into the opposite slot of its own node.
 
 template <class S>
-__global__ void __launch_bounds__(256) k_collide_stream(Lat L, const typename S::T *__restrict__ fin,
-                                                        typename S::T *__restrict__ fout,
+__global__ void __launch_bounds__(256) k_collide_stream(Lat L, const typename S::P *__restrict__ fin,
+                                                        typename S::P *__restrict__ fout,
                                                         const float *__restrict__ psi,
                                                         const uint8_t *__restrict__ type)
 {
@@ -312,9 +272,11 @@ __global__ void __launch_bounds__(256) k_collide_stream(Lat L, const typename S:
     Nbr b = nbr_of(L, co);
     float f[2][Q];
 #pragma unroll
-    for (int c = 0; c < 2; c++)
-#pragma unroll
-        for (int i = 0; i < Q; i++) f[c][i] = S::ld(slot<S>(fin, L, c, i) + n, L.base[c][i]);
+    for (int i = 0; i < Q; i++) {
+        const float2 v = ld2f<S>(fin, L, i, n);
+        f[0][i] = v.x;
+        f[1][i] = v.y;
+    }
     float rho[2], j[2][3];
 #pragma unroll
     for (int c = 0; c < 2; c++) {
@@ -352,6 +314,7 @@ __global__ void __launch_bounds__(256) k_collide_stream(Lat L, const typename S:
     bool solid_nb[Q];
 #pragma unroll
     for (int i = 1; i < Q; i++) solid_nb[i] = nb[i] < 0 || type[nb[i]] != FLUID;
+    float fs[2][Q];
 #pragma unroll
     for (int c = 0; c < 2; c++) {
         float pc = psi[(size_t)c * L.N + n];
@@ -373,22 +336,27 @@ __global__ void __launch_bounds__(256) k_collide_stream(Lat L, const typename S:
             float cu = cx(i) * ue[0] + cy(i) * ue[1] + cz(i) * ue[2];
             float feq = wgt(i) * r * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
             seq += feq;
-            float fs = f[c][i] - (f[c][i] - feq) * it;
-            if (!solid_nb[i]) {
-                S::st(slot<S>(fout, L, c, i) + nb[i], fs, L.base[c][i]);
-            } else {
-                S::st(slot<S>(fout, L, c, opp(i)) + n, fs, L.base[c][opp(i)]);
-            }
+            fs[c][i] = f[c][i] - (f[c][i] - feq) * it;
         }
-        float fs0 = f[c][0] - (f[c][0] - (r - seq)) * it;
-        S::st(slot<S>(fout, L, c, 0) + n, fs0, L.base[c][0]);
+        fs[c][0] = f[c][0] - (f[c][0] - (r - seq)) * it;
     }
+    // push both components of each direction: to the neighbour, or reflected
+    // into the opposite slot of this node (same weight, same base)
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        const float2 v = make_float2(fs[0][i], fs[1][i]);
+        if (!solid_nb[i])
+            st2f<S>(fout, L, i, nb[i], v);
+        else
+            st2f<S>(fout, L, opp(i), n, v);
+    }
+    st2f<S>(fout, L, 0, n, make_float2(fs[0][0], fs[1][0]));
 }
 
 // -------------------------------------------------------------- fields
 
 template <class S>
-__global__ void k_fields(Lat L, const typename S::T *__restrict__ f, const float *__restrict__ psi,
+__global__ void k_fields(Lat L, const typename S::P *__restrict__ f, const float *__restrict__ psi,
                          const uint8_t *__restrict__ type, double *__restrict__ rho_out,
                          double *__restrict__ vel_out)
 {
@@ -405,17 +373,16 @@ __global__ void k_fields(Lat L, const typename S::T *__restrict__ f, const float
     }
     Coord co = coord_of(L, n);
     Nbr b = nbr_of(L, co);
-    float rho[2], m[3] = {0.f, 0.f, 0.f};
+    float rho[2] = {0.f, 0.f}, m[3] = {0.f, 0.f, 0.f};
     for (int c = 0; c < 2; c++) {
-        float r = 0.f;
         for (int i = 0; i < Q; i++) {
-            float v = S::ld(slot<S>(f, L, c, i) + n, L.base[c][i]);
-            r += v;
+            const float2 v2 = ld2f<S>(f, L, i, n);
+            const float v = c ? v2.y : v2.x;
+            rho[c] += v;
             m[0] += cx(i) * v;
             m[1] += cy(i) * v;
             m[2] += cz(i) * v;
         }
-        rho[c] = r;
     }
     for (int c = 0; c < 2; c++) {
         float sx = 0.f, sy = 0.f, sz = 0.f;
@@ -452,31 +419,44 @@ constexpr int MASS_THREADS = 256;
 // so s + e is the exact sum up to the rounding of the small term e (about
 // 1e-15 of the node's mass), and only two FP64 additions per node and
 // component remain (FP64 arithmetic is slow on this part).
-template <class S>
-__device__ __forceinline__ double node_mass(const Lat &L, const typename S::T *__restrict__ f, int c, int n)
+__device__ __forceinline__ void two_sum_acc(float &s, float &e, float v)
 {
-    float s = S::ld(slot<S>(f, L, c, 0) + n, L.base[c][0]), e = 0.f;
-#pragma unroll
-    for (int i = 1; i < Q; i++) {
-        const float v = S::ld(slot<S>(f, L, c, i) + n, L.base[c][i]);
-        const float t = __fadd_rn(s, v);
-        const float vb = __fsub_rn(t, s);
-        e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(t, vb)), __fsub_rn(v, vb)));
-        s = t;
-    }
-    return (double)s + (double)e;
+    const float t = __fadd_rn(s, v);
+    const float vb = __fsub_rn(t, s);
+    e = __fadd_rn(e, __fadd_rn(__fsub_rn(s, __fsub_rn(t, vb)), __fsub_rn(v, vb)));
+    s = t;
 }
 
 template <class S>
-__global__ void __launch_bounds__(MASS_THREADS) k_mass(Lat L, const typename S::T *__restrict__ f,
+__device__ __forceinline__ void node_mass(const Lat &L, const typename S::P *__restrict__ f, long long n, double &m0,
+                                          double &m1)
+{
+    const float2 v0 = ld2f<S>(f, L, 0, n);
+    float s0 = v0.x, s1 = v0.y, e0 = 0.f, e1 = 0.f;
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        const float2 v = ld2f<S>(f, L, i, n);
+        two_sum_acc(s0, e0, v.x);
+        two_sum_acc(s1, e1, v.y);
+    }
+    m0 = (double)s0 + (double)e0;
+    m1 = (double)s1 + (double)e1;
+}
+
+// The grid-stride index is 64-bit: N may come within a stride of 2^31 - 1.
+template <class S>
+__global__ void __launch_bounds__(MASS_THREADS) k_mass(Lat L, const typename S::P *__restrict__ f,
                                                        const uint8_t *__restrict__ type,
                                                        double *__restrict__ partials)
 {
     double a0 = 0.0, a1 = 0.0;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < L.N; n += gridDim.x * blockDim.x) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < L.N; n += stride) {
         if (type[n] != FLUID) continue;
-        a0 += node_mass<S>(L, f, 0, n);
-        a1 += node_mass<S>(L, f, 1, n);
+        double m0, m1;
+        node_mass<S>(L, f, n, m0, m1);
+        a0 += m0;
+        a1 += m1;
     }
     __shared__ double sh[2][MASS_THREADS];
     sh[0][threadIdx.x] = a0;
@@ -521,6 +501,8 @@ __global__ void k_mass_final(const double *__restrict__ partials, int nb, double
 
 // --------------------------------------------------------- raw f access
 
+// The caller's layout is [2][19][N]; element (c, i, n) of the device
+// array is scalar 2 (i S + n) + c.
 template <class S>
 __global__ void k_get_f(Lat L, const typename S::T *__restrict__ f, double *__restrict__ out)
 {
@@ -529,7 +511,8 @@ __global__ void k_get_f(Lat L, const typename S::T *__restrict__ f, double *__re
     if (k >= tot) return;
     int ci = (int)(k / L.N);
     size_t n = k - (size_t)ci * L.N;
-    out[k] = (double)S::cvt(f[(size_t)ci * L.S + n], L.base[ci / Q][ci % Q]);
+    const int c = ci / Q, i = ci % Q;
+    out[k] = (double)(L.base[c][i] + S::raw(f[2 * pidx(L, i, (long long)n) + c]));
 }
 
 template <class S>
@@ -540,7 +523,8 @@ __global__ void k_set_f(Lat L, const double *__restrict__ in, typename S::T *__r
     if (k >= tot) return;
     int ci = (int)(k / L.N);
     size_t n = k - (size_t)ci * L.N;
-    f[(size_t)ci * L.S + n] = S::enc((float)in[k], L.base[ci / Q][ci % Q]);
+    const int c = ci / Q, i = ci % Q;
+    f[2 * pidx(L, i, (long long)n) + c] = S::enc((float)in[k] - L.base[c][i]);
 }
 
 inline unsigned blocks_for(size_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -562,22 +546,21 @@ void launch_init_f(int storage, const Lat &L, const double *rho0, void *f, const
                    cudaStream_t s)
 {
     LBE_DISPATCH(storage, (k_init_f<S><<<blocks_for(L.N, 256), 256, 0, s>>>(
-                              L, rho0, (typename S::T *)f, type)));
+                              L, rho0, (typename S::P *)f, type)));
 }
 
 void launch_moments(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho,
                     float *psi, cudaStream_t s)
 {
     LBE_DISPATCH(storage, (k_moments<S><<<blocks_for(L.N, 256), 256, 0, s>>>(
-                              L, (const typename S::T *)f, type, rho, psi)));
+                              L, (const typename S::P *)f, type, rho, psi)));
 }
 
 void launch_rho(int storage, const Lat &L, const void *f, const uint8_t *type, float *rho, float *psi,
                 cudaStream_t s)
 {
-    const size_t pairs = ((size_t)L.N + 1) / 2;
     LBE_DISPATCH(storage,
-                 (k_rho<S><<<blocks_for(pairs, 256), 256, 0, s>>>(L, (const typename S::T *)f, type, rho, psi)));
+                 (k_rho<S><<<blocks_for(L.N, 256), 256, 0, s>>>(L, (const typename S::P *)f, type, rho, psi)));
 }
 
 static unsigned batch_grid(int total)
@@ -607,21 +590,21 @@ void launch_collide_stream(int storage, const Lat &L, const void *fin, void *fou
                            const uint8_t *type, cudaStream_t s)
 {
     LBE_DISPATCH(storage, (k_collide_stream<S><<<blocks_for(L.N, 256), 256, 0, s>>>(
-                              L, (const typename S::T *)fin, (typename S::T *)fout, psi, type)));
+                              L, (const typename S::P *)fin, (typename S::P *)fout, psi, type)));
 }
 
 void launch_fields(int storage, const Lat &L, const void *f, const float *psi, const uint8_t *type,
                    double *rho_out, double *vel_out, cudaStream_t s)
 {
     LBE_DISPATCH(storage, (k_fields<S><<<blocks_for(L.N, 256), 256, 0, s>>>(
-                              L, (const typename S::T *)f, psi, type, rho_out, vel_out)));
+                              L, (const typename S::P *)f, psi, type, rho_out, vel_out)));
 }
 
 void launch_mass(int storage, const Lat &L, const void *f, const uint8_t *type, double *partials,
                  int nblocks, double *out, cudaStream_t s)
 {
     LBE_DISPATCH(storage, (k_mass<S><<<nblocks, MASS_THREADS, 0, s>>>(
-                              L, (const typename S::T *)f, type, partials)));
+                              L, (const typename S::P *)f, type, partials)));
     k_mass_final<<<1, MASS_THREADS, 0, s>>>(partials, nblocks, out);
 }
 

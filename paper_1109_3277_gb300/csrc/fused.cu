@@ -1,18 +1,24 @@
-// Fused fluid step (§2 of Günther et al., arXiv:1109.3277): the Shan–Chen
-// force (Eq. 3), the shifted-velocity BGK collision (Eq. 2) and push
-// streaming (Eq. 1) with halfway bounce-back, in one pass over the
-// populations.
+// Fused fluid step (§2 of Günther et al., arXiv:1109.3277): densities and
+// ψ = 1 - exp(-ρ) (the weight of Eq. 3), the Shan–Chen force (Eq. 3), the
+// shifted-velocity BGK collision (Eq. 2) and push streaming (Eq. 1) with
+// halfway bounce-back, in one pass over the populations.
 //
-// A CTA owns a TX x TY column of nodes and walks a chunk of z planes.  The
-// populations of its nodes in a plane are staged in shared memory, two
-// planes deep: while the warps collide plane z, the next plane is on its way
-// into the other stage, as one TMA tensor copy (a 32 x 8 x 38-slot box of
-// the population array, completion on an mbarrier) where the lattice's row
-// pitch allows it, else by per-thread loads.  ψ of the tile and a one-node
-// halo (written by the density kernel on fluid nodes, by the shell fill on
-// solid nodes) goes into a four-slot ring of planes; the force at a node
-// reads its 18 neighbours' ψ from the ring.  Moments, force, collision and
-// the stores of one node run in one thread, on (red, blue) pairs.
+// A CTA owns a 32 x TY column of nodes and walks a chunk of z planes.  For
+// every plane from one below the chunk to one above it, one TMA tensor copy
+// brings the populations of the tile and a one-node halo into shared memory
+// (a box of the (x, y, z, direction) array of (red, blue) pairs, x widened
+// to 16-byte boundaries), completing on an mbarrier.  Each thread sums the
+// densities of its node and of at most one halo node, so the ψ of the tile
+// and its halo is formed on chip; halo nodes beyond the lattice edge wrap
+// around and are read from global memory instead.  Solid nodes (walls,
+// particles) take their ψ from the shell fill, which ran before.  The ψ,
+// node type and a per-row bitmask of solid nodes go into a four-slot ring
+// of planes; the collision of plane z reads planes z-1, z and z+1 of it.
+//
+// With τ = 1 for both components the post-collision populations are the
+// equilibria, so a node's populations are needed only for its moments,
+// which are taken when its plane arrives: two stages suffice.  Other τ keep
+// three stages and re-read the node's populations at the collision.
 //
 // Populations streaming into a wall or particle node are reflected into the
 // opposite slot of their own node (halfway bounce-back).  For particle
@@ -29,8 +35,7 @@ namespace lbe {
 
 namespace {
 
-constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int HX = TX + 2, HY = TY + 2, HN = HX * HY, NHALO = HN - NT;
+constexpr int TX = FUSED_TX;
 
 __device__ __forceinline__ int wrapc(int v, int n)
 {
@@ -38,18 +43,58 @@ __device__ __forceinline__ int wrapc(int v, int n)
     return v < 0 ? v + n : v;
 }
 
-// Dynamic shared memory layout (bytes from a 128-byte aligned base).
-template <class S>
-struct Smem {
-    // CTAs per SM the kernels are compiled for: three at 16 bit (51 KB of
-    // shared memory each, 80 registers per thread), two in FP32 (90 KB each)
-    static constexpr int CTAS = sizeof(typename S::T) == 2 ? 3 : 2;
-    static constexpr size_t plane = 2 * Q * NT * sizeof(typename S::T);  // one staged plane
-    static constexpr size_t stage = 0;                                   // T [2][2Q][NT]
-    static constexpr size_t sps = stage + 2 * plane;                     // float2 [4][HN] (ψ_b, ψ_r)
-    static constexpr size_t sty = sps + 4 * HN * sizeof(float2);         // uint8 [4][HN]
-    static constexpr size_t bar = (sty + 4 * HN + 15) / 16 * 16;          // uint64 [2] mbarriers
-    static constexpr size_t bytes = bar + 2 * sizeof(unsigned long long) + 128;  // + alignment slack
+// Compile-time layout of one configuration: storage S, tile rows TY, GEN
+// (any τ) or not (τ = 1), and SELF (the box holds
+// the tile and a one-node halo, whose densities the kernel forms itself) or
+// not (the box holds the tile; ψ of every ring entry comes from memory).
+template <class S, int TY, bool GEN, bool SELF>
+struct Cfg {
+    using P = typename S::P;
+    static constexpr int NT = TX * TY;
+    static constexpr int E = (int)sizeof(P);          // bytes of one (red, blue) pair
+    static constexpr int PADX = SELF ? 16 / E : 0;    // x margin of the box: 16 bytes
+    static constexpr int BX = TX + 2 * PADX, BY = SELF ? TY + 2 : TY;
+    static constexpr int HX = TX + 2, HY = TY + 2, HN = HX * HY, NHALO = HN - NT;
+    // stage buffers: any τ with SELF re-reads plane z's box one iteration
+    // after its densities; every other configuration is done with a box in
+    // the iteration it arrives
+    static constexpr int NST = (GEN && SELF) ? 3 : 2;
+    static constexpr size_t plane = (size_t)Q * BY * BX * E;        // bytes of one box
+    static constexpr size_t pstride = (plane + 127) / 128 * 128;    // stages 128-byte aligned
+    // dynamic shared memory (bytes from a 128-byte aligned base)
+    static constexpr size_t stage = 0;                              // P [NST][Q][BY][BX]
+    static constexpr size_t sps = stage + NST * pstride;            // float2 [4][HN] (ψ_b, ψ_r)
+    static constexpr size_t smask = sps + 4 * HN * sizeof(float2);  // uint64 [4][HY] solid bits per row
+    static constexpr size_t bar = smask + 4 * HY * sizeof(unsigned long long);  // uint64 [NST] mbarriers
+    static constexpr size_t bytes = bar + NST * sizeof(unsigned long long) + 128;  // + alignment slack
+    // CTAs per SM the kernel is compiled for: what shared memory allows
+    // (228 KB per SM, about 1 KB of it reserved per CTA), capped so that a
+    // thread keeps at least 80 registers (τ = 1: 768 threads per SM) or 128
+    // (any τ: 512), which the node arithmetic needs without spilling.
+    static constexpr int by_smem = (int)((228 * 1024) / (bytes + 1024));
+    static constexpr int by_regs = (GEN ? 512 : 768) / NT;
+    static constexpr int CTAS = by_smem < by_regs ? (by_smem > 0 ? by_smem : 1) : by_regs;
+};
+
+// Per stage buffer counters kept in registers (every index a compile-time
+// constant after unrolling).
+template <int N>
+struct Counts {
+    int v[N];
+    __device__ __forceinline__ int get(int b) const
+    {
+        int r = v[0];
+#pragma unroll
+        for (int j = 1; j < N; j++)
+            if (b == j) r = v[j];
+        return r;
+    }
+    __device__ __forceinline__ void inc(int b)
+    {
+#pragma unroll
+        for (int j = 0; j < N; j++)
+            if (b == j) v[j]++;
+    }
 };
 
 __device__ __forceinline__ unsigned char *align128(unsigned char *p)
@@ -73,7 +118,7 @@ __device__ __forceinline__ void mbar_inval(unsigned long long *b)
 // make barrier initialisation visible to the asynchronous (TMA) proxy
 __device__ __forceinline__ void fence_barrier_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
-// order this thread's earlier shared-memory accesses before later TMA writes
+// order earlier shared-memory accesses before later TMA writes
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_expect_tx(unsigned long long *b, unsigned bytes)
@@ -98,17 +143,19 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned pa
 
 // Wait for the phase with this parity; false if it has not completed
 // within the iteration limit (each try may suspend the thread for a while).
-__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity)
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity, int limit)
 {
-    for (int k = 0; k < (1 << 22); k++)
+    for (int k = 0; k < limit; k++)
         if (mbar_try_wait(b, parity)) return true;
     return false;
 }
 
-// One plane of the tile: the box (x0, y0, z, slot 0) of size 32 x 8 x 1 x 38
-// of the 4D population tensor into shared memory, completing on b.
-__device__ __forceinline__ void tma_plane(void *dst, const CUtensorMap *map, int x0, int y0, int z,
-                                          unsigned long long *b)
+// One box of the 4D tensor of population pairs (x, y, z, direction) at
+// (x0, y0, z, 0) into shared memory, completing on b.  x0 * pair bytes is a
+// multiple of 16 (x0 = tile start - 16 bytes); out-of-range elements
+// (x0 or y0 negative, past the lattice) are filled with zeros.
+__device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *map, int x0, int y0, int z,
+                                        unsigned long long *b)
 {
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
@@ -123,7 +170,7 @@ __device__ __forceinline__ void tma_plane(void *dst, const CUtensorMap *map, int
 // inlines these computes the same bits: the single-lattice and the batched
 // fused kernels agree exactly.  Products with the lattice velocities c_i
 // (components 0 or ±1) are exact and stay plain.
-
+//
 // The two components go through the same node arithmetic, so it is done on
 // (red, blue) pairs with the paired FP32 instructions (add, multiply and
 // fused multiply-add on two lanes, each rounded to nearest like its scalar
@@ -133,6 +180,49 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Moments of the stored quantities d_i (δf_i at 16 bit, f_i in FP32) of a
+// node: Δρ^c = Σ_i d_i in direction order and j^c = Σ_i c_i d_i (the bases
+// w_i ρ_ref cancel in j, since Σ_i w_i c_i = 0).  ld(i) gives the (red,
+// blue) pair of direction i.
+struct Mom {
+    float2 dr;     // Δρ = ρ - ρ_ref (ρ itself in FP32)
+    float2 j[3];
+};
+
+template <class LD>
+__device__ __forceinline__ Mom moments(LD ld)
+{
+    Mom m;
+    float2 a = ld(0), jj[3] = {dup2(0.f), dup2(0.f), dup2(0.f)};
+#pragma unroll
+    for (int i = 1; i < Q; i += 2) {
+        // one pass over opposite pairs (i, i+1), c_{i+1} = -c_i; the sum
+        // accumulates in index order
+        const float2 va = ld(i), vb = ld(i + 1);
+        a = add2(a, va);
+        a = add2(a, vb);
+        const float2 d = sub2(va, vb);
+        if (cx(i)) jj[0] = cx(i) > 0 ? add2(jj[0], d) : sub2(jj[0], d);
+        if (cy(i)) jj[1] = cy(i) > 0 ? add2(jj[1], d) : sub2(jj[1], d);
+        if (cz(i)) jj[2] = cz(i) > 0 ? add2(jj[2], d) : sub2(jj[2], d);
+    }
+    m.dr = a;
+    m.j[0] = jj[0];
+    m.j[1] = jj[1];
+    m.j[2] = jj[2];
+    return m;
+}
+
+// Σ_i d_i in direction order (a halo node needs its density only).
+template <class LD>
+__device__ __forceinline__ float2 density_sum(LD ld)
+{
+    float2 a = ld(0);
+#pragma unroll
+    for (int i = 1; i < Q; i++) a = add2(a, ld(i));
+    return a;
+}
 
 // Equilibrium velocities of both components, u' + (τ_c/ρ_c) F^c with the
 // Shan–Chen force F^c = -g ψ^c s^c + ρ^c g_body (Eq. 3), and -1.5 u·u.
@@ -159,217 +249,200 @@ __device__ __forceinline__ void feq_parts(float w, float2 r, float2 dr, float2 w
     odd = mul2(w3r, cu);
 }
 
-// BGK relaxation f + (f^eq - f)/τ.
-__device__ __forceinline__ float2 relax(float2 f, float2 feq, float2 it) { return fma2(sub2(feq, f), it, f); }
+// BGK relaxation f + (f^eq - f)/τ; a component with τ = 1 takes f^eq
+// itself, the value the τ = 1 kernels store without reading f.
+__device__ __forceinline__ float2 relax(float2 f, float2 feq, float2 it)
+{
+    const float2 r = fma2(sub2(feq, f), it, f);
+    return make_float2(it.x == 1.f ? feq.x : r.x, it.y == 1.f ? feq.y : r.y);
+}
 
-// One tile (column bx, by, z chunk bz) of one lattice.  TMA: the planes
-// arrive as tensor copies described by *tmap; otherwise each thread loads
-// its node's populations.  Returns false if a copy never completed (the
-// lattice's status word records it).
-template <class S, bool TMA, bool R32>
-__device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__restrict__ fin,
-                                           typename S::T *__restrict__ fout, const float *__restrict__ rho,
-                                           const float *__restrict__ psi, const uint8_t *__restrict__ type, int zc,
-                                           const FusedOfs &ofs, const CUtensorMap *tmap, int bx, int by, int bz,
+// Halo entry h of the (32 + 2) x (TY + 2) ring: top row, bottom row, left
+// column, right column.
+template <int TY>
+__device__ __forceinline__ void halo_entry(int h, int &ex, int &ey)
+{
+    constexpr int HX = TX + 2, HY = TY + 2;
+    if (h < HX) {
+        ex = h;
+        ey = 0;
+    } else if (h < 2 * HX) {
+        ex = h - HX;
+        ey = HY - 1;
+    } else if (h < 2 * HX + TY) {
+        ex = 0;
+        ey = h - 2 * HX + 1;
+    } else {
+        ex = HX - 1;
+        ey = h - 2 * HX - TY + 1;
+    }
+}
+
+// A ring entry a thread looks after: its place in the ring and in a staged
+// box, its wrapped lattice column (x + nx y), and whether the box holds it
+// (otherwise it is read from global memory).
+struct Ent {
+    int ring, st, xy, ex, ey;
+    bool inlat;
+};
+
+constexpr int WAIT_LIMIT = FUSED_WAIT_LIMIT;
+
+// One tile (column bx, by, z chunk bz) of one lattice.  TMA: the boxes
+// arrive as tensor copies described by *tmap; otherwise every entry is read
+// from global memory.  Each wait for a box tries wait_limit times; if one
+// runs out the CTA stops, waits (with the full limit) for its copies in
+// flight, records the timeout in the lattice's status word and returns
+// false.  SELF: ψ of fluid nodes is formed here from the densities of the
+// box; otherwise psi holds ψ of every node (the density kernel's and the
+// shell fill's), and the box holds the tile only.
+template <class S, int TY, bool GEN, bool SELF, bool TMA, bool R32>
+__device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::P *__restrict__ fin,
+                                           typename S::P *__restrict__ fout, const float *__restrict__ psi,
+                                           const uint8_t *__restrict__ type, int zc, const FusedOfs &ofs,
+                                           const CUtensorMap *tmap, int bx, int by, int bz, int wait_limit,
                                            unsigned char *smem)
 {
-    using T = typename S::T;
-    T *stage = reinterpret_cast<T *>(smem + Smem<S>::stage);        // [stage][c*Q+i][tid]
-    float2 *sps = reinterpret_cast<float2 *>(smem + Smem<S>::sps);  // [slot][e]
-    uint8_t *sty = smem + Smem<S>::sty;                             // [slot][e]
-    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + Smem<S>::bar);
-    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    using C = Cfg<S, TY, GEN, SELF>;
+    using P = typename S::P;
+    constexpr int HX = C::HX, HN = C::HN, BX = C::BX, BY = C::BY, NST = C::NST;
+    constexpr size_t PSTR = C::pstride / sizeof(P);  // pairs from one stage to the next
+    const P *stage = reinterpret_cast<const P *>(smem + C::stage);
+    float2 *sps = reinterpret_cast<float2 *>(smem + C::sps);                                // [slot][e]
+    unsigned long long *smask = reinterpret_cast<unsigned long long *>(smem + C::smask);   // [slot][ey]
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(smem + C::bar);
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     const int x0 = bx * TX, y0 = by * TY;
     const int zb = bz * zc, ze = min(zb + zc, L.nz);
-    const int gx = wrapc(x0 + tx, L.nx), gy = wrapc(y0 + ty, L.ny);
-    const bool active = (x0 + tx < L.nx) && (y0 + ty < L.ny);
     const int nxy = L.nx * L.ny;
-    const int ec = (ty + 1) * HX + (tx + 1);
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool active = gx < L.nx && gy < L.ny;
 
-    // halo entry h of this thread: top row, bottom row, left column, right
-    // column of the (TX+2) x (TY+2) tile; threads 2h and 2h+1 take the two
-    // components of entry h
-    const int h = tid >> 1, hc = tid & 1;
-    int he = 0, hn2 = 0;
-    if (h < NHALO) {
-        int hx, hy;
-        if (h < HX) {
-            hx = h;
-            hy = 0;
-        } else if (h < 2 * HX) {
-            hx = h - HX;
-            hy = HY - 1;
-        } else if (h < 2 * HX + TY) {
-            hx = 0;
-            hy = h - 2 * HX + 1;
-        } else {
-            hx = HX - 1;
-            hy = h - 2 * HX - TY + 1;
+    auto make_ent = [&](int ex, int ey) {
+        Ent e;
+        e.ex = ex;
+        e.ey = ey;
+        e.ring = ey * HX + ex;
+        const int lx = x0 - 1 + ex, ly = y0 - 1 + ey;
+        if (SELF) {
+            e.st = ey * BX + ex - 1 + C::PADX;
+            e.inlat = TMA && lx >= 0 && lx < L.nx && ly >= 0 && ly < L.ny;
+        } else {  // only the own entries of active nodes are in the box
+            e.st = (ey - 1) * BX + ex - 1;
+            e.inlat = TMA && ex >= 1 && ex <= TX && ey >= 1 && ey <= TY && lx < L.nx && ly < L.ny;
         }
-        he = hy * HX + hx;
-        hn2 = wrapc(x0 + hx - 1, L.nx) + L.nx * wrapc(y0 + hy - 1, L.ny);
+        e.xy = wrapc(lx, L.nx) + L.nx * wrapc(ly, L.ny);
+        return e;
+    };
+    const Ent own = make_ent(tx + 1, ty + 1);
+    const bool has_halo = tid < C::NHALO;
+    Ent hal{};
+    if (has_halo) {
+        int ex, ey;
+        halo_entry<TY>(tid, ex, ey);
+        hal = make_ent(ex, ey);
     }
-    const int own2 = gx + L.nx * gy;
 
-    // ψ and node type of plane zz (tile + halo) for the ring: the density
-    // kernel's ψ on fluid nodes and the shell fill's on solid nodes share one
-    // array, so the loads of an entry do not wait on its type; walls beyond
-    // the lattice's z walls.  Loaded one plane ahead into registers, stored
-    // into ring slot zz % 4 after the collision of plane zz - 2.
-    struct RingVals {
-        float p0, p1, ph;
-        uint8_t t, th;
+    // iteration k handles ring plane zb - 1 + k: its box arrives, its
+    // entries go into ring slot k & 3, and plane zb - 2 + k (k >= 2) is
+    // collided
+    const int kmax = ze - zb + 2;
+    auto pvalid = [&](int p) { return !L.walls || (p >= 0 && p < L.nz); };
+    auto gz_of = [&](int p) {  // p in [-1, nz]: two wraps when nz = 1
+        int g = p < 0 ? p + L.nz : p;
+        while (g >= L.nz) g -= L.nz;
+        return g;
     };
-    auto ring_load = [&](int zz) {
-        RingVals v{0.f, 0.f, 0.f, WALL, WALL};
-        bool zin = true;
-        int gz = zz;
-        if (L.walls) {
-            zin = zz >= 0 && zz < L.nz;
-        } else {
-            // planes -1 .. nz+1: two wraps when nz = 1
-            gz = zz < 0 ? zz + L.nz : zz;
-            while (gz >= L.nz) gz -= L.nz;
-        }
-        if (zin) {
-            const int n = own2 + nxy * gz;
-            v.t = type[n];
-            v.p0 = psi[n];
-            v.p1 = psi[(size_t)L.N + n];
-            if (h < NHALO) {
-                const int nh = hn2 + nxy * gz;
-                v.th = type[nh];
-                v.ph = psi[(size_t)hc * L.N + nh];
-            }
-        }
-        return v;
-    };
-    auto ring_store = [&](int zz, const RingVals &v) {
-        const int slot = (zz + 4) & 3;
-        float2 *ps = sps + slot * HN;
-        uint8_t *ts = sty + slot * HN;
-        ps[ec] = make_float2(v.p1, v.p0);  // (ψ_b, ψ_r): the partner component first
-        ts[ec] = v.t;
-        if (h < NHALO) {
-            reinterpret_cast<float *>(ps + he)[1 - hc] = v.ph;
-            if (hc == 0) ts[he] = v.th;
-        }
+    // per stage buffer: boxes issued (thread 0) and waited for (every thread)
+    Counts<NST> issued{}, waited{};
+    auto issue = [&](int k, int b) {
+        if (!TMA || tid != 0) return;
+        const int p = zb - 1 + k;
+        if (!pvalid(p)) return;
+        fence_proxy_async();
+        mbar_expect_tx(&bar[b], (unsigned)C::plane);
+        tma_box(const_cast<P *>(stage) + (size_t)b * PSTR, tmap, x0 - C::PADX, y0 - (SELF ? 1 : 0), gz_of(p),
+                &bar[b]);
+        issued.inc(b);
     };
 
-    // Populations of plane zz into stage zz & 1 (after the barrier that
-    // ended the collision that last read that stage).
-    auto fill = [&](int zz) {
-        T *st = stage + (zz & 1) * 2 * Q * NT;
-        if (TMA) {
-            if (tid == 0) {
-                fence_proxy_async();
-                mbar_expect_tx(&bar[zz & 1], (unsigned)Smem<S>::plane);
-                tma_plane(st, tmap, x0, y0, zz, &bar[zz & 1]);
-            }
-        } else if (active) {
-            const int n = own2 + nxy * zz;
-            if (type[n] == FLUID) {
-                const T *src = fin + n;
-#pragma unroll
-                for (int ci = 0; ci < 2 * Q; ci++) st[ci * NT + tid] = __ldg(src + ofs.pop[ci]);
-            }
-        }
+    // node types one plane ahead, and ψ: SELF loads it for solid nodes
+    // only (once their type is known), otherwise for every node along
+    // with the type
+    auto load_type = [&](int k, const Ent &e) -> uint8_t {
+        const int p = zb - 1 + k;
+        if (!pvalid(p)) return WALL;
+        return type[e.xy + (size_t)nxy * gz_of(p)];
+    };
+    auto load_psi = [&](int k, const Ent &e, uint8_t t) -> float2 {
+        const int p = zb - 1 + k;
+        if ((SELF && t == FLUID) || !pvalid(p)) return dup2(0.f);
+        const size_t n = e.xy + (size_t)nxy * gz_of(p);
+        return make_float2(psi[n], psi[(size_t)L.N + n]);
     };
 
-    if (TMA) {
-        if (tid == 0) {
-            mbar_init(&bar[0], 1);
-            mbar_init(&bar[1], 1);
-            fence_barrier_init();
-        }
-        __syncthreads();
-    }
-    fill(zb);
-    ring_store(zb - 1, ring_load(zb - 1));
-    ring_store(zb, ring_load(zb));
-    ring_store(zb + 1, ring_load(zb + 1));
-    const bool xy_inner = gx >= 1 && gx <= L.nx - 2 && gy >= 1 && gy <= L.ny - 2;
-    bool ok = true;
-    for (int z = zb; z < ze; z++) {
-        if (z + 1 < ze) fill(z + 1);
-        // the ring of plane z+2 is needed by the next collision: its loads
-        // are in flight during this one
-        const RingVals next = ring_load(z + 2);
-        bool late = false;
-        if (TMA) late = !mbar_wait(&bar[z & 1], ((z - zb) >> 1) & 1);
-        if (__syncthreads_or(late)) {
-            ok = false;
-            break;
-        }
-        // ring slots of planes z-1, z, z+1
-        const float2 *pl[3] = {sps + ((z + 3) & 3) * HN, sps + (z & 3) * HN, sps + ((z + 1) & 3) * HN};
-        const uint8_t *tl[3] = {sty + ((z + 3) & 3) * HN, sty + (z & 3) * HN, sty + ((z + 1) & 3) * HN};
-        if (active && tl[1][ec] == FLUID) {
-            const int n = own2 + nxy * z;
-            const bool inner = xy_inner && z >= 1 && z <= L.nz - 2;
-            const T *fb = stage + (z & 1) * 2 * Q * NT + tid;
-            // moments from the stored quantities d_i (δf_i in the 16-bit
-            // modes, f_i in FP32): Δρ^c = Σ_i d_i, ρ^c = ρ_ref + Δρ^c, and
-            // j^c = Σ_i c_i d_i (the bases cancel: Σ_i w_i c_i = 0); the
-            // shifted velocity u' = Σ_c j^c/τ_c / Σ_c ρ^c/τ_c
-            // (red, blue) pairs of the stored quantities of direction i
-            auto ld2 = [&](int i) { return make_float2(S::raw(fb[i * NT]), S::raw(fb[(Q + i) * NT])); };
-            float2 a = ld2(0), jj[3] = {dup2(0.f), dup2(0.f), dup2(0.f)};
-#pragma unroll
-            for (int i = 1; i < Q; i += 2) {
-                // one pass over opposite pairs (i, i+1), c_{i+1} = -c_i; the
-                // sum accumulates in index order
-                const float2 va = ld2(i), vb = ld2(i + 1);
-                a = add2(a, va);
-                a = add2(a, vb);
-                const float2 d = sub2(va, vb);
-                if (cx(i)) jj[0] = cx(i) > 0 ? add2(jj[0], d) : sub2(jj[0], d);
-                if (cy(i)) jj[1] = cy(i) > 0 ? add2(jj[1], d) : sub2(jj[1], d);
-                if (cz(i)) jj[2] = cz(i) > 0 ? add2(jj[2], d) : sub2(jj[2], d);
-            }
-            const float2 drho = a, rho_ = add2(make_float2(L.rref[0], L.rref[1]), a);
-            // 16-bit storage: the collision re-reads the stage, since keeping
-            // the converted populations live in registers would spill under
-            // the three-CTA register budget.  FP32 storage runs two CTAs
-            // per SM (shared memory) and keeps them in registers.
-            if constexpr (sizeof(T) == 2) asm volatile("" ::: "memory");
+    // Collision of plane z with ring slots s0, s1, s2 (planes z - 1, z,
+    // z + 1): the own node's moments from mom_of(), with GEN its stored
+    // pairs from stage buffer bst (or global memory) for the relaxation.
+    auto collide_at = [&](int z, int s0, int s1, int s2, int bst, auto mom_of) {
+        const float2 *pl[3] = {sps + s0 * HN, sps + s1 * HN, sps + s2 * HN};
+        const unsigned long long *ml[3] = {smask + s0 * C::HY, smask + s1 * C::HY, smask + s2 * C::HY};
+        const bool solid_own = (ml[1][ty + 1] >> (tx + 1)) & 1ull;
+        const int n = gx + L.nx * gy + nxy * z;
+        if (active && !solid_own) {
+            const Mom mcur = mom_of();
+            const float2 rref2 = make_float2(L.rref[0], L.rref[1]);
+            const float2 drho = mcur.dr, rho_ = add2(rref2, mcur.dr);
             const float den = __fmaf_rn(rho_.y, L.itau[1], __fmul_rn(rho_.x, L.itau[0]));
             const float iden = den > 0.f ? 1.f / den : 0.f;
             float up[3];
 #pragma unroll
-            for (int k = 0; k < 3; k++)
-                up[k] = __fmul_rn(__fmaf_rn(jj[k].y, L.itau[1], __fmul_rn(jj[k].x, L.itau[0])), iden);
-            // s^c = Σ_i c_i ψ^{c'}(x + c_i): the ring holds (ψ_b, ψ_r), the
-            // partner of (red, blue)
+            for (int d = 0; d < 3; d++)
+                up[d] = __fmul_rn(__fmaf_rn(mcur.j[d].y, L.itau[1], __fmul_rn(mcur.j[d].x, L.itau[0])), iden);
+            // s^c = Σ_i c_i ψ^{c'}(x + c_i): the ring holds (ψ_b, ψ_r),
+            // the partner of (red, blue)
             float2 s[3] = {dup2(0.f), dup2(0.f), dup2(0.f)};
-            uint32_t solid = 0;  // bit i: neighbour i is not fluid
 #pragma unroll
             for (int i = 1; i < Q; i++) {
-                const int e = ec + cy(i) * HX + cx(i);
-                const float2 pp = pl[cz(i) + 1][e];
-                const uint8_t tn = tl[cz(i) + 1][e];
-                solid |= (uint32_t)(tn != FLUID) << i;
+                const float2 pp = pl[cz(i) + 1][own.ring + cy(i) * HX + cx(i)];
                 if (cx(i)) s[0] = cx(i) > 0 ? add2(s[0], pp) : sub2(s[0], pp);
                 if (cy(i)) s[1] = cy(i) > 0 ? add2(s[1], pp) : sub2(s[1], pp);
                 if (cz(i)) s[2] = cz(i) > 0 ? add2(s[2], pp) : sub2(s[2], pp);
             }
-            const float2 pcc = pl[1][ec];
+            const float2 pcc = pl[1][own.ring];
             const float2 pc = make_float2(pcc.y, pcc.x);  // own (ψ_r, ψ_b)
-            T *dst = fout + n;
-            // R32: stores address the node's component c from dc[c] with
-            // 32-bit offsets (one wide multiply-add per address)
-            T *const dc[2] = {dst, dst + (size_t)Q * (size_t)L.S};
-            // A warp whose nodes are all off the lattice boundary and have
-            // no solid neighbour pushes every population to its fixed
-            // offset; the others select, per population, between the push
-            // (with the periodic wrap of boundary nodes) and the reflection.
-            const bool clean = __all_sync(__activemask(), inner && solid == 0u);
+            // solid rows around this warp's row (the same for all its
+            // lanes): a warp without any, all of whose nodes are
+            // active and none on a periodic boundary, pushes every
+            // population to its fixed offset
+            unsigned long long mrow = 0ull;
+#pragma unroll
+            for (int dz = 0; dz < 3; dz++)
+#pragma unroll
+                for (int dy = 0; dy < 3; dy++) mrow |= ml[dz][ty + dy];
+            const bool inner_x = x0 > 0 && x0 + TX < L.nx;
+            const bool inner_y = gy > 0 && gy < L.ny - 1;
+            const bool inner_z = L.walls || (z > 0 && z < L.nz - 1);
+            const bool clean = mrow == 0ull && inner_x && inner_y && inner_z;
+            P *dst = fout + n;
             auto collide = [&](auto clean_tag) {
                 constexpr bool CLEAN = decltype(clean_tag)::value;
-                // Push offsets of nodes on the lattice boundary wrap around
-                // the periodic axes: corrections for c = +1 ([0]) and c = -1 ([1]).
+                // bit (cx+1) + 3 (cy+1) + 9 (cz+1): neighbour is solid
+                uint32_t nb27 = 0;
                 int wx[2] = {0, 0}, wy[2] = {0, 0}, wz[2] = {0, 0};
-                if (!CLEAN && !inner) {
+                if (!CLEAN) {
+#pragma unroll
+                    for (int dz = 0; dz < 3; dz++)
+#pragma unroll
+                        for (int dy = 0; dy < 3; dy++) {
+                            const unsigned long long m = ml[dz][ty + dy];
+                            const uint32_t f3 =
+                                __funnelshift_r((uint32_t)m, (uint32_t)(m >> 32), (uint32_t)tx) & 7u;
+                            nb27 |= f3 << (3 * (dy + 3 * dz));
+                        }
+                    // push offsets of nodes on the lattice boundary wrap
+                    // around the periodic axes: corrections for c = +1
+                    // ([0]) and c = -1 ([1])
                     wx[0] = gx == L.nx - 1 ? -L.nx : 0;
                     wx[1] = gx == 0 ? L.nx : 0;
                     wy[0] = gy == L.ny - 1 ? -nxy : 0;
@@ -379,32 +452,40 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
                         wz[1] = z == 0 ? L.N : 0;
                     }
                 }
-                // store of the post-collision population fs of direction i:
-                // pushed to the neighbour, or reflected into slot opp(i) of
-                // this node (walls and particle nodes; the link kernel adds
-                // the moving-boundary term for the latter).  Both slots have
-                // the same weight, hence the same storage offset; the
-                // address is a select, not a branch.
-                auto put = [&](int c, int i, float fs) {
+                // store of the post-collision pair of direction i: pushed
+                // to the neighbour, or reflected into slot opp(i) of this
+                // node (walls and particle nodes; the link kernel adds
+                // the moving-boundary term for the latter).  Both slots
+                // have the same weight, hence the same storage offset;
+                // the address is a select, not a branch.
+                auto put = [&](int i, float2 fs) {
+                    const P v = S::enc2(fs);
                     if (CLEAN) {
                         if constexpr (R32)
-                            S::st_raw(dc[c] + ofs.push32[c * Q + i], fs);
+                            dst[ofs.push32[i]] = v;
                         else
-                            S::st_raw(dst + ofs.push[c * Q + i], fs);
+                            dst[ofs.push[i]] = v;
                     } else {
+                        const int bit = (cx(i) + 1) + 3 * ((cy(i) + 1) + 3 * (cz(i) + 1));
+                        const bool sol = (nb27 >> bit) & 1u;
                         const int corr = (cx(i) > 0 ? wx[0] : (cx(i) < 0 ? wx[1] : 0)) +
                                          (cy(i) > 0 ? wy[0] : (cy(i) < 0 ? wy[1] : 0)) +
                                          (cz(i) > 0 ? wz[0] : (cz(i) < 0 ? wz[1] : 0));
                         if constexpr (R32) {
-                            const unsigned o = ((solid >> i) & 1u) ? ofs.pop32[c * Q + opp(i)]
-                                                                   : ofs.push32[c * Q + i] + (unsigned)corr;
-                            S::st_raw(dc[c] + o, fs);
+                            const unsigned o = sol ? ofs.pop32[opp(i)] : ofs.push32[i] + (unsigned)corr;
+                            dst[o] = v;
                         } else {
-                            const long long o =
-                                ((solid >> i) & 1u) ? ofs.pop[c * Q + opp(i)] : ofs.push[c * Q + i] + corr;
-                            S::st_raw(dst + o, fs);
+                            const long long o = sol ? ofs.pop[opp(i)] : ofs.push[i] + corr;
+                            dst[o] = v;
                         }
                     }
+                };
+                // GEN: the node's stored pairs for the relaxation, from
+                // the box of plane z (or global memory)
+                const P *fb = stage + (size_t)bst * PSTR + own.st;
+                auto ldf = [&](int i) {
+                    if (TMA) return S::raw2(fb[i * BY * BX]);
+                    return S::raw2(fin[pidx(L, i, (long long)n)]);
                 };
                 float2 ue[3], um15;
                 eq_velocity(L, rho_, pc, s, up, ue, um15);
@@ -430,18 +511,19 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
                     float2 even, odd;
                     feq_parts(wgt(i), rho_, drho, i < 7 ? w3r_a : w3r_d, cu, um15, even, odd);
                     seq = add2(seq, mul2(dup2(2.f), even));
-                    const float2 ra = relax(ld2(i), add2(even, odd), it);
-                    const float2 rb = relax(ld2(i + 1), sub2(even, odd), it);
-                    put(0, i, ra.x);
-                    put(1, i, ra.y);
-                    put(0, i + 1, rb.x);
-                    put(1, i + 1, rb.y);
+                    float2 ra = add2(even, odd), rb = sub2(even, odd);
+                    if (GEN) {
+                        ra = relax(ldf(i), ra, it);
+                        rb = relax(ldf(i + 1), rb, it);
+                    }
+                    put(i, ra);
+                    put(i + 1, rb);
                 }
                 // rest population: equilibrium Δρ - Σ_{i>0} f^eq_i in the
                 // stored quantity (exact mass)
-                const float2 r0 = relax(ld2(0), sub2(drho, seq), it);
-                S::st_raw(R32 ? dc[0] : dst + ofs.pop[0], r0.x);
-                S::st_raw(R32 ? dc[1] : dst + ofs.pop[Q], r0.y);
+                float2 r0 = sub2(drho, seq);
+                if (GEN) r0 = relax(ldf(0), r0, it);
+                dst[0] = S::enc2(r0);
             };
             if (clean)
                 collide(std::true_type{});
@@ -452,49 +534,241 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::T *__
             // particle uncovers gets f^eq in all slots), but writing them
             // keeps every sector of the output fully written: a partly
             // written sector costs a DRAM read when it leaves L2.
-            T *d0 = fout + own2 + nxy * z;
+            P *d0 = fout + n;
 #pragma unroll
-            for (int ci = 0; ci < 2 * Q; ci++) d0[ofs.pop[ci]] = S::enc(0.f, 0.f);
+            for (int i = 0; i < Q; i++) d0[ofs.pop[i]] = S::enc2(make_float2(0.f, 0.f));
         }
-        ring_store(z + 2, next);  // slot (z+2) % 4: not one the collision read
+    };
+
+    if (tid == 0) {
+#pragma unroll
+        for (int b = 0; b < NST; b++) mbar_init(&bar[b], 1);
+        fence_barrier_init();
+    }
+    bool ok = true;
+    if constexpr (!SELF) {
+        // Without SELF the ring runs two planes ahead of the collision:
+        // while plane z collides, the entries of plane z + 2 are loaded into
+        // registers; they go into the ring after the collision.  Each warp
+        // puts whole ring rows (its own row, with the side entries taken by
+        // lanes 30 and 31; warps 0 and 1 also the halo rows 0 and TY + 1,
+        // two entries for lanes 0 and 1), so it forms their solid bits with
+        // ballots and one lane writes each row's word: one barrier per plane,
+        // at its end, which also gathers the copy timeouts.  The own node's
+        // moments come from the box of plane z at the collision.
+        const int lane = tx, warp = ty;
+        const bool has_a = warp < 2, has_b = warp < 2 && lane < 2, has_c = lane >= 30;
+        const int hrow = warp == 0 ? 0 : TY + 1;
+        const Ent ha = make_ent(lane, hrow), hb = make_ent(lane + 32, hrow);
+        const Ent hc = make_ent(lane == 30 ? 0 : HX - 1, warp + 1);
+        struct Vals {
+            uint8_t t0, ta, tb, tc;
+            float2 p0, pa, pb, pc;
+        };
+        auto ring_load = [&](int k) {
+            Vals v;
+            v.t0 = load_type(k, own);
+            v.p0 = load_psi(k, own, v.t0);
+            v.ta = has_a ? load_type(k, ha) : WALL;
+            v.pa = has_a ? load_psi(k, ha, v.ta) : dup2(0.f);
+            v.tb = has_b ? load_type(k, hb) : WALL;
+            v.pb = has_b ? load_psi(k, hb, v.tb) : dup2(0.f);
+            v.tc = has_c ? load_type(k, hc) : WALL;
+            v.pc = has_c ? load_psi(k, hc, v.tc) : dup2(0.f);
+            return v;
+        };
+        auto ring_put = [&](int slot, const Vals &v) {
+            float2 *ps = sps + slot * HN;
+            ps[own.ring] = make_float2(v.p0.y, v.p0.x);  // (ψ_b, ψ_r): the partner first
+            if (has_a) ps[ha.ring] = make_float2(v.pa.y, v.pa.x);
+            if (has_b) ps[hb.ring] = make_float2(v.pb.y, v.pb.x);
+            if (has_c) ps[hc.ring] = make_float2(v.pc.y, v.pc.x);
+            const unsigned bo = __ballot_sync(0xffffffffu, v.t0 != FLUID);
+            const unsigned ba = __ballot_sync(0xffffffffu, v.ta != FLUID);
+            const unsigned bb = __ballot_sync(0xffffffffu, has_b && v.tb != FLUID);
+            const unsigned bc = __ballot_sync(0xffffffffu, has_c && v.tc != FLUID);
+            if (lane == 0) {
+                smask[slot * C::HY + warp + 1] = ((unsigned long long)bo << 1) | ((bc >> 30) & 1u) |
+                                                 ((unsigned long long)((bc >> 31) & 1u) << 33);
+                if (has_a)
+                    smask[slot * C::HY + hrow] = (unsigned long long)ba | ((unsigned long long)(bb & 3u) << 32);
+            }
+        };
+        auto issue_z = [&](int z, int b) {
+            if (!TMA || tid != 0) return;
+            fence_proxy_async();
+            mbar_expect_tx(&bar[b], (unsigned)C::plane);
+            tma_box(const_cast<P *>(stage) + (size_t)b * PSTR, tmap, x0, y0, z, &bar[b]);
+            issued.inc(b);
+        };
+        __syncthreads();  // barriers initialised
+        issue_z(zb, 0);
+        // ring planes zb - 1, zb, zb + 1 (index k = plane - zb + 1)
+        for (int k = 0; k < 3; k++) ring_put(k, ring_load(k));
         __syncthreads();
+        for (int j = 0; j < ze - zb; j++) {
+            const int z = zb + j, b = j & 1;
+            if (z + 1 < ze) issue_z(z + 1, b ^ 1);
+            const int kn = j + 3;  // ring index of plane z + 2
+            const bool more = kn < kmax;
+            Vals vn{};
+            if (more) vn = ring_load(kn);
+            bool late = false;
+            if (TMA) {
+                late = !mbar_wait(&bar[b], (unsigned)(waited.get(b) & 1), wait_limit);
+                waited.inc(b);
+            }
+            // a copy that never arrived leaves stale shared data: the
+            // collision then stores garbage (at valid addresses), and the
+            // step is reported as timed out
+            collide_at(z, j & 3, (j + 1) & 3, (j + 2) & 3, b, [&] {
+                const P *sb = stage + (size_t)b * PSTR;
+                if (TMA) return moments([&](int i) { return S::raw2(sb[i * BY * BX + own.st]); });
+                const size_t n = own.xy + (size_t)nxy * z;
+                return moments([&](int i) { return S::raw2(fin[pidx(L, i, (long long)n)]); });
+            });
+            if (more) ring_put(kn & 3, vn);
+            if (__syncthreads_or(late)) {
+                ok = false;
+                break;
+            }
+        }
+    } else {
+        if (tid < C::HY) smask[tid] = 0ull;  // slot 0
+        __syncthreads();
+        issue(0, 0);
+        uint8_t t_own = load_type(0, own), t_hal = has_halo ? load_type(0, hal) : WALL;
+        float2 p_own = load_psi(0, own, t_own), p_hal = has_halo ? load_psi(0, hal, t_hal) : dup2(0.f);
+        Mom mcur{}, mnext{};
+            int b_cur = 0;  // stage buffer of iteration k
+        for (int k = 0; k < kmax; k++) {
+            const int b_next = b_cur + 1 == NST ? 0 : b_cur + 1;
+            const int b_prev = b_cur == 0 ? NST - 1 : b_cur - 1;
+            if (k + 1 < kmax) issue(k + 1, b_next);
+            const int p = zb - 1 + k;
+            const bool pv = pvalid(p);
+            // types (and without SELF ψ) of the next plane: in flight during this iteration
+            uint8_t tn_own = WALL, tn_hal = WALL;
+            float2 pn_own = dup2(0.f), pn_hal = dup2(0.f);
+            if (k + 1 < kmax) {
+                tn_own = load_type(k + 1, own);
+                if (has_halo) tn_hal = load_type(k + 1, hal);
+                if (!SELF) {
+                    pn_own = load_psi(k + 1, own, tn_own);
+                    if (has_halo) pn_hal = load_psi(k + 1, hal, tn_hal);
+                }
+            }
+            bool late = false;
+            if (TMA && pv) {
+                late = !mbar_wait(&bar[b_cur], (unsigned)(waited.get(b_cur) & 1), wait_limit);
+                waited.inc(b_cur);
+            }
+            if (__syncthreads_or(late)) {
+                ok = false;
+                break;
+            }
+            // this plane's entries into ring slot k & 3: ψ (formed here for
+            // fluid nodes with SELF), type, solid bits; the own node's moments
+            {
+                const int slot = k & 3;
+                const P *sb = stage + (size_t)b_cur * PSTR;
+                const size_t gbase = pv ? (size_t)nxy * gz_of(p) : 0;
+                auto entry = [&](const Ent &e, uint8_t t, float2 ps, bool is_own) {
+                    float2 pq = ps;  // (ψ_r, ψ_b)
+                    if (t == FLUID && pv && (SELF || is_own)) {
+                        float2 dr;
+                        if (e.inlat) {
+                            auto ld = [&](int i) { return S::raw2(sb[i * BY * BX + e.st]); };
+                            if (is_own) {
+                                mnext = moments(ld);
+                                dr = mnext.dr;
+                            } else {
+                                dr = density_sum(ld);
+                            }
+                        } else {
+                            const size_t n = e.xy + gbase;
+                            auto ld = [&](int i) { return S::raw2(fin[pidx(L, i, (long long)n)]); };
+                            if (is_own) {
+                                mnext = moments(ld);
+                                dr = mnext.dr;
+                            } else {
+                                dr = density_sum(ld);
+                            }
+                        }
+                        if (SELF) {
+                            const float2 r = add2(make_float2(L.rref[0], L.rref[1]), dr);
+                            pq = make_float2(1.f - expf(-r.x), 1.f - expf(-r.y));
+                        }
+                    }
+                    sps[slot * HN + e.ring] = make_float2(pq.y, pq.x);  // (ψ_b, ψ_r): the partner first
+                    if (t != FLUID) atomicOr(&smask[slot * C::HY + e.ey], 1ull << e.ex);
+                };
+                // without SELF an own entry of an inactive node holds no moments
+                entry(own, t_own, p_own, SELF || active);
+                if (has_halo) entry(hal, t_hal, p_hal, false);
+            }
+            __syncthreads();
+            // collision of plane z = p - 1 with ring planes z - 1, z, z + 1
+            if (k >= 2) collide_at(p - 1, (k - 2) & 3, (k - 1) & 3, k & 3, b_prev, [&] { return mcur; });
+            mcur = mnext;
+            // ring slot (k+1) & 3 was last read by the collision of iteration
+            // k - 1: clear its solid rows for the next iteration
+            if (tid < C::HY) smask[((k + 1) & 3) * C::HY + tid] = 0ull;
+            // SELF: ψ of the next plane's solid entries, now that their types are in
+            t_own = tn_own;
+            t_hal = tn_hal;
+            if (SELF && k + 1 < kmax) {
+                p_own = load_psi(k + 1, own, t_own);
+                if (has_halo) p_hal = load_psi(k + 1, hal, t_hal);
+            } else {
+                p_own = pn_own;
+                p_hal = pn_hal;
+            }
+            b_cur = b_next;
+            __syncthreads();
+        }
     }
     if (TMA) {
-        if (!ok && tid == 0) {
+        if (tid == 0) {
             // let the copies in flight land (bounded) before the memory is reused
-            const int n_issued = ze - zb;
-            for (int st = 0; st < 2; st++) {
-                const int uses = (n_issued - st + 1) / 2;  // planes zb+st, zb+st+2, ...
-                if (uses > 0) mbar_wait(&bar[(zb + st) & 1], (uses - 1) & 1);
-            }
-            atomicOr(L.status, 1u);
+            bool lost = !ok;
+#pragma unroll
+            for (int b = 0; b < NST; b++)
+                for (int u = waited.get(b); u < issued.get(b); u++)
+                    if (!mbar_wait(&bar[b], (unsigned)(u & 1), WAIT_LIMIT)) lost = true;
+            if (lost) atomicOr(L.status, 1u);
         }
         __syncthreads();
-        if (tid == 0) {
-            mbar_inval(&bar[0]);
-            mbar_inval(&bar[1]);
-        }
+        if (tid == 0)
+#pragma unroll
+            for (int b = 0; b < NST; b++) mbar_inval(&bar[b]);
     }
     return ok;
 }
 
-template <class S, bool TMA, bool R32>
-__global__ void __launch_bounds__(NT, Smem<S>::CTAS) k_fused(Lat L, const typename S::T *__restrict__ fin,
-                                              typename S::T *__restrict__ fout, const float *__restrict__ rho,
-                                              const float *__restrict__ psi,
-                                              const uint8_t *__restrict__ type, int zc, FusedOfs ofs,
-                                              const __grid_constant__ CUtensorMap tmap)
+template <class S, int TY, bool GEN, bool SELF, bool TMA, bool R32>
+__global__ void __launch_bounds__(TX *TY, (Cfg<S, TY, GEN, SELF>::CTAS))
+    k_fused(Lat L, const typename S::P *__restrict__ fin, typename S::P *__restrict__ fout,
+            const float *__restrict__ psi, const uint8_t *__restrict__ type, int zc, FusedOfs ofs,
+            const __grid_constant__ CUtensorMap tmap, int wait_limit)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    fused_tile<S, TMA, R32>(L, fin, fout, rho, psi, type, zc, ofs, &tmap, blockIdx.x, blockIdx.y, blockIdx.z,
-                            align128(smem_raw));
+    fused_tile<S, TY, GEN, SELF, TMA, R32>(L, fin, fout, psi, type, zc, ofs, &tmap, blockIdx.x, blockIdx.y,
+                                           blockIdx.z, wait_limit, align128(smem_raw));
 }
 
 // Persistent multi-lattice variant: CTAs take tiles of all boxes of a batch
 // from one queue (largest boxes first in the queue order set by the host).
+// It runs the any-τ configuration with ψ from memory (the batch runs the
+// density kernel), which stores exactly what the other configurations
+// store: τ = 1 takes f^eq in the relaxation, and ψ from memory has the
+// bits of ψ formed in the kernel.
+constexpr int BATCH_TY = FUSED_TY_BATCH;
+
 template <class S>
-__global__ void __launch_bounds__(NT, Smem<S>::CTAS) k_fused_batch(BatchIndex B, int total)
+__global__ void __launch_bounds__(TX *BATCH_TY, (Cfg<S, BATCH_TY, true, false>::CTAS)) k_fused_batch(BatchIndex B, int total)
 {
+    constexpr int NT = TX * BATCH_TY;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *smem = align128(smem_raw);
     __shared__ int s_tile, s_box;
@@ -518,13 +792,14 @@ __global__ void __launch_bounds__(NT, Smem<S>::CTAS) k_fused_batch(BatchIndex B,
         const int cur = B.par[2 * s_box];
         // the tensor map stays in global memory (a TMA operand cannot be in shared memory)
         const CUtensorMap *tm = &B.box[s_box].tmap[cur];
+        using P = typename S::P;
         bool ok;
         if (sb.tma)
-            ok = fused_tile<S, true, false>(sb.L, (const typename S::T *)sb.f[cur], (typename S::T *)sb.f[1 - cur], sb.rho,
-                                     sb.psi, sb.type, sb.zc, sb.ofs, tm, bx, by, bz, smem);
+            ok = fused_tile<S, BATCH_TY, true, false, true, false>(sb.L, (const P *)sb.f[cur], (P *)sb.f[1 - cur], sb.psi,
+                                                            sb.type, sb.zc, sb.ofs, tm, bx, by, bz, WAIT_LIMIT, smem);
         else
-            ok = fused_tile<S, false, false>(sb.L, (const typename S::T *)sb.f[cur], (typename S::T *)sb.f[1 - cur], sb.rho,
-                                      sb.psi, sb.type, sb.zc, sb.ofs, tm, bx, by, bz, smem);
+            ok = fused_tile<S, BATCH_TY, true, false, false, false>(sb.L, (const P *)sb.f[cur], (P *)sb.f[1 - cur], sb.psi,
+                                                             sb.type, sb.zc, sb.ofs, tm, bx, by, bz, WAIT_LIMIT, smem);
         if (!ok) break;
     }
 }
@@ -540,18 +815,20 @@ __global__ void __launch_bounds__(NT, Smem<S>::CTAS) k_fused_batch(BatchIndex B,
         }                                                             \
     } while (0)
 
-int fused_zchunk(const Lat &L)
+int fused_zchunk(const Lat &L, int ty)
 {
     // About 16 waves of CTAs (three per SM on 152 SMs), so the last wave's
     // idle SMs cost little, each chunk long enough (>= 16 planes where the
-    // lattice allows) that its extra halo planes cost little.
-    long long cols = (long long)((L.nx + TX - 1) / TX) * ((L.ny + TY - 1) / TY);
+    // lattice allows) that its two extra halo planes cost little.
+    long long cols = (long long)((L.nx + TX - 1) / TX) * ((L.ny + ty - 1) / ty);
     int zc = L.nz;
     while (zc > 16 && cols * ((L.nz + zc - 1) / zc) < 48 * 152) zc = (zc + 1) / 2;
     return zc;
 }
 
-bool fused_plane_map(CUtensorMap *map, void *f, const Lat &L, int storage)
+bool fused_tau1(const Lat &L) { return L.itau[0] == 1.f && L.itau[1] == 1.f; }
+
+bool fused_plane_map(CUtensorMap *map, void *f, const Lat &L, int storage, int ty, bool self)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     static bool looked = false;
@@ -564,13 +841,15 @@ bool fused_plane_map(CUtensorMap *map, void *f, const Lat &L, int storage)
             q == cudaDriverEntryPointSuccess)
             encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    const size_t es = storage == LBE_STORE_F32 ? 4 : 2;
+    // one element = the (red, blue) pair of a population
+    const size_t es = storage == LBE_STORE_F32 ? 8 : 4;
+    const unsigned padx = self ? (unsigned)(16 / es) : 0u;
     if (!encode || ((size_t)L.nx * es) % 16 != 0) return false;
-    const cuuint64_t dims[4] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny, (cuuint64_t)L.nz, (cuuint64_t)(2 * Q)};
+    const cuuint64_t dims[4] = {(cuuint64_t)L.nx, (cuuint64_t)L.ny, (cuuint64_t)L.nz, (cuuint64_t)Q};
     const cuuint64_t strides[3] = {(cuuint64_t)L.nx * es, (cuuint64_t)L.nx * L.ny * es, (cuuint64_t)L.S * es};
-    const cuuint32_t box[4] = {TX, TY, 1, 2 * Q};
+    const cuuint32_t box[4] = {(cuuint32_t)(TX + 2 * padx), (cuuint32_t)(self ? ty + 2 : ty), 1, Q};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUtensorMapDataType dt = es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    const CUtensorMapDataType dt = es == 8 ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_UINT32;
     return encode(map, dt, 4, f, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -579,71 +858,101 @@ bool fused_plane_map(CUtensorMap *map, void *f, const Lat &L, int storage)
 FusedOfs fused_offsets(const Lat &L)
 {
     FusedOfs ofs;
-    for (int c = 0; c < 2; c++)
-        for (int i = 0; i < Q; i++) {
-            const long long o = (long long)(c * Q + i) * L.S, r = (long long)i * L.S;
-            const long long d = cx(i) + (long long)cy(i) * L.nx + (long long)cz(i) * L.nx * L.ny;
-            ofs.pop[c * Q + i] = o;
-            ofs.push[c * Q + i] = o + d;
-            // slot 0 never pushes; the others lie at least S - nx*ny - nx - 1 > 0
-            // above the component base
-            ofs.pop32[c * Q + i] = (unsigned)r;
-            ofs.push32[c * Q + i] = (unsigned)(r + d);
-        }
+    for (int i = 0; i < Q; i++) {
+        const long long o = (long long)i * L.S;
+        const long long d = cx(i) + (long long)cy(i) * L.nx + (long long)cz(i) * L.nx * L.ny;
+        ofs.pop[i] = o;
+        ofs.push[i] = o + d;
+        // slot 0 never pushes; the others lie at least S - nx*ny - nx - 1 > 0
+        // above the array base
+        ofs.pop32[i] = (unsigned)o;
+        ofs.push32[i] = (unsigned)(o + d);
+    }
     return ofs;
 }
 
-// The 32-bit offsets hold every store of a component: the highest is slot
-// 18 of the pushed neighbour plus a periodic wrap of N.
+// The 32-bit offsets hold every store: the highest is slot 18 of the pushed
+// neighbour plus a periodic wrap of N.
 bool fused_rel32(const Lat &L)
 {
     return !L.wide && (long long)Q * L.S + 2LL * L.N + (long long)L.nx * L.ny + L.nx + 1 < (1LL << 32);
 }
 
-template <class S>
-static void launch_fused_t(const Lat &L, const void *fin, void *fout, const float *rho, const float *psi,
-                           const uint8_t *type, const CUtensorMap *tmap, cudaStream_t s, int zc_override)
+template <class S, int TY, bool GEN, bool SELF, bool TMA, bool R32>
+static void launch_cfg(const Lat &L, const void *fin, void *fout, const float *psi, const uint8_t *type,
+                       const CUtensorMap &tm, int zc, int wait_limit, cudaStream_t s)
 {
+    using C = Cfg<S, TY, GEN, SELF>;
+    using P = typename S::P;
+    auto kern = k_fused<S, TY, GEN, SELF, TMA, R32>;
     static bool configured = false;  // the attribute is per function and process
     if (!configured) {
-        const int b = (int)Smem<S>::bytes;
-        cudaFuncSetAttribute(k_fused<S, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-        cudaFuncSetAttribute(k_fused<S, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-        cudaFuncSetAttribute(k_fused<S, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-        cudaFuncSetAttribute(k_fused<S, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::bytes);
         configured = true;
     }
-    const int zc = zc_override > 0 ? zc_override : fused_zchunk(L);
     dim3 grid((L.nx + TX - 1) / TX, (L.ny + TY - 1) / TY, (L.nz + zc - 1) / zc);
-    FusedOfs ofs = fused_offsets(L);
-    using T = typename S::T;
-    const CUtensorMap none{};
-    const CUtensorMap &tm = tmap ? *tmap : none;
-    const bool r32 = fused_rel32(L);
-    auto go = [&](auto kernel) {
-        kernel<<<grid, NT, Smem<S>::bytes, s>>>(L, (const T *)fin, (T *)fout, rho, psi, type, zc, ofs, tm);
-    };
-    if (tmap)
-        r32 ? go(k_fused<S, true, true>) : go(k_fused<S, true, false>);
-    else
-        r32 ? go(k_fused<S, false, true>) : go(k_fused<S, false, false>);
+    kern<<<grid, C::NT, C::bytes, s>>>(L, (const P *)fin, (P *)fout, psi, type, zc, fused_offsets(L), tm, wait_limit);
 }
 
-void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *rho, const float *psi,
-                  const uint8_t *type, const CUtensorMap *tmap, cudaStream_t s, int zc_override)
+// Configurations built, each with ψ formed in the kernel (SELF) or from
+// memory: τ = 1 with 32-bit offsets at 4 or 8 rows per tile (TMA) or 8
+// (loads); any τ with 32- or 64-bit offsets at 8 rows (also taken by τ = 1
+// lattices that need 64-bit offsets: same results).
+template <class S, bool SELF>
+static void launch_fused_t(const Lat &L, const void *fin, void *fout, const float *psi, const uint8_t *type,
+                           const CUtensorMap *tmap, cudaStream_t s, int zc, int ty, int wait_limit)
 {
-    LBE_DISPATCH(storage, (launch_fused_t<S>(L, fin, fout, rho, psi, type, tmap, s, zc_override)));
+    const CUtensorMap none{};
+    const CUtensorMap &tm = tmap ? *tmap : none;
+    const bool r32 = fused_rel32(L), tau1 = fused_tau1(L) && r32;
+    if (tau1) {
+        if (tmap && ty == 4)
+            launch_cfg<S, 4, false, SELF, true, true>(L, fin, fout, psi, type, tm, zc, wait_limit, s);
+        else if (tmap)
+            launch_cfg<S, 8, false, SELF, true, true>(L, fin, fout, psi, type, tm, zc, wait_limit, s);
+        else
+            launch_cfg<S, 8, false, SELF, false, true>(L, fin, fout, psi, type, tm, zc, wait_limit, s);
+    } else if (r32) {
+        if (tmap)
+            launch_cfg<S, 8, true, SELF, true, true>(L, fin, fout, psi, type, tm, zc, wait_limit, s);
+        else
+            launch_cfg<S, 8, true, SELF, false, true>(L, fin, fout, psi, type, tm, zc, wait_limit, s);
+    } else {
+        if (tmap)
+            launch_cfg<S, 8, true, SELF, true, false>(L, fin, fout, psi, type, tm, zc, wait_limit, s);
+        else
+            launch_cfg<S, 8, true, SELF, false, false>(L, fin, fout, psi, type, tm, zc, wait_limit, s);
+    }
+}
+
+int fused_rows(const Lat &L, int ty_request, bool tma)
+{
+    // only the τ = 1 configurations with TMA come in two heights
+    return (ty_request == 4 && tma && fused_tau1(L) && fused_rel32(L)) ? 4 : 8;
+}
+
+void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *psi, const uint8_t *type,
+                  const CUtensorMap *tmap, cudaStream_t s, int zc, int ty, int wait_limit, bool self)
+{
+    const int rows = fused_rows(L, ty, tmap != nullptr);
+    if (zc <= 0) zc = fused_zchunk(L, rows);
+    if (zc > L.nz) zc = L.nz;
+    if (self)
+        LBE_DISPATCH(storage, (launch_fused_t<S, true>(L, fin, fout, psi, type, tmap, s, zc, rows, wait_limit)));
+    else
+        LBE_DISPATCH(storage, (launch_fused_t<S, false>(L, fin, fout, psi, type, tmap, s, zc, rows, wait_limit)));
 }
 
 template <class S>
 static void launch_fused_batch_t(const BatchIndex &B, int total, int ctas, cudaStream_t s)
 {
+    using C = Cfg<S, BATCH_TY, true, false>;
     static bool configured = false;
     if (!configured) {
-        cudaFuncSetAttribute(k_fused_batch<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem<S>::bytes);
+        cudaFuncSetAttribute(k_fused_batch<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::bytes);
         configured = true;
     }
-    k_fused_batch<S><<<ctas, NT, Smem<S>::bytes, s>>>(B, total);
+    k_fused_batch<S><<<ctas, C::NT, C::bytes, s>>>(B, total);
 }
 
 void launch_fused_batch(int storage, const BatchIndex &B, int total_tiles, int ctas, cudaStream_t s)
@@ -654,7 +963,8 @@ void launch_fused_batch(int storage, const BatchIndex &B, int total_tiles, int c
 int fused_batch_ctas_per_sm(int storage)
 {
     int n = 0;
-    LBE_DISPATCH(storage, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused_batch<S>, NT, Smem<S>::bytes)));
+    LBE_DISPATCH(storage, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused_batch<S>, TX * BATCH_TY,
+                                                                         Cfg<S, BATCH_TY, true, false>::bytes)));
     return n > 0 ? n : 1;
 }
 

@@ -19,7 +19,9 @@ struct lbe_ctx {
     Pair pair{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    CUtensorMap tmap[2];   // the fused kernel's plane copies of f[0], f[1]
+    // the fused kernel's box copies of f[0], f[1]:
+    // [ψ from memory, ψ formed in the kernel][8-row, 4-row tiles][buffer]
+    CUtensorMap tmap[2][2][2];
     bool tma = false;
     size_t esize = 4;
     void *f[2] = {nullptr, nullptr};
@@ -42,6 +44,8 @@ struct lbe_ctx {
     // graphs keyed by (cur, ocur)
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
     int zc_tuned = 0;  // fused-kernel z chunk chosen by lbe_autotune (0: heuristic)
+    int ty_tuned = 8;  // fused-kernel tile rows chosen by lbe_autotune
+    int wait_limit = FUSED_WAIT_LIMIT;  // tries of each bounded wait for a box copy
     // profiling
     bool profiling = false;
     std::vector<cudaEvent_t> ev;
@@ -165,6 +169,20 @@ __global__ void k_set_types(Lat L, uint8_t *type)
     type[n] = (L.walls && (z == 0 || z == L.nz - 1)) ? WALL : FLUID;
 }
 
+// The fused kernel forms ψ of the fluid nodes itself when no particle needs
+// the densities from memory (a lattice without particles runs no density
+// kernel); with particles, the density kernel feeds the shell fill and the
+// fused kernel reads ψ.
+bool fused_self(const lbe_ctx *c) { return c->np == 0; }
+
+// Tensor map of buffer `buf` for the fused kernel's mode and tile height
+// (null without TMA).
+const CUtensorMap *fused_map(const lbe_ctx *c, int buf, int ty)
+{
+    if (!c->tma) return nullptr;
+    return &c->tmap[fused_self(c) ? 1 : 0][fused_rows(c->L, ty, true) == 4 ? 1 : 0][buf];
+}
+
 // Enqueue one time step (no host synchronisation).
 void enqueue_step(lbe_ctx *c)
 {
@@ -176,20 +194,18 @@ void enqueue_step(lbe_ctx *c)
     const bool links = c->np > 0 && !two_pass;
     if (two_pass) {
         launch_moments(st, L, fin, c->type, c->rho, c->psi, s);
-    } else {
-        if (links) cudaMemsetAsync(c->ll.count, 0, sizeof(int), s);
-        launch_rho(st, L, fin, c->type, c->rho, c->psi, s);
-    }
-    if (two_pass) {
         launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, LinkList{nullptr, nullptr, 0}, s);
     } else {
+        if (links) cudaMemsetAsync(c->ll.count, 0, sizeof(int), s);
         // the solid nodes a fluid node can see: the particles' own nodes and
-        // the wall planes (none for a periodic lattice without particles)
+        // the wall planes (none for a periodic lattice without particles);
+        // without particles the fused kernel forms the densities itself
         if (c->np > 0) {
             c->P.n = c->np;
+            launch_rho(st, L, fin, c->type, c->rho, c->psi, s);
             launch_shell_particles(L, c->P, c->rho, c->psi, c->type, c->owner[c->ocur], c->ll, s);
         }
-        launch_shell_walls(L, c->rho, c->psi, c->type, s);
+        launch_shell_walls(st, L, fin, c->psi, c->type, s);
     }
     if (c->profiling) {
         if (c->ev_used + 2 > c->ev.size()) {
@@ -204,7 +220,8 @@ void enqueue_step(lbe_ctx *c)
     if (two_pass)
         launch_collide_stream(st, L, fin, fout, c->psi, c->type, s);
     else
-        launch_fused(st, L, fin, fout, c->rho, c->psi, c->type, c->tma ? &c->tmap[c->cur] : nullptr, s, c->zc_tuned);
+        launch_fused(st, L, fin, fout, c->psi, c->type, fused_map(c, c->cur, c->ty_tuned), s, c->zc_tuned,
+                     c->ty_tuned, c->wait_limit, fused_self(c));
     if (c->profiling) {
         cudaEventRecord(c->ev[c->ev_used + 1], s);
         c->ev_used += 2;
@@ -385,7 +402,11 @@ lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_c
     if ((e = dalloc(c, &c->mass_out, 2 * sizeof(double))) != cudaSuccess) return bail(e, "cudaMalloc(mass_out)");
     if ((e = dalloc(c, &c->L.status, sizeof(unsigned))) != cudaSuccess) return bail(e, "cudaMalloc(status)");
     cudaMemsetAsync(c->L.status, 0, sizeof(unsigned), c->stream);
-    c->tma = fused_plane_map(&c->tmap[0], c->f[0], L, d->storage) && fused_plane_map(&c->tmap[1], c->f[1], L, d->storage);
+    c->tma = true;
+    for (int m = 0; m < 2; m++)
+        for (int t = 0; t < 2; t++)
+            for (int b = 0; b < 2; b++)
+                c->tma = c->tma && fused_plane_map(&c->tmap[m][t][b], c->f[b], L, d->storage, t == 0 ? 8 : 4, m == 1);
 #ifdef LBE_CHECK
     if ((e = cudaMalloc((void **)&c->L.err, sizeof(unsigned long long))) != cudaSuccess) return bail(e, "cudaMalloc(err)");
     cudaMemset(c->L.err, 0, sizeof(unsigned long long));
@@ -690,13 +711,14 @@ int32_t lbe_kernels_per_step(const lbe_ctx *c)
 {
     if (!c) return 0;
     const bool two_pass = (c->d.flags & LBE_FLAG_TWO_PASS) != 0;
-    // densities, fused fluid (or collide + stream), shell fill: one sweep
-    // (two-pass), else per particle and over the wall planes
-    int k = 2;
+    // two-pass: densities, shell sweep, collide + stream; fused: the fused
+    // kernel, with particles the densities and the shell fill per
+    // particle, with walls the shell fill of the wall planes
+    int k = 0;
     if (two_pass)
-        k += 1;
+        k = 3;
     else
-        k += (c->np > 0 ? 1 : 0) + (c->d.walls_z ? 1 : 0);
+        k = 1 + (c->np > 0 ? 2 : 0) + (c->d.walls_z ? 1 : 0);
     if (c->np > 0) {
         k += 6;  // links, pair cells (count, prefix, fill), pairs, integrate
         if (c->d.particle_mode != LBE_PARTICLES_STATIC) k += 4;  // geometry, claim, transition, reset
@@ -748,40 +770,48 @@ lbe_status lbe_autotune(lbe_ctx *c, int32_t *chosen_zc)
         if (chosen_zc) *chosen_zc = 0;
         return LBE_OK;
     }
-    // Candidates for the z chunk of the fused kernel.  Each runs from the
-    // current populations into the spare buffer, which the next step
-    // overwrites anyway, so the state is not changed.
+    // Candidates: tile heights (8, and 4 where built) times z chunks.
+    // Each runs from the current populations into the spare buffer, which
+    // the next step overwrites anyway, so the state is not changed.
     const Lat &L = c->L;
-    std::vector<int> cand;
-    for (int zc = 4; zc < L.nz; zc *= 2) cand.push_back(zc);
-    cand.push_back(L.nz);
+    std::vector<int> zcs;
+    for (int zc = 4; zc < L.nz; zc *= 2) zcs.push_back(zc);
+    zcs.push_back(L.nz);
+    std::vector<int> tys = {8};
+    if (fused_rows(L, 4, c->tma) == 4) tys.push_back(4);
     cudaEvent_t e0, e1;
     CK(c, cudaEventCreate(&e0));
     CK(c, cudaEventCreate(&e1));
     void *fin = c->f[c->cur], *fout = c->f[1 - c->cur];
+    // ψ of the solid nodes, as the step's shell fill gives them
     launch_rho(c->d.storage, L, fin, c->type, c->rho, c->psi, c->stream);
     launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, LinkList{nullptr, nullptr, 0}, c->stream);
     float best = 1e30f;
-    int best_zc = fused_zchunk(L);
-    for (int zc : cand) {
-        launch_fused(c->d.storage, L, fin, fout, c->rho, c->psi, c->type, c->tma ? &c->tmap[c->cur] : nullptr,
-                     c->stream, zc);  // warm-up
-        cudaEventRecord(e0, c->stream);
-        for (int r = 0; r < 3; r++)
-            launch_fused(c->d.storage, L, fin, fout, c->rho, c->psi, c->type, c->tma ? &c->tmap[c->cur] : nullptr,
-                         c->stream, zc);
-        cudaEventRecord(e1, c->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
-            best = ms;
-            best_zc = zc;
+    int best_zc = 0, best_ty = 8;
+    for (int ty : tys)
+        for (int zc : zcs) {
+            const CUtensorMap *tm = fused_map(c, c->cur, ty);
+            const bool self = fused_self(c);
+            launch_fused(c->d.storage, L, fin, fout, c->psi, c->type, tm, c->stream, zc, ty, FUSED_WAIT_LIMIT,
+                         self);  // warm-up
+            cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < 3; r++)
+                launch_fused(c->d.storage, L, fin, fout, c->psi, c->type, tm, c->stream, zc, ty, FUSED_WAIT_LIMIT,
+                             self);
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_zc = zc;
+                best_ty = ty;
+            }
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->zc_tuned = best_zc;
+    c->ty_tuned = best_ty;
     drop_graphs(c);
     if (chosen_zc) *chosen_zc = best_zc;
     return sync(c, "autotune");
@@ -794,6 +824,42 @@ lbe_status lbe_set_zchunk(lbe_ctx *c, int32_t zc)
     lbe_status st = sync(c, "set_zchunk");  // no captured step in flight when its graph goes
     if (st != LBE_OK) return st;
     c->zc_tuned = zc < c->L.nz ? zc : c->L.nz;
+    drop_graphs(c);
+    return LBE_OK;
+}
+
+lbe_status lbe_set_tile(lbe_ctx *c, int32_t rows, int32_t zc)
+{
+    if (!c || (rows != 4 && rows != 8) || zc < 0) return LBE_EINVAL;
+    cudaSetDevice(c->device);
+    lbe_status st = sync(c, "set_tile");
+    if (st != LBE_OK) return st;
+    c->ty_tuned = rows;
+    c->zc_tuned = zc < c->L.nz ? zc : c->L.nz;
+    drop_graphs(c);
+    return LBE_OK;
+}
+
+lbe_status lbe_get_tile(const lbe_ctx *c, int32_t *rows, int32_t *zc)
+{
+    if (!c || !rows || !zc) return LBE_EINVAL;
+    if (c->d.flags & LBE_FLAG_TWO_PASS) {
+        *rows = 0;
+        *zc = 0;
+        return LBE_OK;
+    }
+    *rows = fused_rows(c->L, c->ty_tuned, c->tma);
+    *zc = c->zc_tuned > 0 ? c->zc_tuned : fused_zchunk(c->L, *rows);
+    return LBE_OK;
+}
+
+lbe_status lbe_set_wait_limit(lbe_ctx *c, int32_t tries)
+{
+    if (!c || tries < 0) return LBE_EINVAL;
+    cudaSetDevice(c->device);
+    lbe_status st = sync(c, "set_wait_limit");
+    if (st != LBE_OK) return st;
+    c->wait_limit = tries > 0 ? tries : FUSED_WAIT_LIMIT;
     drop_graphs(c);
     return LBE_OK;
 }
@@ -914,9 +980,9 @@ lbe_status lbe_batch_create(lbe_ctx *const *members, int32_t n, lbe_batch **out)
         d.L = c->L;
         d.ofs = fused_offsets(c->L);
         d.tma = c->tma ? 1 : 0;
-        if (c->tma) {
-            d.tmap[0] = c->tmap[0];
-            d.tmap[1] = c->tmap[1];
+        if (c->tma) {  // the batched kernel's tiles have FUSED_TY_BATCH = 8 rows
+            d.tmap[0] = c->tmap[0][0][0];  // ψ from memory: the batch runs the density kernel
+            d.tmap[1] = c->tmap[0][0][1];
         }
         d.f[0] = c->f[0];
         d.f[1] = c->f[1];
@@ -930,9 +996,9 @@ lbe_status lbe_batch_create(lbe_ctx *const *members, int32_t n, lbe_batch **out)
         d.pair = c->pair;
         d.mode = c->d.particle_mode;
         d.links = c->np > 0 ? c->ll : LinkList{nullptr, nullptr, 0};
-        d.zc = c->zc_tuned > 0 ? c->zc_tuned : fused_zchunk(c->L);
+        d.zc = c->zc_tuned > 0 ? c->zc_tuned : fused_zchunk(c->L, FUSED_TY_BATCH);
         d.ntx = (c->L.nx + FUSED_TX - 1) / FUSED_TX;
-        d.nty = (c->L.ny + FUSED_TY - 1) / FUSED_TY;
+        d.nty = (c->L.ny + FUSED_TY_BATCH - 1) / FUSED_TY_BATCH;
         d.nzc = (c->L.nz + d.zc - 1) / d.zc;
         tile0[k + 1] = tile0[k] + d.ntx * d.nty * d.nzc;
         node0[k + 1] = node0[k] + c->L.N;

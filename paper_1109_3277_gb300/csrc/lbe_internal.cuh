@@ -39,64 +39,44 @@ __host__ __device__ constexpr double wgtd(int i) { return i == 0 ? 1.0 / 3.0 : (
 
 // Population storage.  FP32 stores f itself; the 16-bit modes store
 // δf = f - w_i ρ_ref^c (the offset from the rest equilibrium at ρ_ref).
-// raw/st_raw read and write the stored quantity (δf, or f for FP32) in
-// FP32; ld/ldc/st/cvt/enc convert to and from f with the slot's base.
+// The two components of one direction at one node sit side by side: the
+// population array is P[19][S] with P = (red, blue) of the storage type, so
+// element (c, i, n) lies at 2 (i S + n) + c in units of T.  One 32-bit
+// (16-bit modes) or 64-bit (FP32) access moves both components.
+// raw2/enc2 convert a pair of stored quantities (δf, or f for FP32) to and
+// from FP32; ld2f/st2f add and subtract the slot's base (w_i ρ_ref^c, 0 in
+// FP32); raw/enc convert one scalar element.
 struct StF32 {
     using T = float;
+    using P = float2;
     static __device__ __forceinline__ float raw(T v) { return v; }
-    static __device__ __forceinline__ void st_raw(T *p, float v) { *p = v; }
-    static __device__ __forceinline__ float ld(const T *p, float) { return __ldg(p); }
-    static __device__ __forceinline__ float ldc(const T *p, float) { return *p; }
-    static __device__ __forceinline__ void st(T *p, float v, float) { *p = v; }
-    static __device__ __forceinline__ float cvt(T v, float) { return v; }
-    static __device__ __forceinline__ T enc(float v, float) { return v; }
-    // two consecutive elements (p 8-byte aligned)
-    static __device__ __forceinline__ void ld2(const T *p, float, float &x, float &y)
-    {
-        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
-        x = v.x;
-        y = v.y;
-    }
+    static __device__ __forceinline__ T enc(float v) { return v; }
+    static __device__ __forceinline__ float2 raw2(P v) { return v; }
+    static __device__ __forceinline__ P enc2(float2 v) { return v; }
 };
 struct StF16 {
     using T = __half;
+    using P = __half2;
     static __device__ __forceinline__ float raw(T v) { return __half2float(v); }
-    static __device__ __forceinline__ void st_raw(T *p, float v) { *p = __float2half_rn(v); }
-    static __device__ __forceinline__ float ld(const T *p, float b) { return b + __half2float(__ldg(p)); }
-    static __device__ __forceinline__ float ldc(const T *p, float b) { return b + __half2float(*p); }
-    static __device__ __forceinline__ void st(T *p, float v, float b) { *p = __float2half_rn(v - b); }
-    static __device__ __forceinline__ float cvt(T v, float b) { return b + __half2float(v); }
-    static __device__ __forceinline__ T enc(float v, float b) { return __float2half_rn(v - b); }
-    static __device__ __forceinline__ void ld2(const T *p, float b, float &x, float &y)
-    {
-        const __half2 v = __ldg(reinterpret_cast<const __half2 *>(p));
-        x = b + __low2float(v);
-        y = b + __high2float(v);
-    }
+    static __device__ __forceinline__ T enc(float v) { return __float2half_rn(v); }
+    static __device__ __forceinline__ float2 raw2(P v) { return __half22float2(v); }
+    static __device__ __forceinline__ P enc2(float2 v) { return __floats2half2_rn(v.x, v.y); }
 };
 struct StBF16 {
     using T = __nv_bfloat16;
+    using P = __nv_bfloat162;
     static __device__ __forceinline__ float raw(T v) { return __bfloat162float(v); }
-    static __device__ __forceinline__ void st_raw(T *p, float v) { *p = __float2bfloat16_rn(v); }
-    static __device__ __forceinline__ float ld(const T *p, float b) { return b + __bfloat162float(__ldg(p)); }
-    static __device__ __forceinline__ float ldc(const T *p, float b) { return b + __bfloat162float(*p); }
-    static __device__ __forceinline__ void st(T *p, float v, float b) { *p = __float2bfloat16_rn(v - b); }
-    static __device__ __forceinline__ float cvt(T v, float b) { return b + __bfloat162float(v); }
-    static __device__ __forceinline__ T enc(float v, float b) { return __float2bfloat16_rn(v - b); }
-    static __device__ __forceinline__ void ld2(const T *p, float b, float &x, float &y)
-    {
-        const __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162 *>(p));
-        x = b + __low2float(v);
-        y = b + __high2float(v);
-    }
+    static __device__ __forceinline__ T enc(float v) { return __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ float2 raw2(P v) { return __bfloat1622float2(v); }
+    static __device__ __forceinline__ P enc2(float2 v) { return __floats2bfloat162_rn(v.x, v.y); }
 };
 
 // Lattice parameters passed by value to every kernel.
 struct Lat {
     int nx, ny, nz, walls;
     int N;                 // nodes (< 2^31)
-    long long S;           // elements per population array (>= N, padded so the
-                           // 38 arrays are not a power of two apart)
+    long long S;           // pairs per direction array (>= N, padded so the 19
+                           // arrays are not a power of two apart)
     float tau[2], itau[2];
     float g;
     float body[3];
@@ -108,6 +88,45 @@ struct Lat {
     unsigned *status;              // bit 0: a TMA copy of the fused kernel never completed
     unsigned long long *err;       // bounds-check record (checked builds only)
 };
+
+// Pair index of direction i at node n (units of the storage's pair type).
+__host__ __device__ __forceinline__ size_t pidx(const Lat &L, int i, long long n)
+{
+    return (size_t)i * (size_t)L.S + (size_t)n;
+}
+
+// Base (w_i ρ_ref^red, w_i ρ_ref^blue) of direction i: f = stored + base.
+__device__ __forceinline__ float2 base2(const Lat &L, int i) { return make_float2(L.base[0][i], L.base[1][i]); }
+
+// f of both components of slot i at node n, and the store of f.
+template <class S>
+__device__ __forceinline__ float2 ld2f(const typename S::P *f, const Lat &L, int i, long long n)
+{
+    const float2 v = S::raw2(f[pidx(L, i, n)]);
+    return make_float2(L.base[0][i] + v.x, L.base[1][i] + v.y);
+}
+template <class S>
+__device__ __forceinline__ void st2f(typename S::P *f, const Lat &L, int i, long long n, float2 v)
+{
+    f[pidx(L, i, n)] = S::enc2(make_float2(v.x - L.base[0][i], v.y - L.base[1][i]));
+}
+
+// Densities (ρ^red, ρ^blue) of node n from its stored populations: the
+// stored quantities summed in direction order, then ρ_ref added (0 in
+// FP32).  Every kernel that needs a node's density from memory takes it
+// from here, so they agree bit for bit.
+template <class S>
+__device__ __forceinline__ float2 node_rho2(const typename S::P *__restrict__ f, const Lat &L, long long n)
+{
+    float2 a = S::raw2(f[pidx(L, 0, n)]);
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        const float2 v = S::raw2(f[pidx(L, i, n)]);
+        a.x = __fadd_rn(a.x, v.x);
+        a.y = __fadd_rn(a.y, v.y);
+    }
+    return make_float2(__fadd_rn(L.rref[0], a.x), __fadd_rn(L.rref[1], a.y));
+}
 
 // Checked builds (-DLBE_CHECK) verify every data-dependent or computed index
 // before use; a bad one is recorded (code << 40 | index) and the access is
@@ -158,10 +177,12 @@ constexpr double FIXED_UNIT = 1.0 / 1099511627776.0;  // 2^-40
 // its fluid neighbours, the colour Δρ added to red if positive, else |Δρ| to
 // blue, then ψ^c = 1 - exp(-ρ^c).  Nothing for a node without a fluid
 // neighbour (never read by a fluid node).  nb(i) is the neighbour index
-// along c_i, -1 beyond a wall.  Returns the mask of fluid neighbours.
-template <class NB>
-__device__ __forceinline__ uint32_t shell_fill(const Lat &L, const float *__restrict__ rho, float *__restrict__ psi,
-                                               const uint8_t *__restrict__ type, int n, float dr, NB nb)
+// along c_i, -1 beyond a wall; rho_of(m) gives (ρ^red, ρ^blue) of fluid node
+// m.  Returns the mask of fluid neighbours.
+template <class NB, class RHO>
+__device__ __forceinline__ uint32_t shell_fill_with(const Lat &L, float *__restrict__ psi,
+                                                    const uint8_t *__restrict__ type, int n, float dr, NB nb,
+                                                    RHO rho_of)
 {
     float s0 = 0.f, s1 = 0.f;
     int cnt = 0;
@@ -170,8 +191,9 @@ __device__ __forceinline__ uint32_t shell_fill(const Lat &L, const float *__rest
     for (int i = 1; i < Q; i++) {
         const int m = nb(i);
         if (m < 0 || type[m] != FLUID) continue;
-        s0 += rho[m];
-        s1 += rho[(size_t)L.N + m];
+        const float2 r = rho_of(m);
+        s0 += r.x;
+        s1 += r.y;
         cnt++;
         fm |= 1u << i;
     }
@@ -184,6 +206,15 @@ __device__ __forceinline__ uint32_t shell_fill(const Lat &L, const float *__rest
     psi[n] = 1.f - expf(-r0);
     psi[(size_t)L.N + n] = 1.f - expf(-r1);
     return fm;
+}
+
+// The same with the neighbours' densities from the array rho[2][N].
+template <class NB>
+__device__ __forceinline__ uint32_t shell_fill(const Lat &L, const float *__restrict__ rho, float *__restrict__ psi,
+                                               const uint8_t *__restrict__ type, int n, float dr, NB nb)
+{
+    return shell_fill_with(L, psi, type, n, dr, nb,
+                           [&](int m) { return make_float2(rho[m], rho[(size_t)L.N + m]); });
 }
 
 // Append (n, m) for the lanes with m != 0 to a link list: one atomic per
@@ -217,18 +248,16 @@ struct Cells {
     int *cid;          // [cap] cell of each particle
 };
 
-// Offsets of the population arrays of a lattice: pop[c*Q+i] = (c*Q+i)*S and
-// push[c*Q+i] = pop[c*Q+i] + (cx + cy*nx + cz*nx*ny), so the address of a
-// load or of an interior push is one add.
-// Element offsets of the fused kernel's loads and stores from a node: its
-// own slot (pop) and the neighbour's it pushes to (push), from the base of
-// the population array; and the same from the base of the node's component
-// as 32-bit words (pop32, push32), used where they fit (fused_rel32).
+// Pair offsets of the fused kernel's loads and stores from a node: its own
+// slot pop[i] = i S and the neighbour's it pushes to, push[i] = pop[i] +
+// (cx + cy nx + cz nx ny), so the address of a load or of an interior push
+// is one add; as 64-bit words, and as 32-bit words (pop32, push32) used
+// where they fit (fused_rel32).
 struct FusedOfs {
-    long long pop[2 * Q];
-    long long push[2 * Q];
-    unsigned pop32[2 * Q];
-    unsigned push32[2 * Q];
+    long long pop[Q];
+    long long push[Q];
+    unsigned pop32[Q];
+    unsigned push32[Q];
 };
 FusedOfs fused_offsets(const Lat &L);
 bool fused_rel32(const Lat &L);
@@ -278,9 +307,13 @@ void launch_shell(const Lat &L, const float *rho, float *psi, const uint8_t *typ
 // Shell fill of the particles' own nodes (one CTA per particle over its
 // candidate rows) and of the wall planes: the solid nodes a fluid node can
 // see, without a sweep of the lattice.
+// Shell fill of the particles' own nodes (one CTA per particle over its
+// candidate rows), with the neighbours' densities from rho, and of the wall
+// planes, with the densities of the planes next to the walls computed from
+// the populations f (a lattice without particles runs no density kernel).
 void launch_shell_particles(const Lat &L, const Parts &P, const float *rho, float *psi, const uint8_t *type,
                             const uint32_t *owner, const LinkList &ll, cudaStream_t s);
-void launch_shell_walls(const Lat &L, const float *rho, float *psi, const uint8_t *type, cudaStream_t s);
+void launch_shell_walls(int storage, const Lat &L, const void *f, float *psi, const uint8_t *type, cudaStream_t s);
 void launch_collide_stream(int storage, const Lat &L, const void *fin, void *fout, const float *psi,
                            const uint8_t *type, cudaStream_t s);
 void launch_fields(int storage, const Lat &L, const void *f, const float *psi, const uint8_t *type,
@@ -307,14 +340,28 @@ void launch_link_batch(int storage, const BatchIndex &B, cudaStream_t s);
 void launch_flip_batch(const BatchIndex &B, cudaStream_t s);
 
 // ---- launchers (fused.cu) -------------------------------------------------
-void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *rho, const float *psi,
-                  const uint8_t *type, const CUtensorMap *tmap, cudaStream_t s, int zc_override = 0);
-int fused_zchunk(const Lat &L);
-// Tensor map of one population buffer for the fused kernel's plane copies
-// (box 32 x 8 x 1 x 38 of the (x, y, z, slot) array); false if the lattice's
-// row pitch is not a multiple of 16 bytes or the driver lacks the call.
-bool fused_plane_map(CUtensorMap *map, void *f, const Lat &L, int storage);
-constexpr int FUSED_TX = 32, FUSED_TY = 8;
+// The fused kernel's tiles are 32 nodes wide and 4 or 8 rows high; zc is the
+// z chunk in planes (0: the default for the lattice), ty the requested tile
+// height (4 or 8; configurations without a 4-row variant take 8), and
+// wait_limit the tries of each bounded wait for a box copy.
+constexpr int FUSED_TX = 32, FUSED_TY_BATCH = 8;
+constexpr int FUSED_WAIT_LIMIT = 1 << 22;
+// self: the kernel forms ψ of fluid nodes from the densities of the tile
+// and a one-node halo (psi then holds ψ of solid nodes only); otherwise psi
+// holds ψ of every node (density kernel and shell fill).
+void launch_fused(int storage, const Lat &L, const void *fin, void *fout, const float *psi, const uint8_t *type,
+                  const CUtensorMap *tmap, cudaStream_t s, int zc, int ty, int wait_limit, bool self);
+int fused_zchunk(const Lat &L, int ty);
+// The tile height launch_fused takes for a request (4 only where built).
+int fused_rows(const Lat &L, int ty_request, bool tma);
+bool fused_tau1(const Lat &L);
+// Tensor map of one population buffer for the fused kernel's box copies
+// (tile plus a one-node halo, x widened to 16-byte boundaries: 40 x (ty+2) x
+// 1 x 19 pairs at 16 bit, 36 x (ty+2) x 1 x 19 in FP32, of the (x, y, z,
+// direction) array); false if the lattice's row pitch is not a multiple of
+// 16 bytes or the driver lacks the call.
+// self: the box with the halo; otherwise the tile alone (32 x ty x 1 x 19).
+bool fused_plane_map(CUtensorMap *map, void *f, const Lat &L, int storage, int ty, bool self);
 
 // Box lookup: the box b with off[b] <= i < off[b+1] (binary search).
 __device__ __forceinline__ int find_box(const int *off, int nbox, int i)

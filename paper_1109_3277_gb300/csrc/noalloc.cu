@@ -19,7 +19,10 @@ double *g_scratch_ptr[MAX_DEVICES] = {};
 
 // Device address of the scratch array on `dev` (which must be current).
 // The host-side name of the array is only a stand-in, so the address is
-// looked up once per device and cached.
+// looked up once per device and cached for the life of the process.  A
+// device reset (cudaDeviceReset) reloads the module, after which the cached
+// address is stale: callers that reset a device must not call
+// lbe_mass_noalloc on it afterwards.
 cudaError_t scratch_on(int dev, double **out)
 {
     std::lock_guard<std::mutex> lock(g_mutex);
@@ -44,25 +47,31 @@ extern "C" LBE_API lbe_status lbe_mass_noalloc(const void *f, int32_t storage, c
     if (nodes < 1 || nodes > LBE_NOALLOC_MAX_NODES || slot_stride < nodes) return LBE_EINVAL;
     if (storage < LBE_STORE_F32 || storage > LBE_STORE_F16_OFS) return LBE_EINVAL;
     if (storage != LBE_STORE_F32 && !rho_ref) return LBE_EINVAL;
-    int dev = device;
-    if (dev >= 0) {
-        if (cudaSetDevice(dev) != cudaSuccess) return LBE_EINVAL;
-    } else if (cudaGetDevice(&dev) != cudaSuccess) {
-        return LBE_ECUDA;
-    }
+    if (device < -1) return LBE_EINVAL;
+    int prev = 0;
+    if (cudaGetDevice(&prev) != cudaSuccess) return LBE_ECUDA;
+    const int dev = device >= 0 ? device : prev;
     if (dev >= MAX_DEVICES) return LBE_EINVAL;
+    if (dev != prev && cudaSetDevice(dev) != cudaSuccess) return LBE_EINVAL;
+    lbe_status st = LBE_OK;
     double *scratch = nullptr;
-    if (scratch_on(dev, &scratch) != cudaSuccess) return LBE_ECUDA;
-    Lat L{};
-    L.nx = (int)nodes;
-    L.ny = 1;
-    L.nz = 1;
-    L.N = (int)nodes;
-    L.S = slot_stride;
-    for (int c = 0; c < 2; c++)
-        for (int i = 0; i < Q; i++)
-            L.base[c][i] = storage == LBE_STORE_F32 ? 0.f : (float)(wgtd(i) * rho_ref[c]);
-    // every block writes its own partial sums, so nothing needs clearing
-    launch_mass(storage, L, f, node_type, scratch, SCRATCH_BLOCKS, out, (cudaStream_t)cuda_stream);
-    return cudaGetLastError() == cudaSuccess ? LBE_OK : LBE_ECUDA;
+    if (scratch_on(dev, &scratch) != cudaSuccess) {
+        st = LBE_ECUDA;
+    } else {
+        Lat L{};
+        L.nx = (int)nodes;
+        L.ny = 1;
+        L.nz = 1;
+        L.N = (int)nodes;
+        L.S = slot_stride;
+        for (int c = 0; c < 2; c++)
+            for (int i = 0; i < Q; i++)
+                L.base[c][i] = storage == LBE_STORE_F32 ? 0.f : (float)(wgtd(i) * rho_ref[c]);
+        // every block writes its own partial sums, so nothing needs clearing
+        launch_mass(storage, L, f, node_type, scratch, SCRATCH_BLOCKS, out, (cudaStream_t)cuda_stream);
+        if (cudaGetLastError() != cudaSuccess) st = LBE_ECUDA;
+    }
+    // the caller's current device is left as it was
+    if (dev != prev) cudaSetDevice(prev);
+    return st;
 }

@@ -409,12 +409,6 @@ __device__ void block_sum(double (&v)[K], double (*sh)[PT / 32])
     }
 }
 
-template <class S>
-__device__ __forceinline__ typename S::T *slot(typename S::T *f, const Lat &L, int c, int i)
-{
-    return f + (size_t)(c * Q + i) * (size_t)L.S;
-}
-
 __device__ __forceinline__ int nbr_node(const Lat &L, int x, int y, int z, int i)
 {
     int xx = x + cx(i), yy = y + cy(i), zz = z + cz(i);
@@ -436,7 +430,7 @@ __device__ __forceinline__ int nbr_node(const Lat &L, int x, int y, int z, int i
 // particle F = (2 f*_ī + C) c_ī and r_b × F (Eq. 5).
 
 template <class S>
-__global__ void __launch_bounds__(PT) k_links(Lat L, Parts P, typename S::T *__restrict__ fnew,
+__global__ void __launch_bounds__(PT) k_links(Lat L, Parts P, typename S::P *__restrict__ fnew,
                                               const float *__restrict__ rho,
                                               const uint8_t *__restrict__ type,
                                               const uint32_t *__restrict__ owner)
@@ -477,12 +471,13 @@ __global__ void __launch_bounds__(PT) k_links(Lat L, Parts P, typename S::T *__r
             float us[3] = {sV[0] + sW[1] * rb[2] - sW[2] * rb[1], sV[1] + sW[2] * rb[0] - sW[0] * rb[2],
                            sV[2] + sW[0] * rb[1] - sW[1] * rb[0]};
             float uc = us[0] * cx(i) + us[1] * cy(i) + us[2] * cz(i);
+            const float2 fr2 = ld2f<S>(fnew, L, i, m);
+            float2 out2;
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                typename S::T *sl = slot<S>(fnew, L, c, i) + m;
-                float fr = S::ldc(sl, L.base[c][i]);
+                float fr = c ? fr2.y : fr2.x;
                 float C = 6.f * wgt(i) * rho[(size_t)c * L.N + m] * uc;
-                S::st(sl, fr + C, L.base[c][i]);
+                (c ? out2.y : out2.x) = fr + C;
                 float a = -(2.f * fr + C);  // F = (2 f* + C) c_ī, c_ī = -c_i
                 float F[3] = {a * cx(i), a * cy(i), a * cz(i)};
                 aF[0] += F[0];
@@ -492,6 +487,7 @@ __global__ void __launch_bounds__(PT) k_links(Lat L, Parts P, typename S::T *__r
                 aT[1] += rb[2] * F[0] - rb[0] * F[2];
                 aT[2] += rb[0] * F[1] - rb[1] * F[0];
             }
+            st2f<S>(fnew, L, i, m, out2);
         }
         for (int k2 = 0; k2 < 3; k2++) {
             acc[k2] += (double)aF[k2];
@@ -556,7 +552,7 @@ template <class S>
 __device__ __forceinline__ void link_entry(const Lat &L, uint2 e, bool valid, const float *__restrict__ rho,
                                            const uint32_t *__restrict__ owner, const float4 *__restrict__ X32,
                                            const float4 *__restrict__ K32, unsigned long long *fix,
-                                           typename S::T *fout)
+                                           typename S::P *fout)
 {
     unsigned long long acc[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
     uint32_t fm = valid ? e.y : 0u;
@@ -609,16 +605,15 @@ __device__ __forceinline__ void link_entry(const Lat &L, uint2 e, bool valid, co
         // u_surf·c_i with c_i = -c_j
         const float uci = -__fadd_rn(__fadd_rn(usx * cx(j), usy * cy(j)), usz * cz(j));
         const float w6 = j < 7 ? -6.f / 18.f : -6.f / 36.f;
+        // both components of slot j of the fluid node: one pair access
+        typename S::P *q = fout + pidx(L, j, yf);
+        const float2 fs = ld2f<S>(fout, L, j, yf);
+        const float C0 = __fmul_rn(__fmul_rn(w6, __ldg(rho + yf)), uci);
+        const float C1 = __fmul_rn(__fmul_rn(w6, __ldg(rho + (size_t)L.N + yf)), uci);
+        *q = S::enc2(make_float2(__fadd_rn(fs.x, C0) - L.base[0][j], __fadd_rn(fs.y, C1) - L.base[1][j]));
         float a = 0.f;
-#pragma unroll
-        for (int c = 0; c < 2; c++) {
-            const float base = L.base[c][j];
-            typename S::T *q = fout + (size_t)(c * Q + j) * (size_t)L.S + yf;
-            const float fs = S::ldc(q, base);
-            const float C = __fmul_rn(__fmul_rn(w6, __ldg(rho + (size_t)c * L.N + yf)), uci);
-            S::st(q, __fadd_rn(fs, C), base);
-            a = __fadd_rn(a, __fmaf_rn(2.f, fs, C));
-        }
+        a = __fadd_rn(a, __fmaf_rn(2.f, fs.x, C0));
+        a = __fadd_rn(a, __fmaf_rn(2.f, fs.y, C1));
         // F = a c_i = -a c_j
         const float Fx = -a * cx(j), Fy = -a * cy(j), Fz = -a * cz(j);
         acc[0] += to_fixed(Fx);
@@ -635,7 +630,7 @@ __device__ __forceinline__ void link_entry(const Lat &L, uint2 e, bool valid, co
 // reductions).
 template <class S>
 __device__ __forceinline__ void link_list(const Lat &L, const LinkList &ll, const float *rho, const uint32_t *owner,
-                                          const Parts &P, typename S::T *fout, int first, int stride)
+                                          const Parts &P, typename S::P *fout, int first, int stride)
 {
     const int count = min(*ll.count, ll.cap);
     for (int w0 = first + (int)(threadIdx.x & ~31u); w0 < count; w0 += stride) {
@@ -647,7 +642,7 @@ __device__ __forceinline__ void link_list(const Lat &L, const LinkList &ll, cons
 
 template <class S>
 __global__ void __launch_bounds__(256) k_link(Lat L, LinkList ll, const float *rho, const uint32_t *owner, Parts P,
-                                              typename S::T *fout)
+                                              typename S::P *fout)
 {
     link_list<S>(L, ll, rho, owner, P, fout, blockIdx.x * blockDim.x, gridDim.x * blockDim.x);
 }
@@ -662,7 +657,7 @@ __global__ void __launch_bounds__(256) k_link_batch(BatchIndex B)
     const BoxDev &bx = B.box[b];
     if (!bx.links.ent || bx.P.n == 0) return;
     const int cur = B.par[2 * b], ocur = B.par[2 * b + 1];
-    link_list<S>(bx.L, bx.links, bx.rho, bx.owner[ocur], bx.P, (typename S::T *)bx.f[1 - cur],
+    link_list<S>(bx.L, bx.links, bx.rho, bx.owner[ocur], bx.P, (typename S::P *)bx.f[1 - cur],
                  blockIdx.x * blockDim.x, gridDim.x * blockDim.x);
 }
 
@@ -1075,7 +1070,7 @@ __global__ void __launch_bounds__(PT) k_claim(Lat L, Parts P, uint32_t *__restri
 // With placement != 0 (particles just added) nodes only change type.
 
 template <class S>
-__device__ __forceinline__ void transition_body(const Lat &L, const Parts &P, int p, typename S::T *__restrict__ f,
+__device__ __forceinline__ void transition_body(const Lat &L, const Parts &P, int p, typename S::P *__restrict__ f,
                                                 uint8_t *__restrict__ type, const uint32_t *__restrict__ own_old,
                                                 const uint32_t *__restrict__ own_new, int placement)
 {
@@ -1105,7 +1100,8 @@ __device__ __forceinline__ void transition_body(const Lat &L, const Parts &P, in
             for (int c = 0; c < 2; c++)
 #pragma unroll
                 for (int i = 0; i < Q; i++) {
-                    float v = S::ldc(slot<S>(f, L, c, i) + n, L.base[c][i]);
+                    const float2 v2 = ld2f<S>(f, L, i, n);
+                    float v = c ? v2.y : v2.x;
                     if (cx(i)) mom[0] += cx(i) * (double)v;
                     if (cy(i)) mom[1] += cy(i) * (double)v;
                     if (cz(i)) mom[2] += cz(i) * (double)v;
@@ -1130,8 +1126,9 @@ __device__ __forceinline__ void transition_body(const Lat &L, const Parts &P, in
                 float a0 = 0.f, a1 = 0.f;
 #pragma unroll
                 for (int j = 0; j < Q; j++) {
-                    a0 += S::ldc(slot<S>(f, L, 0, j) + m, L.base[0][j]);
-                    a1 += S::ldc(slot<S>(f, L, 1, j) + m, L.base[1][j]);
+                    const float2 v2 = ld2f<S>(f, L, j, m);
+                    a0 += v2.x;
+                    a1 += v2.y;
                 }
                 sr0 += a0;
                 sr1 += a1;
@@ -1145,6 +1142,7 @@ __device__ __forceinline__ void transition_body(const Lat &L, const Parts &P, in
                            (float)(sV[2] + sW[0] * r[1] - sW[1] * r[0])};
             float uu = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
             double mom[3] = {0, 0, 0};
+            float fe2[2][Q];
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 float rc = c ? rb1 : rb0;
@@ -1152,12 +1150,14 @@ __device__ __forceinline__ void transition_body(const Lat &L, const Parts &P, in
                 for (int i = 0; i < Q; i++) {
                     float cu = cx(i) * us[0] + cy(i) * us[1] + cz(i) * us[2];
                     float fe = wgt(i) * rc * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
-                    S::st(slot<S>(f, L, c, i) + n, fe, L.base[c][i]);
+                    fe2[c][i] = fe;
                     if (cx(i)) mom[0] += cx(i) * (double)fe;
                     if (cy(i)) mom[1] += cy(i) * (double)fe;
                     if (cz(i)) mom[2] += cz(i) * (double)fe;
                 }
             }
+#pragma unroll
+            for (int i = 0; i < Q; i++) st2f<S>(f, L, i, n, make_float2(fe2[0][i], fe2[1][i]));
             double t[3];
             cross3(r, mom, t);
             for (int k2 = 0; k2 < 3; k2++) {
@@ -1197,7 +1197,7 @@ __device__ __forceinline__ void transition_body(const Lat &L, const Parts &P, in
 // compare two owner words, and the occupancy hides their latency; the
 // rare fill and empty spill a few registers.
 template <class S>
-__global__ void __launch_bounds__(PT, 8) k_transition(Lat L, Parts P, typename S::T *__restrict__ f,
+__global__ void __launch_bounds__(PT, 8) k_transition(Lat L, Parts P, typename S::P *__restrict__ f,
                                                    uint8_t *__restrict__ type,
                                                    const uint32_t *__restrict__ own_old,
                                                    const uint32_t *__restrict__ own_new,
@@ -1235,6 +1235,7 @@ __global__ void __launch_bounds__(PT) k_reset(Lat L, Parts P, int use_old, uint3
 // over its candidate rows; its nodes with fluid neighbours enter the link
 // list.  With the wall planes these are all the solid nodes a fluid node
 // can see.
+// The densities of the fluid neighbours come from the density kernel.
 __global__ void __launch_bounds__(PT) k_shell_particles(Lat L, Parts P, const float *__restrict__ rho,
                                                         float *__restrict__ psi, const uint8_t *__restrict__ type,
                                                         const uint32_t *__restrict__ owner, LinkList ll)
@@ -1258,8 +1259,10 @@ __global__ void __launch_bounds__(PT) k_shell_particles(Lat L, Parts P, const fl
     });
 }
 
-// Shell fill of the wall planes z = 0 and nz - 1 (Δρ = 0).
-__global__ void k_shell_walls(Lat L, const float *__restrict__ rho, float *__restrict__ psi,
+// Shell fill of the wall planes z = 0 and nz - 1 (Δρ = 0), with the
+// densities of the neighbouring planes' fluid nodes from the populations.
+template <class S>
+__global__ void k_shell_walls(Lat L, const typename S::P *__restrict__ f, float *__restrict__ psi,
                               const uint8_t *__restrict__ type)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1269,7 +1272,8 @@ __global__ void k_shell_walls(Lat L, const float *__restrict__ rho, float *__res
     const int x = r % L.nx, y = r / L.nx;
     const int n = x + L.nx * (y + L.ny * z);
     if (type[n] != WALL) return;
-    shell_fill(L, rho, psi, type, n, 0.f, [&](int i) { return nbr_node(L, x, y, z, i); });
+    shell_fill_with(L, psi, type, n, 0.f, [&](int i) { return nbr_node(L, x, y, z, i); },
+                    [&](int m) { return node_rho2<S>(f, L, m); });
 }
 
 // ------------------------------------------------------------- batched
@@ -1293,7 +1297,7 @@ __global__ void __launch_bounds__(PT) k_transition_batch(BatchIndex B, int total
     const BoxDev &bx = B.box[b];
     if (bx.mode == LBE_PARTICLES_STATIC) return;
     const int cur = B.par[2 * b], ocur = B.par[2 * b + 1];
-    transition_body<S>(bx.L, bx.P, g - B.part0[b], (typename S::T *)bx.f[1 - cur], bx.type, bx.owner[ocur],
+    transition_body<S>(bx.L, bx.P, g - B.part0[b], (typename S::P *)bx.f[1 - cur], bx.type, bx.owner[ocur],
                        bx.owner[1 - ocur], 0);
 }
 
@@ -1444,7 +1448,7 @@ void launch_links(int storage, const Lat &L, const Parts &P, void *fnew, const f
                   const uint8_t *type, const uint32_t *owner, cudaStream_t s)
 {
     if (P.n == 0) return;
-    LBE_DISPATCH(storage, (k_links<S><<<P.n, PT, 0, s>>>(L, P, (typename S::T *)fnew, rho, type, owner)));
+    LBE_DISPATCH(storage, (k_links<S><<<P.n, PT, 0, s>>>(L, P, (typename S::P *)fnew, rho, type, owner)));
 }
 
 void launch_pairs(const Lat &L, const Parts &P, const Pair &pp, const Cells &C, cudaStream_t s)
@@ -1483,7 +1487,7 @@ void launch_transition(int storage, const Lat &L, const Parts &P, void *f, uint8
                        cudaStream_t s)
 {
     if (P.n == 0) return;
-    LBE_DISPATCH(storage, (k_transition<S><<<P.n, PT, 0, s>>>(L, P, (typename S::T *)f, type, owner_old,
+    LBE_DISPATCH(storage, (k_transition<S><<<P.n, PT, 0, s>>>(L, P, (typename S::P *)f, type, owner_old,
                                                                owner_new, placement)));
 }
 
@@ -1499,7 +1503,7 @@ void launch_link(int storage, const Lat &L, const LinkList &ll, const float *rho
     if (P.n == 0 || !ll.ent) return;
     int blocks = (L.N + 255) / 256;
     if (blocks > 8 * 152) blocks = 8 * 152;
-    LBE_DISPATCH(storage, (k_link<S><<<blocks, 256, 0, s>>>(L, ll, rho, owner, P, (typename S::T *)fout)));
+    LBE_DISPATCH(storage, (k_link<S><<<blocks, 256, 0, s>>>(L, ll, rho, owner, P, (typename S::P *)fout)));
 }
 
 void launch_link_batch(int storage, const BatchIndex &B, cudaStream_t s)
@@ -1515,11 +1519,11 @@ void launch_shell_particles(const Lat &L, const Parts &P, const float *rho, floa
     k_shell_particles<<<P.n, PT, 0, s>>>(L, P, rho, psi, type, owner, ll);
 }
 
-void launch_shell_walls(const Lat &L, const float *rho, float *psi, const uint8_t *type, cudaStream_t s)
+void launch_shell_walls(int storage, const Lat &L, const void *f, float *psi, const uint8_t *type, cudaStream_t s)
 {
     if (!L.walls) return;
     const int n = 2 * L.nx * L.ny;
-    k_shell_walls<<<(n + 255) / 256, 256, 0, s>>>(L, rho, psi, type);
+    LBE_DISPATCH(storage, (k_shell_walls<S><<<(n + 255) / 256, 256, 0, s>>>(L, (const typename S::P *)f, psi, type)));
 }
 
 void launch_reset(const Lat &L, const Parts &P, int use_old, uint32_t *owner, cudaStream_t s)

@@ -68,6 +68,9 @@ SIGNATURES = {
                                          ctypes.c_int32, _P, _P]),
     "lbe_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "lbe_set_zchunk": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "lbe_set_tile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "lbe_get_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
+    "lbe_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int32]),
     "lbe_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_P)]),
     "lbe_batch_step": (ctypes.c_int, [_P, ctypes.c_int32]),
     "lbe_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
@@ -233,6 +236,20 @@ class Lattice:
     def set_zchunk(self, zc):
         """Fix the fused kernel's z chunk (0: default); results do not depend on it."""
         self._check(load().lbe_set_zchunk(self._ptr, int(zc)), "set_zchunk")
+
+    def set_tile(self, rows, zc=0):
+        """Fix the fused kernel's tile height (4 or 8) and z chunk (0: default)."""
+        self._check(load().lbe_set_tile(self._ptr, int(rows), int(zc)), "set_tile")
+
+    def tile(self):
+        """(rows, z chunk) of the fused kernel's tiles in use."""
+        r, z = ctypes.c_int32(), ctypes.c_int32()
+        self._check(load().lbe_get_tile(self._ptr, ctypes.byref(r), ctypes.byref(z)), "get_tile")
+        return r.value, z.value
+
+    def set_wait_limit(self, tries):
+        """Tries of each bounded wait for a box copy (0: the default)."""
+        self._check(load().lbe_set_wait_limit(self._ptr, int(tries)), "set_wait_limit")
 
     def device_bytes(self):
         return int(load().lbe_device_bytes(self._ptr))
