@@ -56,6 +56,8 @@ def parse(argv=None):
                     help="fused-kernel z chunk in planes (default 0: the library's autotuner picks it)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="leave out the short serving leg of the default line")
     return ap.parse_args(argv)
 
 
@@ -212,19 +214,25 @@ def add_particles(lat, w):
         lat.add_particles(p["pos"], p["quat"], p["r_par"], p["r_perp"], p["delta_rho"])
 
 
-def cpu_sample_workload(w):
-    """A bounded sample of the workload for the CPU oracle: a sub-box with
-    the same node mix, particle shape and particle number density."""
-    if w.name.startswith("pickering"):
-        return W.pickering(seed=1113, n=64), "64^3 sub-box of the same recipe"
-    if w.name.startswith("bijel"):
-        return W.bijel(seed=1112, n=64), "64^3 sub-box of the same recipe"
-    if w.name.startswith("spinodal"):
-        return W.spinodal(seed=1111, n=64), "64^3 sub-box of the same recipe"
+def cpu_sample_workload(w, n=96):
+    """A bounded sample of the workload (a workload, or its recipe's name)
+    for the CPU oracle: a sub-box with the same node mix, particle shape and
+    particle number density."""
+    name = w if isinstance(w, str) else w.name
+    if name.startswith("pickering"):
+        return W.pickering(seed=1113, n=n), f"{n}^3 sub-box of the same recipe"
+    if name.startswith("bijel"):
+        return W.bijel(seed=1112, n=n), f"{n}^3 sub-box of the same recipe"
+    if name.startswith("spinodal"):
+        return W.spinodal(seed=1111, n=n), f"{n}^3 sub-box of the same recipe"
+    if isinstance(w, str):
+        return make_workload(w), "the full workload"
     return w, "the full workload"
 
 
 def time_oracle(w, steps, warmup=1):
+    """MLUPS of the FP64 oracle on w in this process (the serial build, or
+    the one LBREF_LIB names) and the seconds the timed steps took."""
     from oracle import lbref
     params = dict(w.params)
     lat = lbref.Lattice(w.shape, w.rho0, **params)
@@ -239,6 +247,32 @@ def time_oracle(w, steps, warmup=1):
     n = int(np.prod(w.shape))
     lat.close()
     return n * steps / dt / 1e6, dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def time_oracle_all_cores(workload, sample_n, steps, warmup=1):
+    """The oracle's OpenMP build (per-node phases over threads, results equal
+    to the serial build's) timed on every host core, in a child process so
+    that its library does not replace the serial one here.  Returns (MLUPS,
+    seconds, threads)."""
+    from oracle import lbref
+    lib = lbref.build(omp=True)
+    threads = host_cores()
+    code = ("import json, bench\n"
+            f"w, _ = bench.cpu_sample_workload({workload!r}, {sample_n})\n"
+            f"print(json.dumps(bench.time_oracle(w, {steps}, {warmup})))\n")
+    env = dict(os.environ, LBREF_LIB=lib, OMP_NUM_THREADS=str(threads), OMP_PROC_BIND="spread")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing on all cores failed: " + r.stderr[-2000:])
+    v, dt = json.loads(r.stdout.strip().splitlines()[-1])
+    return v, dt, threads
 
 
 def run_ours(args):
@@ -263,6 +297,7 @@ def run_ours(args):
         zc = args.zchunk
     else:
         zc = lat.autotune()  # the library's z-chunk autotuner (CUDA events, state unchanged)
+    rows, zc = lat.tile()
     torch.cuda.synchronize()
     lat.profile_enable(True)
     clocks = Clocks(dist.local)
@@ -328,9 +363,21 @@ def run_ours(args):
     cpu = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         ws, what = cpu_sample_workload(w)
-        v, dt = time_oracle(ws, steps=3, warmup=1)
-        cpu = {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{what}: {ws.name}, 3 steps after 1 warm-up ({dt:.1f} s, FP64, 1 thread)"}
+        v1, dt1 = time_oracle(ws, steps=3, warmup=1)
+        va, dta, thr = time_oracle_all_cores(args.workload, 96, steps=6, warmup=1)
+        cpu = {"value": round(va, 4), "unit": UNIT, "cores": thr, "kind": "oracle",
+               "sample": f"{what}: {ws.name}, FP64; on {thr} threads (OpenMP build, per-node phases in "
+                         f"parallel) 6 steps after 1 warm-up ({dta:.1f} s); on 1 thread 3 steps ({dt1:.1f} s)",
+               "single_thread": {"value": round(v1, 4), "unit": UNIT, "cores": 1}}
+    # ---------------- a short serving leg (rank 0, N = 1)
+    serving = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_serving and args.workload == "pickering":
+        results, same, budget = serving_arms(12, 50.0, 0)
+        serving = {"requests": 12, "rate_per_s": 50.0, "workload": "adsorption boxes, edge 32..96, "
+                   "tilt tolerance 1e-4 per 100 steps, at most 20000 steps", "arms": results,
+                   "batched_f32_equals_one_at_a_time_f32": bool(same),
+                   "throughput_ratio_batched_f32_vs_one_at_a_time_f32":
+                       round(results["batched_f32"]["boxes_per_s"] / results["one_at_a_time_f32"]["boxes_per_s"], 2)}
     if dist.rank == 0:
         line = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": dist.world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4),
@@ -340,34 +387,30 @@ def run_ours(args):
                            "particles": int(len(w.particles["pos"])) if w.particles else 0,
                            "storage": storage, "bytes_per_node_update": 2 * 2 * 19 * ESIZE[storage],
                            "parallelism": f"replicas x{dist.world}", "fused_z_chunk": zc,
+                           "fused_tile_rows": rows,
                            "l2": "inputs larger than L2 (populations %.1f GB)" % (
                                2 * nodes * 2 * 19 * ESIZE[storage] / 1e9)},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "serving": serving,
                 "gpu_launches": int(kernels_per_step * args.steps), "clocks": clk,
                 "mass": [float(x) for x in m]}
         print(json.dumps(line), flush=True)
     dist.close()
 
 
-def run_serving(args):
-    """Serving of single-particle adsorption requests (cubic boxes of edge
-    32..96 with walls, one ellipsoid of aspect ratio 0.25..4 near a flat
-    interface, run until the tilt changes by < 1e-4 rad per 100 steps, at
-    most 20,000 steps) arriving as a Poisson stream that saturates the GPU.
-    Arms: continuous batching in FP16-offset and FP32 storage, and one box at
-    a time in FP32.  Latency is submission to result; throughput is boxes
-    per second and node updates per second over the whole run."""
+def serving_arms(K, rate, rank, edge_range=(32, 96)):
+    """Serve K single-particle adsorption requests (cubic boxes with walls,
+    one ellipsoid of aspect ratio 0.25..4 near a flat interface, run until
+    the tilt changes by < 1e-4 rad per 100 steps, at most 20,000 steps)
+    arriving as a Poisson stream of the given rate, in three arms:
+    continuous batching in FP16-offset and FP32 storage, and one box at a
+    time in FP32.  Returns (per-arm results, whether batched FP32 equals one
+    at a time bit for bit, the HBM budget)."""
     import torch
     from paper_1109_3277_gb300 import lbe
-    from paper_1109_3277_gb300 import build as lbe_build
 
-    world, rank, local = dist_info()
-    torch.cuda.set_device(local)
-    lbe_build.build()
-    K = args.requests
-    reqs = [W.adsorption_request(1114 + rank, i) for i in range(K)]
+    reqs = [W.adsorption_request(1114 + rank, i, edge_range=edge_range) for i in range(K)]
     u = W.uniform(1115 + rank, (K,), stream=7)
-    arrivals = np.cumsum(-np.log1p(-u) / args.rate)
+    arrivals = np.cumsum(-np.log1p(-u) / rate)
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
     arms = [("batched", "f16", 256), ("batched", "f32", 256), ("one_at_a_time", "f32", 1)]
@@ -409,6 +452,21 @@ def run_serving(args):
     same = all((a[2] is None and b[2] is None) or
                (a[2] is not None and b[2] is not None and np.array_equal(a[2], b[2], equal_nan=True))
                for a, b in zip(outs[("batched", "f32")], outs[("one_at_a_time", "f32")]))
+    return results, same, budget
+
+
+def run_serving(args):
+    """Serving of single-particle adsorption requests (serving_arms) as its
+    own line: latency is submission to result; throughput is boxes per
+    second and node updates per second over the whole run."""
+    import torch
+    from paper_1109_3277_gb300 import build as lbe_build
+
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    lbe_build.build()
+    K = args.requests
+    results, same, budget = serving_arms(K, args.rate, rank)
     if rank == 0:
         b, o = results["batched_f16"], results["one_at_a_time_f32"]
         line = {"metric": "adsorption serving: p50/p99 solve latency, boxes/s", "value": b["boxes_per_s"],
@@ -514,26 +572,17 @@ def run_reference(args):
     if rank != 0:
         return
     w = make_workload(args.workload, args.n, args.storage)
-    ws, what = cpu_sample_workload(w)
-    from oracle import lbref
-    lat = lbref.Lattice(ws.shape, ws.rho0, **ws.params)
-    p = ws.particles
-    if p:
-        lat.add_particles(p["pos"], p["quat"], p["r_par"], p["r_perp"], p["delta_rho"])
-    lat.step(args.warmup)
-    t = time.perf_counter()
-    lat.step(args.steps)
-    dt = time.perf_counter() - t
-    nodes = int(np.prod(ws.shape))
-    v = nodes * args.steps / dt / 1e6
-    sample = f"{what}: {ws.name}, {args.steps} steps after {args.warmup} warm-up, FP64, 1 thread"
+    ws, what = cpu_sample_workload(w, 64)
+    v, dt, thr = time_oracle_all_cores(args.workload, 64, args.steps, args.warmup)
+    sample = (f"{what}: {ws.name}, {args.steps} steps after {args.warmup} warm-up, FP64, OpenMP build "
+              f"on {thr} threads")
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded recipe of the paper's workload)",
             "config": {"workload": w.name, "lattice": list(w.shape), "sample_lattice": list(ws.shape),
                        "storage": "f64"},
-            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": thr, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -218,15 +218,26 @@ LBE_API lbe_status lbe_set_tile(lbe_ctx *c, int32_t rows, int32_t zc);
 LBE_API lbe_status lbe_get_tile(const lbe_ctx *c, int32_t *rows, int32_t *zc);
 
 /* Failure detection of the fused kernel's copies: every wait for a plane's
- * box copy gives up after a bounded number of tries (about 2^22 by
- * default; each try may suspend the thread for a while).  The CTA then
- * stops, waits with the default bound for its copies in flight, and sets
- * the lattice's status word; the next synchronising call returns
- * LBE_ETIMEOUT.  lbe_set_wait_limit sets the number of tries (0 restores
- * the default) so that tests can make the wait run out; a run that timed
- * out has left the populations of the step partly written.  Synchronises
- * first; LBE_EINVAL for a negative count. */
-LBE_API lbe_status lbe_set_wait_limit(lbe_ctx *c, int32_t tries);
+ * box copy gives up after a bounded number of tries (a non-blocking look,
+ * then about 2^22 tries by default, each of which may suspend the thread
+ * for a while).  The CTA then stops, waits with the default bound for its
+ * copies in flight, and sets the lattice's status word; the next
+ * synchronising call returns LBE_ETIMEOUT.  lbe_set_wait_limit sets the
+ * number of tries (0 restores the default); with unreachable != 0 every
+ * wait is for a barrier phase that no copy completes, so that tests can
+ * make the wait run out without any fault.  A run that timed out has left
+ * the populations of the step partly written.  Synchronises first;
+ * LBE_EINVAL for a negative count. */
+LBE_API lbe_status lbe_set_wait_limit(lbe_ctx *c, int32_t tries, int32_t unreachable);
+
+/* Failure detection of allocations (for tests): the next `after` device
+ * allocations of the library succeed and every later one fails as if the
+ * device were out of memory, until lbe_fail_allocations(-1).  A call that
+ * meets the failure returns LBE_ENOMEM and frees what it had allocated
+ * (lbe_init_lattice keeps nothing; lbe_add_particles keeps the context as
+ * it was); a server request whose lattice cannot be created fails with
+ * LBE_ENOMEM and releases its share of the server's budget.  Process-wide. */
+LBE_API void lbe_fail_allocations(int32_t after);
 
 /* Batches: several lattices stepped together, every kernel of the step
  * covering all of them in one launch (the fused fluid kernel as a persistent

@@ -396,6 +396,9 @@ int lbref_add_particles(lbref_ctx *c, int32_t n, const double *pos, const double
 static void phase_moments(lbref_ctx *c)
 {
     long N = c->N;
+#ifdef LBREF_OMP
+#pragma omp parallel for schedule(static)
+#endif
     for (long n = 0; n < N; n++) {
         for (int cc = 0; cc < 2; cc++) {
             double r = 0, j0 = 0, j1 = 0, j2 = 0;
@@ -424,6 +427,9 @@ static void phase_moments(lbref_ctx *c)
 static void phase_psi(lbref_ctx *c)
 {
     long N = c->N;
+#ifdef LBREF_OMP
+#pragma omp parallel for schedule(static)
+#endif
     for (long n = 0; n < N; n++) {
         if (c->type[n] == T_FLUID) {
             for (int cc = 0; cc < 2; cc++) c->psi[cc * N + n] = 1.0 - exp(-c->rho[cc * N + n]);
@@ -462,6 +468,9 @@ static void phase_force(lbref_ctx *c)
 {
     long N = c->N;
     double g = c->d.g_br;
+#ifdef LBREF_OMP
+#pragma omp parallel for schedule(static)
+#endif
     for (long n = 0; n < N; n++) {
         for (int k = 0; k < 6; k++) c->frc[k * N + n] = 0.0;
         if (c->type[n] != T_FLUID) continue;
@@ -491,6 +500,9 @@ static void phase_force(lbref_ctx *c)
 static void phase_collide(lbref_ctx *c)
 {
     long N = c->N;
+#ifdef LBREF_OMP
+#pragma omp parallel for schedule(static)
+#endif
     for (long n = 0; n < N; n++) {
         if (c->type[n] != T_FLUID) continue;
         double num[3] = {0, 0, 0}, den = 0;

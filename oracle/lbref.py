@@ -22,16 +22,26 @@ _LIB = os.path.join(_HERE, "liblbref.so")
 Q = 19
 
 
-def build(force=False):
-    """Compile the oracle with plain gcc (no contraction of multiply-adds)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+_LIB_OMP = os.path.join(_HERE, "liblbref_omp.so")
+
+
+def build(force=False, omp=False):
+    """Compile the oracle with plain gcc (no contraction of multiply-adds).
+    omp=True builds liblbref_omp.so, whose per-node phases (moments, psi,
+    force, collision) run over OpenMP threads; every node is computed by the
+    same operations, and the particle sums stay serial, so its results equal
+    the serial build's bit for bit.  The pins run the serial build."""
+    lib_path = _LIB_OMP if omp else _LIB
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= max(
             os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "lbref.h"))):
-        return _LIB
+        return lib_path
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", _SRC,
-           "-o", _LIB + ".tmp", "-lm"]
+           "-o", lib_path + ".tmp", "-lm"]
+    if omp:
+        cmd[1:1] = ["-fopenmp", "-DLBREF_OMP"]
     subprocess.check_call(cmd)
-    os.replace(_LIB + ".tmp", _LIB)
-    return _LIB
+    os.replace(lib_path + ".tmp", lib_path)
+    return lib_path
 
 
 class LatticeDesc(ctypes.Structure):

@@ -141,11 +141,29 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *b, unsigned pa
     return ok != 0;
 }
 
+// Non-blocking look at the phase with this parity.
+__device__ __forceinline__ bool mbar_test_wait(unsigned long long *b, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for the phase with this parity; false if it has not completed
-// within the iteration limit (each try may suspend the thread for a while).
+// within `limit` tries: a non-blocking look, then tries that may each
+// suspend the thread for a while.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity, int limit)
 {
-    for (int k = 0; k < limit; k++)
+    if (mbar_test_wait(b, parity)) return true;
+    for (int k = 1; k < limit; k++)
         if (mbar_try_wait(b, parity)) return true;
     return false;
 }
@@ -293,7 +311,8 @@ constexpr int WAIT_LIMIT = FUSED_WAIT_LIMIT;
 // from global memory.  Each wait for a box tries wait_limit times; if one
 // runs out the CTA stops, waits (with the full limit) for its copies in
 // flight, records the timeout in the lattice's status word and returns
-// false.  SELF: ψ of fluid nodes is formed here from the densities of the
+// false.  A negative wait_limit makes every wait one that nothing completes
+// (tests).  SELF: ψ of fluid nodes is formed here from the densities of the
 // box; otherwise psi holds ψ of every node (the density kernel's and the
 // shell fill's), and the box holds the tile only.
 template <class S, int TY, bool GEN, bool SELF, bool TMA, bool R32>
@@ -314,6 +333,11 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::P *__
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
     const int x0 = bx * TX, y0 = by * TY;
     const int zb = bz * zc, ze = min(zb + zc, L.nz);
+    // wait_limit < 0 (tests of the timeout path): every wait for a box is
+    // for the barrier's next phase, which no copy completes, with |limit|
+    // tries; the cleanup below still waits for the copies in flight
+    const unsigned unreachable = wait_limit < 0 ? 1u : 0u;
+    const int limit = wait_limit < 0 ? -wait_limit : wait_limit;
     const int nxy = L.nx * L.ny;
     const int gx = x0 + tx, gy = y0 + ty;
     const bool active = gx < L.nx && gy < L.ny;
@@ -615,8 +639,8 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::P *__
             if (more) vn = ring_load(kn);
             bool late = false;
             if (TMA) {
-                late = !mbar_wait(&bar[b], (unsigned)(waited.get(b) & 1), wait_limit);
-                waited.inc(b);
+                late = !mbar_wait(&bar[b], (unsigned)(waited.get(b) & 1) ^ unreachable, limit);
+                if (!late) waited.inc(b);
             }
             // a copy that never arrived leaves stale shared data: the
             // collision then stores garbage (at valid addresses), and the
@@ -660,8 +684,8 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::P *__
             }
             bool late = false;
             if (TMA && pv) {
-                late = !mbar_wait(&bar[b_cur], (unsigned)(waited.get(b_cur) & 1), wait_limit);
-                waited.inc(b_cur);
+                late = !mbar_wait(&bar[b_cur], (unsigned)(waited.get(b_cur) & 1) ^ unreachable, limit);
+                if (!late) waited.inc(b_cur);
             }
             if (__syncthreads_or(late)) {
                 ok = false;

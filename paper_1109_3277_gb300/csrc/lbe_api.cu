@@ -1,5 +1,6 @@
 // Host side of liblbe: context, device memory, the per-step launch
 // sequence (captured in CUDA graphs) and the C ABI of include/lbe.h.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -153,10 +154,43 @@ void free_all(lbe_ctx *c)
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
 }
 
+// Allocation-failure injection (lbe_fail_allocations): the number of device
+// allocations still allowed, or -1 for no limit.
+std::atomic<int> g_alloc_left{-1};
+
+bool alloc_refused()
+{
+    int n = g_alloc_left.load();
+    while (n >= 0) {
+        if (n == 0) return true;
+        if (g_alloc_left.compare_exchange_weak(n, n - 1)) return false;
+    }
+    return false;
+}
+
+// Every device allocation of a context goes through these two.
+cudaError_t lib_malloc(void **p, size_t bytes)
+{
+    if (alloc_refused()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t lib_malloc_async(void **p, size_t bytes, cudaStream_t s)
+{
+    if (alloc_refused()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, s);
+}
+
 template <class T>
 cudaError_t dalloc(lbe_ctx *c, T **p, size_t bytes)
 {
-    cudaError_t e = cudaMalloc((void **)p, bytes);
+    cudaError_t e = lib_malloc((void **)p, bytes);
     if (e == cudaSuccess) c->bytes += bytes;
     return e;
 }
@@ -252,42 +286,48 @@ void enqueue_step(lbe_ctx *c)
 
 // Cell list for the pair forces: cells of edge >= the largest pair reach
 // (2 max radius + Δc + the prefilter's margin), at least 2 nodes a side.
-lbe_status build_cells(lbe_ctx *c, const std::vector<double> &blk, int cap)
+// (np particles of the block blk laid out for capacity cap; on failure the
+// context keeps its old cells)
+lbe_status build_cells(lbe_ctx *c, const std::vector<double> &blk, int cap, int np)
 {
     double rmax = 0.0;
-    for (int p = 0; p < c->np; p++)
+    for (int p = 0; p < np; p++)
         rmax = std::fmax(rmax, std::fmax(blk[(size_t)ORP * cap + p], blk[(size_t)ORO * cap + p]));
     const double reach = 2.0 * rmax + c->pair.lub_cut + 0.1;
     Cells &C = c->cells;
     const int dim[3] = {c->L.nx, c->L.ny, c->L.nz};
     long long ncell = 1;
+    int cn[3];
+    float cinv[3];
     for (int k = 0; k < 3; k++) {
         int n = (int)std::floor(dim[k] / reach);
         n = std::max(1, std::min(n, dim[k] / 2));
-        C.n[k] = n;
-        C.inv[k] = (float)((double)n / dim[k]);
+        cn[k] = n;
+        cinv[k] = (float)((double)n / dim[k]);
         ncell *= n;
+    }
+    // count | start | fill in one buffer, idx | cid in another; the old
+    // buffers go only once the new ones exist
+    const size_t b0 = (size_t)(3 * ncell + 1) * sizeof(int), b1 = (size_t)2 * cap * sizeof(int);
+    int *ncount = nullptr, *nidx = nullptr;
+    cudaError_t e = lib_malloc((void **)&ncount, b0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "add_particles: cudaMalloc(cells)");
+    e = lib_malloc((void **)&nidx, b1);
+    if (e != cudaSuccess) {
+        cudaFree(ncount);
+        return cuda_fail(c, e, "add_particles: cudaMalloc(cells)");
     }
     if (C.count) {
         cudaFree(C.count);
         cudaFree(C.idx);
-        C.count = C.idx = nullptr;
         c->bytes -= c->cells_bytes;
-        c->cells_bytes = 0;
     }
-    // count | start | fill in one buffer, idx | cid in another
+    C.count = ncount;
+    C.idx = nidx;
     C.ncell = (int)ncell;
-    const size_t b0 = (size_t)(3 * ncell + 1) * sizeof(int), b1 = (size_t)2 * cap * sizeof(int);
-    cudaError_t e = cudaMalloc((void **)&C.count, b0);
-    if (e != cudaSuccess) {
-        C.count = nullptr;
-        return cuda_fail(c, e, "add_particles: cudaMalloc(cells)");
-    }
-    e = cudaMalloc((void **)&C.idx, b1);
-    if (e != cudaSuccess) {
-        cudaFree(C.count);
-        C.count = C.idx = nullptr;
-        return cuda_fail(c, e, "add_particles: cudaMalloc(cells)");
+    for (int k = 0; k < 3; k++) {
+        C.n[k] = cn[k];
+        C.inv[k] = cinv[k];
     }
     C.start = C.count + ncell;
     C.fill = C.start + ncell + 1;
@@ -419,7 +459,7 @@ lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_c
     cudaMemsetAsync(c->f[1], 0, fbytes, s);
     k_set_types<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(L, c->type);
     double *drho0 = nullptr;
-    if ((e = cudaMallocAsync((void **)&drho0, (size_t)2 * N * sizeof(double), s)) != cudaSuccess)
+    if ((e = lib_malloc_async((void **)&drho0, (size_t)2 * N * sizeof(double), s)) != cudaSuccess)
         return bail(e, "cudaMallocAsync(rho0)");
     cudaMemcpyAsync(drho0, rho0, (size_t)2 * N * sizeof(double), cudaMemcpyHostToDevice, s);
     launch_init_f(d->storage, L, drho0, c->f[0], c->type, s);
@@ -507,15 +547,35 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
         x32[ncap + 2 * p + 1] = make_float4((float)blk[OW * cp + 3 * p], (float)blk[OW * cp + 3 * p + 1],
                                             (float)blk[OW * cp + 3 * p + 2], 0.f);
     }
+    if (!c->ll.ent) {
+        // a fluid node enters the link list at most once per step: N entries
+        uint2 *ent = nullptr;
+        int *cnt = nullptr;
+        CK(c, lib_malloc((void **)&ent, (size_t)c->L.N * sizeof(uint2)));
+        cudaError_t e = lib_malloc((void **)&cnt, sizeof(int));
+        if (e != cudaSuccess) {
+            cudaFree(ent);
+            return cuda_fail(c, e, "add_particles: cudaMalloc(link list)");
+        }
+        CK(c, cudaMemset(cnt, 0, sizeof(int)));
+        c->ll.ent = ent;
+        c->ll.count = cnt;
+        c->ll.cap = c->L.N;
+        c->bytes += (size_t)c->L.N * sizeof(uint2) + sizeof(int);
+    }
+    {
+        lbe_status cst = build_cells(c, blk, ncap, np);
+        if (cst != LBE_OK) return cst;
+    }
     if (ncap != cap) {
         double *nb = nullptr;
         float4 *nx32 = nullptr;
         double *npp = nullptr;
         void *ngeo = nullptr;
-        CK(c, cudaMalloc((void **)&nb, blk.size() * sizeof(double)));
-        cudaError_t e = cudaMalloc((void **)&nx32, x32.size() * sizeof(float4));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&npp, (size_t)6 * ncap * sizeof(double));
-        if (e == cudaSuccess) e = cudaMalloc(&ngeo, (size_t)ncap * geom_bytes_per_particle());
+        CK(c, lib_malloc((void **)&nb, blk.size() * sizeof(double)));
+        cudaError_t e = lib_malloc((void **)&nx32, x32.size() * sizeof(float4));
+        if (e == cudaSuccess) e = lib_malloc((void **)&npp, (size_t)6 * ncap * sizeof(double));
+        if (e == cudaSuccess) e = lib_malloc(&ngeo, (size_t)ncap * geom_bytes_per_particle());
         if (e != cudaSuccess) {
             cudaFree(nb);
             cudaFree(nx32);
@@ -538,20 +598,11 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
         c->cap = ncap;
         c->bytes += (size_t)ncap * per_cap;
     }
-    if (!c->ll.ent) {
-        // a fluid node enters the link list at most once per step: N entries
-        CK(c, dalloc(c, &c->ll.ent, (size_t)c->L.N * sizeof(uint2)));
-        CK(c, dalloc(c, &c->ll.count, sizeof(int)));
-        CK(c, cudaMemset(c->ll.count, 0, sizeof(int)));
-        c->ll.cap = c->L.N;
-    }
     CK(c, cudaMemcpy(c->pbuf, blk.data(), blk.size() * sizeof(double), cudaMemcpyHostToDevice));
     CK(c, cudaMemcpy(c->x32, x32.data(), x32.size() * sizeof(float4), cudaMemcpyHostToDevice));
     c->np = np;
     c->L.np = np;
     bind_parts(c);
-    lbe_status cst = build_cells(c, blk, ncap);
-    if (cst != LBE_OK) return cst;
     drop_graphs(c);
     cudaStream_t s = c->stream;
     uint32_t *oo = c->owner[c->ocur], *on = c->owner[1 - c->ocur];
@@ -605,9 +656,9 @@ lbe_status lbe_read_fields(lbe_ctx *c, double *rho, double *vel, uint8_t *node_t
     launch_moments(c->d.storage, L, c->f[c->cur], c->type, c->rho, c->psi, s);
     launch_shell(L, c->rho, c->psi, c->type, c->owner[c->ocur], c->P.drho, LinkList{nullptr, nullptr, 0}, s);
     double *dr = nullptr, *dv = nullptr;
-    if (rho) CK(c, cudaMallocAsync((void **)&dr, 2 * N * sizeof(double), s));
+    if (rho) CK(c, lib_malloc_async((void **)&dr, 2 * N * sizeof(double), s));
     if (vel) {
-        cudaError_t e = cudaMallocAsync((void **)&dv, 3 * N * sizeof(double), s);
+        cudaError_t e = lib_malloc_async((void **)&dv, 3 * N * sizeof(double), s);
         if (e != cudaSuccess) {
             if (dr) cudaFreeAsync(dr, s);
             return cuda_fail(c, e, "cudaMallocAsync(vel)");
@@ -853,13 +904,16 @@ lbe_status lbe_get_tile(const lbe_ctx *c, int32_t *rows, int32_t *zc)
     return LBE_OK;
 }
 
-lbe_status lbe_set_wait_limit(lbe_ctx *c, int32_t tries)
+void lbe_fail_allocations(int32_t after) { g_alloc_left.store(after < 0 ? -1 : after); }
+
+lbe_status lbe_set_wait_limit(lbe_ctx *c, int32_t tries, int32_t unreachable)
 {
     if (!c || tries < 0) return LBE_EINVAL;
     cudaSetDevice(c->device);
     lbe_status st = sync(c, "set_wait_limit");
     if (st != LBE_OK) return st;
-    c->wait_limit = tries > 0 ? tries : FUSED_WAIT_LIMIT;
+    const int t = tries > 0 ? tries : FUSED_WAIT_LIMIT;
+    c->wait_limit = unreachable ? -t : t;
     drop_graphs(c);
     return LBE_OK;
 }

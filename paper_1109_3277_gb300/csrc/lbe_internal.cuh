@@ -62,13 +62,46 @@ struct StF16 {
     static __device__ __forceinline__ float2 raw2(P v) { return __half22float2(v); }
     static __device__ __forceinline__ P enc2(float2 v) { return __floats2half2_rn(v.x, v.y); }
 };
+// BF16 keeps 8 significant bits.  Rounding a population's offset to nearest
+// would bias the flow: in a demixed fluid the offsets are ~0.6 w_i, whose
+// half-ulp (~1e-4) is of the order of the velocity part 3 w_i ρ c·u, and
+// the same values round the same way step after step.  The pairs are
+// therefore rounded up with probability equal to the discarded fraction
+// (unbiased): a 16-bit increment, taken from a hash of the pair's own FP32
+// bits, is added to each value's bit pattern before truncation.  The hash
+// makes the result a fixed function of the value (runs and batches stay
+// bit-identical), and over the values a node sees it acts as a uniform
+// random increment.
+__device__ __forceinline__ uint32_t mix32(uint32_t a, uint32_t b)
+{
+    uint32_t h = a * 0x9E3779B1u ^ (b + 0x7F4A7C15u) * 0x85EBCA77u;
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 12;
+    h *= 0x297A2D39u;
+    h ^= h >> 15;
+    return h;
+}
+__device__ __forceinline__ uint16_t bf16_unbiased(float v, uint32_t r16)
+{
+    const uint32_t b = __float_as_uint(v);
+    if ((b & 0x7F800000u) == 0x7F800000u) return (uint16_t)(b >> 16);  // inf, NaN: truncated
+    return (uint16_t)((b + r16) >> 16);  // carries into the exponent are the correct round-up
+}
 struct StBF16 {
     using T = __nv_bfloat16;
     using P = __nv_bfloat162;
     static __device__ __forceinline__ float raw(T v) { return __bfloat162float(v); }
     static __device__ __forceinline__ T enc(float v) { return __float2bfloat16_rn(v); }
     static __device__ __forceinline__ float2 raw2(P v) { return __bfloat1622float2(v); }
-    static __device__ __forceinline__ P enc2(float2 v) { return __floats2bfloat162_rn(v.x, v.y); }
+    static __device__ __forceinline__ P enc2(float2 v)
+    {
+        const uint32_t h = mix32(__float_as_uint(v.x), __float_as_uint(v.y));
+        __nv_bfloat162_raw r;
+        r.x = bf16_unbiased(v.x, h & 0xFFFFu);
+        r.y = bf16_unbiased(v.y, h >> 16);
+        return P(r);
+    }
 };
 
 // Lattice parameters passed by value to every kernel.

@@ -70,7 +70,8 @@ SIGNATURES = {
     "lbe_set_zchunk": (ctypes.c_int, [_P, ctypes.c_int32]),
     "lbe_set_tile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "lbe_get_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
-    "lbe_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "lbe_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "lbe_fail_allocations": (None, [ctypes.c_int32]),
     "lbe_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int32, ctypes.POINTER(_P)]),
     "lbe_batch_step": (ctypes.c_int, [_P, ctypes.c_int32]),
     "lbe_batch_autotune": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
@@ -247,9 +248,10 @@ class Lattice:
         self._check(load().lbe_get_tile(self._ptr, ctypes.byref(r), ctypes.byref(z)), "get_tile")
         return r.value, z.value
 
-    def set_wait_limit(self, tries):
-        """Tries of each bounded wait for a box copy (0: the default)."""
-        self._check(load().lbe_set_wait_limit(self._ptr, int(tries)), "set_wait_limit")
+    def set_wait_limit(self, tries, unreachable=False):
+        """Tries of each bounded wait for a box copy (0: the default);
+        unreachable: wait for a phase no copy completes (timeout tests)."""
+        self._check(load().lbe_set_wait_limit(self._ptr, int(tries), int(bool(unreachable))), "set_wait_limit")
 
     def device_bytes(self):
         return int(load().lbe_device_bytes(self._ptr))
@@ -314,6 +316,12 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def fail_allocations(after):
+    """Make the library's device allocations fail after `after` more (tests of
+    the out-of-memory paths); -1 lifts the limit."""
+    load().lbe_fail_allocations(int(after))
 
 
 def footprint(shape, nparticles=0, **params):

@@ -45,7 +45,9 @@ def test_cpu_samples_are_bounded_sub_boxes():
     from paper_1109_3277_gb300 import workloads as W
     w = W.spinodal(n=128)
     s, what = bench.cpu_sample_workload(w)
-    assert s.shape == (64, 64, 64) and "64^3" in what
+    assert s.shape == (96, 96, 96) and "96^3" in what
+    s1, what1 = bench.cpu_sample_workload("spinodal", 64)
+    assert s1.shape == (64, 64, 64) and "64^3" in what1
     a = W.adsorption_box()
     s2, what2 = bench.cpu_sample_workload(a)
     assert s2 is a and what2 == "the full workload"

@@ -30,11 +30,8 @@ def _golden():
 
 
 # Bound on the relative error of L(t) and of the interface area from step
-# 300 to 2000.  FP32 and FP16 offsets meet the 1% target (measured: FP32
-# 3e-4, FP16 0.5% / 0.05%).  BF16 offsets (8-bit mantissa) meet it up to
-# about step 850 and then coarsen slightly slower than the oracle: measured
-# 2.9% (L) and 2.1% (area) at step 2000; the bound states that.
-TOL = {"f32": (0.01, 0.01), "f16": (0.01, 0.01), "bf16": (0.035, 0.025)}
+# 300 to 2000: 1% for every storage mode.
+TOL = {"f32": (0.01, 0.01), "f16": (0.01, 0.01), "bf16": (0.01, 0.01)}
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
