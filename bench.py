@@ -54,6 +54,8 @@ def parse(argv=None):
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default=None)
     ap.add_argument("--zchunk", type=int, default=0,
                     help="fused-kernel z chunk in planes (default 0: the library's autotuner picks it)")
+    ap.add_argument("--rows", type=int, default=8, choices=[4, 8],
+                    help="fused-kernel tile rows when --zchunk fixes the tile")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true",
@@ -293,10 +295,9 @@ def run_ours(args):
     add_particles(lat, w)
     lat.step(args.warmup)
     if args.zchunk > 0:
-        lat.set_zchunk(args.zchunk)
-        zc = args.zchunk
+        lat.set_tile(args.rows, args.zchunk)
     else:
-        zc = lat.autotune()  # the library's z-chunk autotuner (CUDA events, state unchanged)
+        lat.autotune()  # the library's tile autotuner (CUDA events, state unchanged)
     rows, zc = lat.tile()
     torch.cuda.synchronize()
     lat.profile_enable(True)
