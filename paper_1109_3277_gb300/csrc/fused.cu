@@ -55,25 +55,34 @@ struct Cfg {
     static constexpr int PADX = SELF ? 16 / E : 0;    // x margin of the box: 16 bytes
     static constexpr int BX = TX + 2 * PADX, BY = SELF ? TY + 2 : TY;
     static constexpr int HX = TX + 2, HY = TY + 2, HN = HX * HY, NHALO = HN - NT;
-    // stage buffers: any τ with SELF re-reads plane z's box one iteration
-    // after its densities; every other configuration is done with a box in
-    // the iteration it arrives
-    static constexpr int NST = (GEN && SELF) ? 3 : 2;
     static constexpr size_t plane = (size_t)Q * BY * BX * E;        // bytes of one box
     static constexpr size_t pstride = (plane + 127) / 128 * 128;    // stages 128-byte aligned
-    // dynamic shared memory (bytes from a 128-byte aligned base)
-    static constexpr size_t stage = 0;                              // P [NST][Q][BY][BX]
-    static constexpr size_t sps = stage + NST * pstride;            // float2 [4][HN] (ψ_b, ψ_r)
-    static constexpr size_t smask = sps + 4 * HN * sizeof(float2);  // uint64 [4][HY] solid bits per row
-    static constexpr size_t bar = smask + 4 * HY * sizeof(unsigned long long);  // uint64 [NST] mbarriers
-    static constexpr size_t bytes = bar + NST * sizeof(unsigned long long) + 128;  // + alignment slack
     // CTAs per SM the kernel is compiled for: what shared memory allows
     // (228 KB per SM, about 1 KB of it reserved per CTA), capped so that a
     // thread keeps at least 80 registers (τ = 1: 768 threads per SM) or 128
     // (any τ: 512), which the node arithmetic needs without spilling.
-    static constexpr int by_smem = (int)((228 * 1024) / (bytes + 1024));
     static constexpr int by_regs = (GEN ? 512 : 768) / NT;
-    static constexpr int CTAS = by_smem < by_regs ? (by_smem > 0 ? by_smem : 1) : by_regs;
+    static constexpr size_t twords = SELF ? 0 : (size_t)NT * 4 * sizeof(uint32_t);  // type words in flight
+    static constexpr size_t other =
+        4 * HN * sizeof(float2) + 4 * HY * sizeof(unsigned long long) + twords + 128 + 1024;
+    static constexpr int ctas_for(int nst)
+    {
+        const int m = (int)((228 * 1024) / (nst * pstride + nst * 8 + other));
+        return m < by_regs ? (m > 0 ? m : 1) : by_regs;
+    }
+    // stage buffers: any τ with SELF re-reads plane z's box one iteration
+    // after its densities (three); otherwise a box is done with in the
+    // iteration it arrives, and a third buffer lets the copies run two
+    // planes ahead where it costs no CTA per SM
+    static constexpr int NST = (GEN && SELF) ? 3 : (SELF ? 2 : (ctas_for(3) >= ctas_for(2) ? 3 : 2));
+    static constexpr int CTAS = ctas_for(NST);
+    // dynamic shared memory (bytes from a 128-byte aligned base)
+    static constexpr size_t stage = 0;                              // P [NST][Q][BY][BX]
+    static constexpr size_t sps = stage + NST * pstride;            // float2 [4][HN] (ψ_b, ψ_r)
+    static constexpr size_t smask = sps + 4 * HN * sizeof(float2);  // uint64 [4][HY] solid bits per row
+    static constexpr size_t stw = smask + 4 * HY * sizeof(unsigned long long);  // uint32 [NT][4] type words
+    static constexpr size_t bar = stw + twords;                     // uint64 [NST] mbarriers
+    static constexpr size_t bytes = bar + NST * sizeof(unsigned long long) + 128;  // + alignment slack
 };
 
 // Per stage buffer counters kept in registers (every index a compile-time
@@ -190,19 +199,66 @@ __device__ __forceinline__ void tma_box(void *dst, const CUtensorMap *map, int x
 // (components 0 or ±1) are exact and stay plain.
 //
 // The two components go through the same node arithmetic, so it is done on
-// (red, blue) pairs with the paired FP32 instructions (add, multiply and
-// fused multiply-add on two lanes, each rounded to nearest like its scalar
-// form): every component's result has the bits of the scalar sequence.
+// (red, blue) pairs with the paired FP32 instructions (add, subtract,
+// multiply and fused multiply-add on two lanes, each rounded to nearest
+// like its scalar form; the subtraction, which has no intrinsic, in PTX):
+// every component's result has the bits of the scalar sequence.
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b)
+{
+    float2 r;
+    asm("{\n"
+        " .reg .b64 ra, rb, rd;\n"
+        " mov.b64 ra, {%2, %3};\n"
+        " mov.b64 rb, {%4, %5};\n"
+        " sub.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n"
+        "}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+struct Add2 {
+    __device__ __forceinline__ float2 operator()(float2 a, float2 b) const { return add2(a, b); }
+};
+
+// Reciprocal by the hardware approximation (PTX rcp.approx; error of the
+// order of one unit in the last place): the inverse densities of the
+// equilibrium velocity.  Like the other operations it gives the same bits
+// wherever it is inlined.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Σ_k c_{2k+1} d_k over the nine opposite pairs (2k+1, 2k+2), where d_k is
+// the quantity of direction 2k+1 minus that of 2k+2 (c_{2k+2} = -c_{2k+1}):
+// the three Cartesian components, terms added in k order as they come.
+// c_1, c_3, c_5 are the unit vectors x, y, z: each component starts there.
+__device__ __forceinline__ void odd_put(float2 out[3], int k, float2 d)
+{
+    const int i = 2 * k + 1;
+    const int c[3] = {cx(i), cy(i), cz(i)};
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        if (!c[a]) continue;
+        if (k == a)
+            out[a] = d;
+        else
+            out[a] = c[a] > 0 ? add2(out[a], d) : sub2(out[a], d);
+    }
+}
 
 // Moments of the stored quantities d_i (δf_i at 16 bit, f_i in FP32) of a
-// node: Δρ^c = Σ_i d_i in direction order and j^c = Σ_i c_i d_i (the bases
-// w_i ρ_ref cancel in j, since Σ_i w_i c_i = 0).  ld(i) gives the (red,
-// blue) pair of direction i.
+// node: Δρ^c = Σ_i d_i (in the order of PairTree) and j^c = Σ_i c_i
+// d_i (the bases w_i ρ_ref cancel in j, since Σ_i w_i c_i = 0).  ld(i)
+// gives the (red, blue) pair of direction i.
 struct Mom {
     float2 dr;     // Δρ = ρ - ρ_ref (ρ itself in FP32)
     float2 j[3];
@@ -212,59 +268,63 @@ template <class LD>
 __device__ __forceinline__ Mom moments(LD ld)
 {
     Mom m;
-    float2 a = ld(0), jj[3] = {dup2(0.f), dup2(0.f), dup2(0.f)};
+    PairTree t;
 #pragma unroll
-    for (int i = 1; i < Q; i += 2) {
-        // one pass over opposite pairs (i, i+1), c_{i+1} = -c_i; the sum
-        // accumulates in index order
-        const float2 va = ld(i), vb = ld(i + 1);
-        a = add2(a, va);
-        a = add2(a, vb);
-        const float2 d = sub2(va, vb);
-        if (cx(i)) jj[0] = cx(i) > 0 ? add2(jj[0], d) : sub2(jj[0], d);
-        if (cy(i)) jj[1] = cy(i) > 0 ? add2(jj[1], d) : sub2(jj[1], d);
-        if (cz(i)) jj[2] = cz(i) > 0 ? add2(jj[2], d) : sub2(jj[2], d);
+    for (int k = 0; k < 9; k++) {
+        const float2 va = ld(2 * k + 1), vb = ld(2 * k + 2);
+        t.put(k, add2(va, vb), Add2{});
+        odd_put(m.j, k, sub2(va, vb));
     }
-    m.dr = a;
-    m.j[0] = jj[0];
-    m.j[1] = jj[1];
-    m.j[2] = jj[2];
+    m.dr = t.finish(ld(0), Add2{});
     return m;
 }
 
-// Σ_i d_i in direction order (a halo node needs its density only).
+// Σ_i d_i alone (a halo node needs its density only), in the same order.
 template <class LD>
 __device__ __forceinline__ float2 density_sum(LD ld)
 {
-    float2 a = ld(0);
+    PairTree t;
 #pragma unroll
-    for (int i = 1; i < Q; i++) a = add2(a, ld(i));
-    return a;
+    for (int k = 0; k < 9; k++) t.put(k, add2(ld(2 * k + 1), ld(2 * k + 2)), Add2{});
+    return t.finish(ld(0), Add2{});
 }
 
 // Equilibrium velocities of both components, u' + (τ_c/ρ_c) F^c with the
 // Shan–Chen force F^c = -g ψ^c s^c + ρ^c g_body (Eq. 3), and -1.5 u·u.
+// TAU1 (τ = 1 for both) skips the products with τ_c = 1, which are exact:
+// the same bits as the general form.
+template <bool TAU1>
 __device__ __forceinline__ void eq_velocity(const Lat &L, float2 r, float2 pc, const float2 s[3], const float up[3],
                                             float2 ue[3], float2 &um15)
 {
-    const float2 ir = make_float2(r.x > 0.f ? __fdiv_rn(L.tau[0], r.x) : 0.f,
-                                  r.y > 0.f ? __fdiv_rn(L.tau[1], r.y) : 0.f);
+    float2 ir = make_float2(r.x > 0.f ? rcp_approx(r.x) : 0.f, r.y > 0.f ? rcp_approx(r.y) : 0.f);
+    if (!TAU1) ir = mul2(make_float2(L.tau[0], L.tau[1]), ir);
     const float2 gp = mul2(dup2(-L.g), pc);
+    if (L.body[0] != 0.f || L.body[1] != 0.f || L.body[2] != 0.f) {
 #pragma unroll
-    for (int k = 0; k < 3; k++) ue[k] = fma2(ir, fma2(gp, s[k], mul2(r, dup2(L.body[k]))), dup2(up[k]));
+        for (int k = 0; k < 3; k++) ue[k] = fma2(ir, fma2(gp, s[k], mul2(r, dup2(L.body[k]))), dup2(up[k]));
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; k++) ue[k] = fma2(ir, mul2(gp, s[k]), dup2(up[k]));
+    }
     const float2 uu = fma2(ue[0], ue[0], fma2(ue[1], ue[1], mul2(ue[2], ue[2])));
     um15 = mul2(dup2(-1.5f), uu);
 }
 
-// f^eq_i = w_i ρ (1 + 3 c·u + 4.5 (c·u)^2 - 1.5 u·u) relative to the stored
-// quantity's base w_i ρ_ref: even part w_i (ρ (4.5 (c·u)^2 - 1.5 u·u) + Δρ)
-// with Δρ = ρ - ρ_ref (for FP32 storage ρ_ref = 0, Δρ = ρ), odd part
-// 3 w_i ρ c·u (w3r = 3 w_i ρ comes per weight).
-__device__ __forceinline__ void feq_parts(float w, float2 r, float2 dr, float2 w3r, float2 cu, float2 um15,
-                                          float2 &even, float2 &odd)
+// c_i·u for odd i: the first non-zero component of c_i is +1, the second
+// (diagonals) ±1.
+__device__ __forceinline__ float2 cu_odd(int i, const float2 ue[3])
 {
-    even = mul2(dup2(w), fma2(r, fma2(mul2(dup2(4.5f), cu), cu, um15), dr));
-    odd = mul2(w3r, cu);
+    const int c[3] = {cx(i), cy(i), cz(i)};
+    float2 r = dup2(0.f);
+    bool first = true;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        if (!c[a]) continue;
+        r = first ? ue[a] : (c[a] > 0 ? add2(r, ue[a]) : sub2(r, ue[a]));
+        first = false;
+    }
+    return r;
 }
 
 // BGK relaxation f + (f^eq - f)/τ; a component with τ = 1 takes f^eq
@@ -372,11 +432,7 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::P *__
     // collided
     const int kmax = ze - zb + 2;
     auto pvalid = [&](int p) { return !L.walls || (p >= 0 && p < L.nz); };
-    auto gz_of = [&](int p) {  // p in [-1, nz]: two wraps when nz = 1
-        int g = p < 0 ? p + L.nz : p;
-        while (g >= L.nz) g -= L.nz;
-        return g;
-    };
+    auto gz_of = [&](int p) { return p < 0 ? p + L.nz : (p >= L.nz ? p - L.nz : p); };  // p in [-1, nz]
     // per stage buffer: boxes issued (thread 0) and waited for (every thread)
     Counts<NST> issued{}, waited{};
     auto issue = [&](int k, int b) {
@@ -417,28 +473,34 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::P *__
             const Mom mcur = mom_of();
             const float2 rref2 = make_float2(L.rref[0], L.rref[1]);
             const float2 drho = mcur.dr, rho_ = add2(rref2, mcur.dr);
-            const float den = __fmaf_rn(rho_.y, L.itau[1], __fmul_rn(rho_.x, L.itau[0]));
-            const float iden = den > 0.f ? 1.f / den : 0.f;
+            // u' = Σ_c j^c/τ_c / Σ_c ρ^c/τ_c; with τ = 1 the products with
+            // 1/τ_c = 1 are exact and left out (the same bits)
+            const float den = GEN ? __fmaf_rn(rho_.y, L.itau[1], __fmul_rn(rho_.x, L.itau[0]))
+                                  : __fadd_rn(rho_.x, rho_.y);
+            const float iden = den > 0.f ? rcp_approx(den) : 0.f;
             float up[3];
 #pragma unroll
-            for (int d = 0; d < 3; d++)
-                up[d] = __fmul_rn(__fmaf_rn(mcur.j[d].y, L.itau[1], __fmul_rn(mcur.j[d].x, L.itau[0])), iden);
-            // s^c = Σ_i c_i ψ^{c'}(x + c_i): the ring holds (ψ_b, ψ_r),
-            // the partner of (red, blue)
-            float2 s[3] = {dup2(0.f), dup2(0.f), dup2(0.f)};
+            for (int d = 0; d < 3; d++) {
+                const float jt = GEN ? __fmaf_rn(mcur.j[d].y, L.itau[1], __fmul_rn(mcur.j[d].x, L.itau[0]))
+                                     : __fadd_rn(mcur.j[d].x, mcur.j[d].y);
+                up[d] = __fmul_rn(jt, iden);
+            }
+            // s^c = Σ_i c_i ψ^{c'}(x + c_i) over opposite pairs: the ring
+            // holds (ψ_b, ψ_r), the partner of (red, blue)
+            float2 s[3];
 #pragma unroll
-            for (int i = 1; i < Q; i++) {
-                const float2 pp = pl[cz(i) + 1][own.ring + cy(i) * HX + cx(i)];
-                if (cx(i)) s[0] = cx(i) > 0 ? add2(s[0], pp) : sub2(s[0], pp);
-                if (cy(i)) s[1] = cy(i) > 0 ? add2(s[1], pp) : sub2(s[1], pp);
-                if (cz(i)) s[2] = cz(i) > 0 ? add2(s[2], pp) : sub2(s[2], pp);
+            for (int k = 0; k < 9; k++) {
+                const int i = 2 * k + 1;
+                odd_put(s, k, sub2(pl[cz(i) + 1][own.ring + cy(i) * HX + cx(i)],
+                                   pl[1 - cz(i)][own.ring - cy(i) * HX - cx(i)]));
             }
             const float2 pcc = pl[1][own.ring];
             const float2 pc = make_float2(pcc.y, pcc.x);  // own (ψ_r, ψ_b)
             // solid rows around this warp's row (the same for all its
-            // lanes): a warp without any, all of whose nodes are
-            // active and none on a periodic boundary, pushes every
-            // population to its fixed offset
+            // lanes) and whether its nodes lie on a periodic boundary:
+            // mode 0 (neither, all nodes active) pushes every population to
+            // its fixed offset; mode 1 (solid neighbours) reflects where
+            // the neighbour is solid; mode 2 also wraps the push offsets
             unsigned long long mrow = 0ull;
 #pragma unroll
             for (int dz = 0; dz < 3; dz++)
@@ -447,14 +509,14 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::P *__
             const bool inner_x = x0 > 0 && x0 + TX < L.nx;
             const bool inner_y = gy > 0 && gy < L.ny - 1;
             const bool inner_z = L.walls || (z > 0 && z < L.nz - 1);
-            const bool clean = mrow == 0ull && inner_x && inner_y && inner_z;
+            const bool inner = inner_x && inner_y && inner_z;
             P *dst = fout + n;
-            auto collide = [&](auto clean_tag) {
-                constexpr bool CLEAN = decltype(clean_tag)::value;
+            auto collide = [&](auto mode_tag) {
+                constexpr int MODE = decltype(mode_tag)::value;
                 // bit (cx+1) + 3 (cy+1) + 9 (cz+1): neighbour is solid
                 uint32_t nb27 = 0;
                 int wx[2] = {0, 0}, wy[2] = {0, 0}, wz[2] = {0, 0};
-                if (!CLEAN) {
+                if (MODE >= 1) {
 #pragma unroll
                     for (int dz = 0; dz < 3; dz++)
 #pragma unroll
@@ -464,6 +526,8 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::P *__
                                 __funnelshift_r((uint32_t)m, (uint32_t)(m >> 32), (uint32_t)tx) & 7u;
                             nb27 |= f3 << (3 * (dy + 3 * dz));
                         }
+                }
+                if (MODE == 2) {
                     // push offsets of nodes on the lattice boundary wrap
                     // around the periodic axes: corrections for c = +1
                     // ([0]) and c = -1 ([1])
@@ -484,7 +548,7 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::P *__
                 // the address is a select, not a branch.
                 auto put = [&](int i, float2 fs) {
                     const P v = S::enc2(fs);
-                    if (CLEAN) {
+                    if (MODE == 0) {
                         if constexpr (R32)
                             dst[ofs.push32[i]] = v;
                         else
@@ -512,30 +576,26 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::P *__
                     return S::raw2(fin[pidx(L, i, (long long)n)]);
                 };
                 float2 ue[3], um15;
-                eq_velocity(L, rho_, pc, s, up, ue, um15);
+                eq_velocity<!GEN>(L, rho_, pc, s, up, ue, um15);
                 const float2 it = make_float2(L.itau[0], L.itau[1]);
-                // 3 w ρ per weight (axis 1/18, diagonal 1/36)
-                const float2 w3r_a = mul2(dup2(3.f * wgt(1)), rho_), w3r_d = mul2(dup2(3.f * wgt(7)), rho_);
-                float2 seq = dup2(0.f);
-                // opposite pairs share the even part of the equilibrium
+                // f^eq_i relative to the stored quantity's base w_i ρ_ref:
+                // w_i (ρ (4.5 (c·u)^2 - 1.5 u·u) + Δρ) ± 3 w_i ρ c·u for the
+                // opposite pair (i, i+1), with per weight (axis 1/18,
+                // diagonal 1/36) A = w (ρ (-1.5 u·u) + Δρ), B = 4.5 w ρ and
+                // C = 3 w ρ (Δρ = ρ, base 0 in FP32)
+                const float2 a0 = fma2(rho_, um15, drho);
+                const float2 A[2] = {mul2(dup2(wgt(1)), a0), mul2(dup2(wgt(7)), a0)};
+                const float2 B[2] = {mul2(dup2(4.5f * wgt(1)), rho_), mul2(dup2(4.5f * wgt(7)), rho_)};
+                const float2 Cp[2] = {mul2(dup2(3.f * wgt(1)), rho_), mul2(dup2(3.f * wgt(7)), rho_)};
+                const float2 Cm[2] = {mul2(dup2(-3.f * wgt(1)), rho_), mul2(dup2(-3.f * wgt(7)), rho_)};
+                float2 seq[2];  // Σ of the even parts per weight
 #pragma unroll
                 for (int i = 1; i < Q; i += 2) {
-                    // c·u with c components in {-1, 0, 1}: sums in x, y, z order
-                    float2 cu = dup2(0.f);
-                    bool first = true;
-                    auto acc = [&](int ck, float2 v) {
-                        if (!ck) return;
-                        const float2 t = ck > 0 ? v : make_float2(-v.x, -v.y);
-                        cu = first ? t : add2(cu, t);
-                        first = false;
-                    };
-                    acc(cx(i), ue[0]);
-                    acc(cy(i), ue[1]);
-                    acc(cz(i), ue[2]);
-                    float2 even, odd;
-                    feq_parts(wgt(i), rho_, drho, i < 7 ? w3r_a : w3r_d, cu, um15, even, odd);
-                    seq = add2(seq, mul2(dup2(2.f), even));
-                    float2 ra = add2(even, odd), rb = sub2(even, odd);
+                    const int wc = i < 7 ? 0 : 1;
+                    const float2 cu = cu_odd(i, ue);
+                    const float2 even = fma2(mul2(B[wc], cu), cu, A[wc]);
+                    seq[wc] = i == 1 || i == 7 ? even : add2(seq[wc], even);
+                    float2 ra = fma2(Cp[wc], cu, even), rb = fma2(Cm[wc], cu, even);
                     if (GEN) {
                         ra = relax(ldf(i), ra, it);
                         rb = relax(ldf(i + 1), rb, it);
@@ -543,24 +603,32 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::P *__
                     put(i, ra);
                     put(i + 1, rb);
                 }
-                // rest population: equilibrium Δρ - Σ_{i>0} f^eq_i in the
-                // stored quantity (exact mass)
-                float2 r0 = sub2(drho, seq);
+                // rest population: Δρ - Σ_{i>0} f^eq_i in the stored
+                // quantity, so that the equilibria carry the node's mass
+                float2 r0 = fma2(dup2(-2.f), add2(seq[0], seq[1]), drho);
                 if (GEN) r0 = relax(ldf(0), r0, it);
                 dst[0] = S::enc2(r0);
             };
-            if (clean)
-                collide(std::true_type{});
+            if (inner && mrow == 0ull)
+                collide(std::integral_constant<int, 0>{});
+            else if (inner)
+                collide(std::integral_constant<int, 1>{});
             else
-                collide(std::false_type{});
+                collide(std::integral_constant<int, 2>{});
         } else if (active) {
             // A solid node's populations are never read (a node that a
             // particle uncovers gets f^eq in all slots), but writing them
             // keeps every sector of the output fully written: a partly
             // written sector costs a DRAM read when it leaves L2.
             P *d0 = fout + n;
+            const P zero = S::enc2(make_float2(0.f, 0.f));
 #pragma unroll
-            for (int i = 0; i < Q; i++) d0[ofs.pop[i]] = S::enc2(make_float2(0.f, 0.f));
+            for (int i = 0; i < Q; i++) {
+                if constexpr (R32)
+                    d0[ofs.pop32[i]] = zero;
+                else
+                    d0[ofs.pop[i]] = zero;
+            }
         }
     };
 
@@ -571,46 +639,62 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::P *__
     }
     bool ok = true;
     if constexpr (!SELF) {
-        // Without SELF the ring runs two planes ahead of the collision:
-        // while plane z collides, the entries of plane z + 2 are loaded into
-        // registers; they go into the ring after the collision.  Each warp
-        // puts whole ring rows (its own row, with the side entries taken by
-        // lanes 30 and 31; warps 0 and 1 also the halo rows 0 and TY + 1,
-        // two entries for lanes 0 and 1), so it forms their solid bits with
-        // ballots and one lane writes each row's word: one barrier per plane,
-        // at its end, which also gathers the copy timeouts.  The own node's
-        // moments come from the box of plane z at the collision.
+        // Without SELF the ring runs two planes ahead of the collision: the
+        // entries of plane z + 2 are copied into their ring slot (which the
+        // collision of plane z does not read) by asynchronous copies issued
+        // before the collision and waited for after it, so that their
+        // latency is hidden behind it: ψ straight into the slot, the 32-bit
+        // word holding each entry's node type into per-thread scratch.  Each
+        // warp puts whole ring rows (its own row, with the side entries
+        // taken by lanes 30 and 31; warps 0 and 1 also the halo rows 0 and
+        // TY + 1, two entries for lanes 0 and 1), so after the wait it forms
+        // their solid bits with ballots and one lane writes each row's word:
+        // one barrier per plane, at its end, which also makes the copies
+        // visible and gathers the copy timeouts.  The own node's moments
+        // come from the box of plane z at the collision.
         const int lane = tx, warp = ty;
         const bool has_a = warp < 2, has_b = warp < 2 && lane < 2, has_c = lane >= 30;
         const int hrow = warp == 0 ? 0 : TY + 1;
         const Ent ha = make_ent(lane, hrow), hb = make_ent(lane + 32, hrow);
         const Ent hc = make_ent(lane == 30 ? 0 : HX - 1, warp + 1);
-        struct Vals {
-            uint8_t t0, ta, tb, tc;
-            float2 p0, pa, pb, pc;
+        uint32_t *tw = reinterpret_cast<uint32_t *>(smem + C::stw) + 4 * tid;  // own, a, b, c
+        auto cp4 = [](void *dst, const void *src) {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
         };
-        auto ring_load = [&](int k) {
-            Vals v;
-            v.t0 = load_type(k, own);
-            v.p0 = load_psi(k, own, v.t0);
-            v.ta = has_a ? load_type(k, ha) : WALL;
-            v.pa = has_a ? load_psi(k, ha, v.ta) : dup2(0.f);
-            v.tb = has_b ? load_type(k, hb) : WALL;
-            v.pb = has_b ? load_psi(k, hb, v.tb) : dup2(0.f);
-            v.tc = has_c ? load_type(k, hc) : WALL;
-            v.pc = has_c ? load_psi(k, hc, v.tc) : dup2(0.f);
-            return v;
-        };
-        auto ring_put = [&](int slot, const Vals &v) {
+        auto ring_fetch = [&](int k, int slot) {
+            const int p = zb - 1 + k;
+            const bool pv = pvalid(p);
+            const size_t g = pv ? (size_t)nxy * gz_of(p) : 0;
             float2 *ps = sps + slot * HN;
-            ps[own.ring] = make_float2(v.p0.y, v.p0.x);  // (ψ_b, ψ_r): the partner first
-            if (has_a) ps[ha.ring] = make_float2(v.pa.y, v.pa.x);
-            if (has_b) ps[hb.ring] = make_float2(v.pb.y, v.pb.x);
-            if (has_c) ps[hc.ring] = make_float2(v.pc.y, v.pc.x);
-            const unsigned bo = __ballot_sync(0xffffffffu, v.t0 != FLUID);
-            const unsigned ba = __ballot_sync(0xffffffffu, v.ta != FLUID);
-            const unsigned bb = __ballot_sync(0xffffffffu, has_b && v.tb != FLUID);
-            const unsigned bc = __ballot_sync(0xffffffffu, has_c && v.tc != FLUID);
+            auto one = [&](const Ent &e, int q) {
+                float2 *d = ps + e.ring;
+                if (!pv) {  // beyond a wall: solid, ψ = 0
+                    *d = dup2(0.f);
+                    tw[q] = 0x01010101u * WALL;
+                    return;
+                }
+                const size_t n = e.xy + g;
+                cp4(&d->x, psi + (size_t)L.N + n);  // (ψ_b, ψ_r): the partner first
+                cp4(&d->y, psi + n);
+                cp4(&tw[q], reinterpret_cast<const void *>(reinterpret_cast<uintptr_t>(type + n) & ~uintptr_t(3)));
+            };
+            one(own, 0);
+            if (has_a) one(ha, 1);
+            if (has_b) one(hb, 2);
+            if (has_c) one(hc, 3);
+        };
+        auto ring_masks = [&](int k, int slot) {
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            const int p = zb - 1 + k;
+            const size_t g = pvalid(p) ? (size_t)nxy * gz_of(p) : 0;
+            auto solid = [&](const Ent &e, int q) {
+                const unsigned sh = 8u * (unsigned)(reinterpret_cast<uintptr_t>(type + e.xy + g) & 3u);
+                return ((tw[q] >> sh) & 0xFFu) != FLUID;
+            };
+            const unsigned bo = __ballot_sync(0xffffffffu, solid(own, 0));
+            const unsigned ba = __ballot_sync(0xffffffffu, has_a && solid(ha, 1));
+            const unsigned bb = __ballot_sync(0xffffffffu, has_b && solid(hb, 2));
+            const unsigned bc = __ballot_sync(0xffffffffu, has_c && solid(hc, 3));
             if (lane == 0) {
                 smask[slot * C::HY + warp + 1] = ((unsigned long long)bo << 1) | ((bc >> 30) & 1u) |
                                                  ((unsigned long long)((bc >> 31) & 1u) << 33);
@@ -626,17 +710,24 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::P *__
             issued.inc(b);
         };
         __syncthreads();  // barriers initialised
-        issue_z(zb, 0);
+        // plane zb + j arrives in stage buffer j mod NST; the copies run
+        // NST - 1 planes ahead
+#pragma unroll
+        for (int q = 0; q + 1 < NST; q++)
+            if (zb + q < ze) issue_z(zb + q, q);
         // ring planes zb - 1, zb, zb + 1 (index k = plane - zb + 1)
-        for (int k = 0; k < 3; k++) ring_put(k, ring_load(k));
+        for (int k = 0; k < 3; k++) {
+            ring_fetch(k, k);
+            ring_masks(k, k);
+        }
         __syncthreads();
+        int b = 0;
         for (int j = 0; j < ze - zb; j++) {
-            const int z = zb + j, b = j & 1;
-            if (z + 1 < ze) issue_z(z + 1, b ^ 1);
+            const int z = zb + j;
+            const int b_ahead = b == 0 ? NST - 1 : b - 1;  // (j + NST - 1) mod NST
+            if (z + NST - 1 < ze) issue_z(z + NST - 1, b_ahead);
             const int kn = j + 3;  // ring index of plane z + 2
-            const bool more = kn < kmax;
-            Vals vn{};
-            if (more) vn = ring_load(kn);
+            if (kn < kmax) ring_fetch(kn, kn & 3);
             bool late = false;
             if (TMA) {
                 late = !mbar_wait(&bar[b], (unsigned)(waited.get(b) & 1) ^ unreachable, limit);
@@ -651,7 +742,8 @@ __device__ __forceinline__ bool fused_tile(const Lat &L, const typename S::P *__
                 const size_t n = own.xy + (size_t)nxy * z;
                 return moments([&](int i) { return S::raw2(fin[pidx(L, i, (long long)n)]); });
             });
-            if (more) ring_put(kn & 3, vn);
+            if (kn < kmax) ring_masks(kn, kn & 3);
+            b = b + 1 == NST ? 0 : b + 1;
             if (__syncthreads_or(late)) {
                 ok = false;
                 break;

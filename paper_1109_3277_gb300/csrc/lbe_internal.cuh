@@ -144,20 +144,54 @@ __device__ __forceinline__ void st2f(typename S::P *f, const Lat &L, int i, long
     f[pidx(L, i, n)] = S::enc2(make_float2(v.x - L.base[0][i], v.y - L.base[1][i]));
 }
 
+// The order in which a node's 19 stored quantities are summed: the nine
+// opposite pairs p_k = d_{2k+1} + d_{2k+2} first, then a balanced tree
+// ((p0 + p1) + (p2 + p3)) + ((p4 + p5) + (p6 + p7)) + (p8 + d0), each
+// addition rounded to nearest per component.  Every kernel that sums a
+// node's populations (the density kernel, the shell fill, the fused
+// kernel's moments) takes this order, so they agree bit for bit; the tree
+// keeps the chain of dependent additions five deep.  The pair sums are fed
+// in k order as they are formed (put), so that few stay live.
+struct FaddLanes {
+    __device__ __forceinline__ float2 operator()(float2 a, float2 b) const
+    {
+        return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
+    }
+};
+struct PairTree {
+    float2 h, a, b;
+    template <class ADD>
+    __device__ __forceinline__ void put(int k, float2 p, ADD add)
+    {
+        if (k == 0 || k == 2 || k == 4 || k == 6 || k == 8) {
+            h = p;
+            return;
+        }
+        const float2 q = add(h, p);
+        if (k == 1) a = q;
+        if (k == 3) a = add(a, q);
+        if (k == 5) b = q;
+        if (k == 7) b = add(b, q);
+    }
+    template <class ADD>
+    __device__ __forceinline__ float2 finish(float2 d0, ADD add) const
+    {
+        return add(add(a, b), add(h, d0));
+    }
+};
+
 // Densities (ρ^red, ρ^blue) of node n from its stored populations: the
-// stored quantities summed in direction order, then ρ_ref added (0 in
+// stored quantities summed in the order above, then ρ_ref added (0 in
 // FP32).  Every kernel that needs a node's density from memory takes it
-// from here, so they agree bit for bit.
+// from here.
 template <class S>
 __device__ __forceinline__ float2 node_rho2(const typename S::P *__restrict__ f, const Lat &L, long long n)
 {
-    float2 a = S::raw2(f[pidx(L, 0, n)]);
+    PairTree t;
 #pragma unroll
-    for (int i = 1; i < Q; i++) {
-        const float2 v = S::raw2(f[pidx(L, i, n)]);
-        a.x = __fadd_rn(a.x, v.x);
-        a.y = __fadd_rn(a.y, v.y);
-    }
+    for (int k = 0; k < 9; k++)
+        t.put(k, FaddLanes{}(S::raw2(f[pidx(L, 2 * k + 1, n)]), S::raw2(f[pidx(L, 2 * k + 2, n)])), FaddLanes{});
+    const float2 a = t.finish(S::raw2(f[pidx(L, 0, n)]), FaddLanes{});
     return make_float2(__fadd_rn(L.rref[0], a.x), __fadd_rn(L.rref[1], a.y));
 }
 
