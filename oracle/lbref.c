@@ -645,7 +645,15 @@ void lbref_pair_hertz(double k_hertz, double rp, double ro, const double r[3], c
  * lubrication correction of Eq. 9 with 2R replaced by σ and R^2 by (σ/2)^2,
  * μ = lub_rho ν, ν = (mean τ - 1/2)/3, only for gaps 0 < r - σ < Δc, and
  * signed so that it opposes the normal approach velocity.  Two particles of
- * different shape interact with the mean of their radii. */
+ * different shape interact with the mean of their radii.
+ *
+ * Reading (the paper does not say how its explicit update treats Eq. 9):
+ * the coefficient γ = K (1/h - 1/Δc) of the normal relative velocity is
+ * capped at the pair's reduced mass M_i M_j / (M_i + M_j).  One update
+ * (Δt = 1) changes the normal approach speed by γ/M_red times itself, so at
+ * the cap the correction removes the approach in one step; above it the
+ * 1/h growth at small gaps would reverse the approach with a larger speed
+ * each step and the pair would fly apart. */
 static void phase_pairs(lbref_ctx *c)
 {
     for (int p = 0; p < c->np; p++)
@@ -677,7 +685,10 @@ static void phase_pairs(lbref_ctx *c)
                 double rh[3] = {r[0] / rl, r[1] / rl, r[2] / rl};
                 double du[3] = {A->V[0] - B->V[0], A->V[1] - B->V[1], A->V[2] - B->V[2]};
                 double K = 3.0 * M_PI * mu * sigma * sigma / 8.0;
-                double s = K * dot(rh, du) * (1.0 / h - 1.0 / c->d.lub_cut);
+                double gam = K * (1.0 / h - 1.0 / c->d.lub_cut);
+                double mred = A->M * B->M / (A->M + B->M);
+                if (gam > mred) gam = mred;
+                double s = gam * dot(rh, du);
                 for (int k = 0; k < 3; k++) {
                     A->Fpair[k] -= s * rh[k];
                     B->Fpair[k] += s * rh[k];

@@ -721,9 +721,12 @@ __device__ double hertz_bp(double K, double rp, double ro, const double r[3], co
 
 // The Hertz and lubrication (Eq. 9 with 2R -> σ, R^2 -> (σ/2)^2, only for
 // gaps 0 < r - σ < Δc, opposing the normal approach) contribution of
-// partner j to particle i.  A pair is evaluated in FP64 only when the FP32
-// distance of the centres is within reach_i + reach_j + Δc (+0.05 for the
-// FP32 error).
+// partner j to particle i.  The lubrication coefficient K (1/h - 1/Δc) is
+// capped at the pair's reduced mass M_i M_j / (M_i + M_j): at the cap one
+// update (Δt = 1) removes the normal approach speed; above it the explicit
+// update would reverse the approach with growing speed as h -> 0.  A pair
+// is evaluated in FP64 only when the FP32 distance of the centres is within
+// reach_i + reach_j + Δc (+0.05 for the FP32 error).
 
 __device__ void pair_term(const Lat &L, const Parts &P, const Pair &pp, int i, int j, const double oi[3],
                           double F[3], double T[3])
@@ -748,7 +751,10 @@ __device__ void pair_term(const Lat &L, const Parts &P, const Pair &pp, int i, i
         double rh[3] = {r[0] / rl, r[1] / rl, r[2] / rl};
         double du[3] = {P.V[3 * a] - P.V[3 * b], P.V[3 * a + 1] - P.V[3 * b + 1], P.V[3 * a + 2] - P.V[3 * b + 2]};
         double K = 3.0 * M_PI * pp.mu * sigma * sigma / 8.0;
-        double s = K * dot3(rh, du) * (1.0 / h - 1.0 / pp.lub_cut);
+        double gam = K * (1.0 / h - 1.0 / pp.lub_cut);
+        const double mred = P.M[a] * P.M[b] / (P.M[a] + P.M[b]);
+        if (gam > mred) gam = mred;
+        double s = gam * dot3(rh, du);
         for (int k = 0; k < 3; k++) F[k] += i == a ? -s * rh[k] : s * rh[k];
     }
 }

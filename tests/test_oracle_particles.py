@@ -344,6 +344,40 @@ def test_lubrication_sphere_limit(gap):
     assert np.allclose(dF[:, 1:], 0.0, atol=1e-14)
 
 
+def test_lubrication_capped_at_reduced_mass():
+    """At a gap where the coefficient K (1/h - 1/Δc) of Eq. 9 exceeds the
+    pair's reduced mass (two spheres of radius 4 at h = 0.01: about 1,040
+    against M/2 = 134), the correction is the reduced mass times the normal
+    approach speed, so one update (Δt = 1) removes the approach (reading:
+    the cap keeps the explicit update from reversing the approach with a
+    growing speed).  Two spheres started a little further apart, at h =
+    0.03, close in without flying apart."""
+    R, tau, rho_bar, cut = 4.0, 0.8, 1.4, 2.0 / 3.0
+    n = (32, 16, 16)
+    rho0 = np.zeros((2, 16, 16, 32))
+    rho0[0] = 1.0
+    v, xa, gap = 0.01, 10.0, 0.01
+    M = 4.0 / 3.0 * np.pi * R ** 3
+    F = []
+    for c in (cut, 0.0):
+        L = lbref.Lattice(n, rho0, g_br=0.0, tau=(tau, tau), particle_mode=1, lub_cut=c, lub_rho=rho_bar)
+        L.add_particles([[xa, 8.0, 8.0], [xa + 2 * R + gap, 8.0, 8.0]], [[1.0, 0, 0, 0]] * 2, R, R, 0.0,
+                        vel=[[v, 0, 0], [-v, 0, 0]])
+        L.step(1)
+        F.append(L.read_particles()["force"])
+    dF = F[0] - F[1]
+    assert dF[0, 0] == pytest.approx(-0.5 * M * 2 * v, rel=1e-10)
+    assert dF[1, 0] == pytest.approx(0.5 * M * 2 * v, rel=1e-10)
+    L = lbref.Lattice(n, rho0, g_br=0.0, tau=(tau, tau), particle_mode=1, lub_cut=cut, lub_rho=rho_bar)
+    L.add_particles([[xa, 8.0, 8.0], [xa + 2 * R + 0.03, 8.0, 8.0]], [[1.0, 0, 0, 0]] * 2, R, R, 0.0,
+                    vel=[[v, 0, 0], [-v, 0, 0]])
+    for _ in range(8):
+        L.step(1)
+        p = L.read_particles()
+        assert np.all(np.abs(p["vel"]) <= 2 * v)
+    assert p["pos"][1, 0] - p["pos"][0, 0] > 2 * R - 0.1
+
+
 @pytest.mark.parametrize("drho", [0.15, -0.15])
 def test_colour_rule_sign(drho):
     """The colour rule of §2: Δρ > 0 adds red density to the particle's
