@@ -297,18 +297,21 @@ def adsorption_study_box(tilt_deg, seed=1116, edge=64, r_par=12.0, r_perp=6.0, d
 
 def bijel_study_box(concentration, seed=1117, n=256, r_par=8.0, r_perp=4.0, g_br=0.08, steps=20000):
     """Domain size against particle concentration (§4): an n^3 periodic box
-    of random red- or blue-rich nodes (fluid ratio 1:1), g = 0.08, and
-    prolate ellipsoids of aspect ratio r_par / r_perp = 2 with Δρ = 0
-    (Θ = 90°) placed by random sequential addition to the volume fraction
-    ``concentration``.  The placement keeps half a node between particles,
-    so that random sequential addition still reaches C = 0.24 (with a whole
-    node it stalls near 0.18); the concentration reached is the number
-    placed times the particle volume over n^3."""
+    with random initial densities, g = 0.08, and prolate ellipsoids of
+    aspect ratio r_par / r_perp = 2 with Δρ = 0 (Θ = 90°) placed by random
+    sequential addition to the volume fraction ``concentration``.  Each
+    node's two densities are independent and uniform in [0, 1.4) (fluid
+    ratio 1:1, mean 0.7 per component as in the spinodal start): at g =
+    0.08 this mixture separates, while nodes that are red- or blue-rich at
+    0.7 / 0.04 (mean 0.37) stay mixed.  The placement keeps half a node
+    between particles, so that random sequential addition still reaches C =
+    0.24 (with a whole node it stalls near 0.18); the concentration reached
+    is the number placed times the particle volume over n^3."""
     shape = (n, n, n)
     vol = 4.0 / 3.0 * np.pi * r_par * r_perp * r_perp
     count = int(round(concentration * n ** 3 / vol))
     pos, quat = place_ellipsoids(shape, count, r_par, r_perp, seed, margin=0.5)
+    rho0 = uniform(seed, (2, n, n, n), stream=7, lo=0.0, hi=1.4)
     return Workload(f"bijel-study-{n}^3-C{concentration:g}-{len(pos)}prolate", shape,
-                    dict(walls_z=False, tau=(1.0, 1.0), g_br=g_br, rho_ref=(0.37, 0.37)),
-                    random_phases(shape, 0.5, seed=seed), steps,
-                    _particles(pos, quat, r_par, r_perp, 0.0), storage="f16")
+                    dict(walls_z=False, tau=(1.0, 1.0), g_br=g_br, rho_ref=(0.7, 0.7)),
+                    rho0, steps, _particles(pos, quat, r_par, r_perp, 0.0), storage="f16")

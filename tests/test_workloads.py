@@ -76,3 +76,6 @@ def test_study_recipes():
     vol = 4.0 / 3.0 * np.pi * 8.0 * 4.0 * 4.0
     assert len(b.particles["pos"]) == int(round(0.2 * 64 ** 3 / vol))
     assert b.params["g_br"] == 0.08 and not b.params["walls_z"]
+    # random initial densities, 1:1, uniform in [0, 1.4) per component
+    assert b.rho0.min() >= 0.0 and b.rho0.max() < 1.4
+    assert np.allclose(b.rho0.reshape(2, -1).mean(axis=1), 0.7, atol=0.01)
