@@ -87,6 +87,8 @@ typedef struct {
     void   *cuda_stream;     /* cudaStream_t to enqueue on (of the chosen device), or NULL */
     int32_t device;          /* CUDA device ordinal; -1 = the library's current device */
     int32_t flags;           /* 0, or LBE_FLAG_TWO_PASS | LBE_FLAG_WIDE_OFFSETS */
+    double  rho_particle;    /* particle mass density (mass ρ_p times the ellipsoid's volume,
+                                solid-ellipsoid inertia); the paper gives none; 0 means 1 */
 } lbe_lattice_desc;
 
 /* Run the fluid update as two passes (densities and ψ of every node to

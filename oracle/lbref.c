@@ -371,7 +371,7 @@ int lbref_add_particles(lbref_ctx *c, int32_t n, const double *pos, const double
         P->drho = delta_rho[k];
         /* Reading: particle density 1, solid-ellipsoid inertia about the
          * symmetry axis (0.4 M ro^2) and across it (0.2 M (rp^2 + ro^2)). */
-        P->M = 4.0 / 3.0 * M_PI * P->rp * P->ro * P->ro;
+        P->M = (c->d.rho_particle > 0 ? c->d.rho_particle : 1.0) * 4.0 / 3.0 * M_PI * P->rp * P->ro * P->ro;
         P->Ipar = 0.4 * P->M * P->ro * P->ro;
         P->Iperp = 0.2 * P->M * (P->rp * P->rp + P->ro * P->ro);
     }

@@ -43,6 +43,7 @@ typedef struct {
     void   *cuda_stream;       /* unused by the oracle */
     int32_t device;            /* unused by the oracle */
     int32_t flags;             /* unused by the oracle */
+    double  rho_particle;      /* particle mass density (0 means 1): mass ρ_p times volume */
 } lbref_lattice_desc;
 
 /* Create a lattice with populations at rest-equilibrium f_i = w_i rho0 (Eq. 2

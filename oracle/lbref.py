@@ -60,6 +60,7 @@ class LatticeDesc(ctypes.Structure):
         ("cuda_stream", ctypes.c_void_p),
         ("device", ctypes.c_int32),
         ("flags", ctypes.c_int32),
+        ("rho_particle", ctypes.c_double),
     ]
 
 
@@ -117,7 +118,7 @@ def _f64(a, shape=None):
 
 def make_desc(shape, walls_z=False, tau=(1.0, 1.0), g_br=0.1, body_force=(0.0, 0.0, 0.0),
               rho_ref=(0.7, 0.7), particle_mode=0, k_hertz=100.0, lub_cut=2.0 / 3.0, lub_rho=1.4,
-              **_ignored):
+              rho_particle=1.0, **_ignored):
     nx, ny, nz = shape
     d = LatticeDesc()
     d.nx, d.ny, d.nz = nx, ny, nz
@@ -135,6 +136,7 @@ def make_desc(shape, walls_z=False, tau=(1.0, 1.0), g_br=0.1, body_force=(0.0, 0
     d.cuda_stream = None
     d.device = -1
     d.flags = 0
+    d.rho_particle = rho_particle
     return d
 
 

@@ -378,6 +378,7 @@ lbe_status lbe_init_lattice(const lbe_lattice_desc *d, const double *rho0, lbe_c
     if (d->storage < LBE_STORE_F32 || d->storage > LBE_STORE_F16_OFS) return LBE_EINVAL;
     if (d->particle_mode < 0 || d->particle_mode > 2) return LBE_EINVAL;
     if (d->flags & ~(LBE_FLAG_TWO_PASS | LBE_FLAG_WIDE_OFFSETS)) return LBE_EINVAL;
+    if (!(d->rho_particle >= 0) || !(d->rho_particle < 1e30)) return LBE_EINVAL;
     long long N = (long long)d->nx * d->ny * d->nz;
     if (N > 0x7fffffffLL) return LBE_EINVAL;
     if (d->ny > 65535 || d->nz > 65535) return LBE_EINVAL;  // launch-grid rows and planes
@@ -523,8 +524,10 @@ lbe_status lbe_add_particles(lbe_ctx *c, int32_t n, const double *pos, const dou
         }
         for (int j = 0; j < 4; j++) blk[OQ * cp + 4 * p + j] = quat[4 * k + j] / qn;
         double rp = r_par[k], ro = r_perp[k];
-        // reading: particle density 1; solid-ellipsoid inertia
-        double M = 4.0 / 3.0 * M_PI * rp * ro * ro;
+        // mass density ρ_p of the descriptor (the paper gives none; 0 means
+        // 1), solid-ellipsoid inertia
+        const double rho_p = c->d.rho_particle > 0 ? c->d.rho_particle : 1.0;
+        double M = rho_p * 4.0 / 3.0 * M_PI * rp * ro * ro;
         blk[ORP * cp + p] = rp;
         blk[ORO * cp + p] = ro;
         blk[ODR * cp + p] = delta_rho[k];

@@ -45,6 +45,7 @@ class LatticeDesc(ctypes.Structure):
         ("cuda_stream", ctypes.c_void_p),
         ("device", ctypes.c_int32),
         ("flags", ctypes.c_int32),
+        ("rho_particle", ctypes.c_double),
     ]
 
 
@@ -122,7 +123,7 @@ def _f64(a, shape=None):
 
 def make_desc(shape, walls_z=False, tau=(1.0, 1.0), g_br=0.1, body_force=(0.0, 0.0, 0.0),
               rho_ref=(0.37, 0.37), storage="f32", particle_mode="free", k_hertz=100.0,
-              lub_cut=2.0 / 3.0, lub_rho=1.4, stream=None, device=-1, flags=0):
+              lub_cut=2.0 / 3.0, lub_rho=1.4, stream=None, device=-1, flags=0, rho_particle=1.0):
     nx, ny, nz = shape
     d = LatticeDesc()
     d.nx, d.ny, d.nz = nx, ny, nz
@@ -140,6 +141,7 @@ def make_desc(shape, walls_z=False, tau=(1.0, 1.0), g_br=0.1, body_force=(0.0, 0
     d.cuda_stream = stream
     d.device = int(device)
     d.flags = int(flags)
+    d.rho_particle = rho_particle
     return d
 
 

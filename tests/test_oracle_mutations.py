@@ -73,7 +73,7 @@ MUTANTS = {
         [PART + "test_lubrication_sphere_limit"]),
     "lubrication without the reduced-mass cap": (
         [("if (gam > mred) gam = mred;", "", 1)],
-        [PART + "test_lubrication_capped_at_reduced_mass"]),
+        [PART + "test_lubrication_capped_at_reduced_mass[1.0]"]),
     "Hertz strength with the wrong power of sigma": (
         [("double ebar = k_hertz * pow(sbar, 2.5);", "double ebar = k_hertz * pow(sbar, 1.5);", 1)],
         [PART + "test_sphere_limit_is_hertz"]),

@@ -344,23 +344,26 @@ def test_lubrication_sphere_limit(gap):
     assert np.allclose(dF[:, 1:], 0.0, atol=1e-14)
 
 
-def test_lubrication_capped_at_reduced_mass():
+@pytest.mark.parametrize("rho_p", [1.0, 3.0])
+def test_lubrication_capped_at_reduced_mass(rho_p):
     """At a gap where the coefficient K (1/h - 1/Δc) of Eq. 9 exceeds the
     pair's reduced mass (two spheres of radius 4 at h = 0.01: about 1,040
-    against M/2 = 134), the correction is the reduced mass times the normal
-    approach speed, so one update (Δt = 1) removes the approach (reading:
-    the cap keeps the explicit update from reversing the approach with a
-    growing speed).  Two spheres started a little further apart, at h =
+    against M/2 = 134 ρ_p), the correction is the reduced mass times the
+    normal approach speed, so one update (Δt = 1) removes the approach
+    (reading: the cap keeps the explicit update from reversing the approach
+    with a growing speed).  The mass is the particle density ρ_p times the
+    sphere's volume.  Two spheres started a little further apart, at h =
     0.03, close in without flying apart."""
     R, tau, rho_bar, cut = 4.0, 0.8, 1.4, 2.0 / 3.0
     n = (32, 16, 16)
     rho0 = np.zeros((2, 16, 16, 32))
     rho0[0] = 1.0
     v, xa, gap = 0.01, 10.0, 0.01
-    M = 4.0 / 3.0 * np.pi * R ** 3
+    M = rho_p * 4.0 / 3.0 * np.pi * R ** 3
     F = []
     for c in (cut, 0.0):
-        L = lbref.Lattice(n, rho0, g_br=0.0, tau=(tau, tau), particle_mode=1, lub_cut=c, lub_rho=rho_bar)
+        L = lbref.Lattice(n, rho0, g_br=0.0, tau=(tau, tau), particle_mode=1, lub_cut=c, lub_rho=rho_bar,
+                          rho_particle=rho_p)
         L.add_particles([[xa, 8.0, 8.0], [xa + 2 * R + gap, 8.0, 8.0]], [[1.0, 0, 0, 0]] * 2, R, R, 0.0,
                         vel=[[v, 0, 0], [-v, 0, 0]])
         L.step(1)
@@ -368,7 +371,8 @@ def test_lubrication_capped_at_reduced_mass():
     dF = F[0] - F[1]
     assert dF[0, 0] == pytest.approx(-0.5 * M * 2 * v, rel=1e-10)
     assert dF[1, 0] == pytest.approx(0.5 * M * 2 * v, rel=1e-10)
-    L = lbref.Lattice(n, rho0, g_br=0.0, tau=(tau, tau), particle_mode=1, lub_cut=cut, lub_rho=rho_bar)
+    L = lbref.Lattice(n, rho0, g_br=0.0, tau=(tau, tau), particle_mode=1, lub_cut=cut, lub_rho=rho_bar,
+                      rho_particle=rho_p)
     L.add_particles([[xa, 8.0, 8.0], [xa + 2 * R + 0.03, 8.0, 8.0]], [[1.0, 0, 0, 0]] * 2, R, R, 0.0,
                     vel=[[v, 0, 0], [-v, 0, 0]])
     for _ in range(8):
