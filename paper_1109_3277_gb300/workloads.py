@@ -303,10 +303,11 @@ def bijel_study_box(concentration, seed=1117, n=256, r_par=8.0, r_perp=4.0, g_br
     node's two densities are independent and uniform in [0, 1.4) (fluid
     ratio 1:1, mean 0.7 per component as in the spinodal start): at g =
     0.08 this mixture separates, while nodes that are red- or blue-rich at
-    0.7 / 0.04 (mean 0.37) stay mixed.  The particles' mass density is 4,
-    about three times the fluid's 1.4: lighter particles (density 1 or 2)
-    made the explicit update diverge within 5,000 steps at 256^3 and C =
-    0.24 (the paper gives no particle mass).  The placement keeps half a node
+    0.7 / 0.04 (mean 0.37) stay mixed.  The particles' mass density is 8,
+    about six times the fluid's 1.4: lighter particles made the explicit
+    update diverge at 256^3 and C = 0.24 (densities 1 and 2 within 5,000
+    steps, 4 by step 9,000; 8 ran 20,000).  The paper gives no particle
+    mass.  The placement keeps half a node
     between particles, so that random sequential addition still reaches C =
     0.24 (with a whole node it stalls near 0.18); the concentration reached
     is the number placed times the particle volume over n^3."""
@@ -316,5 +317,5 @@ def bijel_study_box(concentration, seed=1117, n=256, r_par=8.0, r_perp=4.0, g_br
     pos, quat = place_ellipsoids(shape, count, r_par, r_perp, seed, margin=0.5)
     rho0 = uniform(seed, (2, n, n, n), stream=7, lo=0.0, hi=1.4)
     return Workload(f"bijel-study-{n}^3-C{concentration:g}-{len(pos)}prolate", shape,
-                    dict(walls_z=False, tau=(1.0, 1.0), g_br=g_br, rho_ref=(0.7, 0.7), rho_particle=4.0),
+                    dict(walls_z=False, tau=(1.0, 1.0), g_br=g_br, rho_ref=(0.7, 0.7), rho_particle=8.0),
                     rho0, steps, _particles(pos, quat, r_par, r_perp, 0.0), storage="f16")
