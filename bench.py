@@ -556,7 +556,7 @@ def run_domain_size(args):
         line = {"metric": "bijel domain size against particle concentration", "value": round(res["a"], 3),
                 "unit": "a of L = a/C + b", "n_gpus": world, "higher_is_better": None, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32 arithmetic, f16-offset storage",
-                "data": "synthetic (seeded random phases, RSA placement)",
+                "data": "synthetic (seeded random densities, RSA placement)",
                 "config": {"workload": f"bijel-study-{args.n or 256}^3-m2", "C": res["C"],
                            "C_placed": [round(c, 4) for c in res["C_placed"]],
                            "particles": res["particles"], "steps": 20000},
