@@ -86,8 +86,7 @@ __global__ void __launch_bounds__(256) k_moments(Lat L, const typename S::P *__r
         r0 += v.x;
         r1 += v.y;
     }
-    rho[n] = r0;
-    rho[(size_t)L.N + n] = r1;
+    st_pair(rho, n, make_float2(r0, r1));
     psi[n] = 1.f - expf(-r0);
     psi[(size_t)L.N + n] = 1.f - expf(-r1);
 }
@@ -108,8 +107,7 @@ __global__ void __launch_bounds__(256) k_rho(Lat L, const typename S::P *__restr
     const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (n >= L.N || type[n] != FLUID) return;
     const float2 r = node_rho2<S>(f, L, n);
-    rho[n] = r.x;
-    rho[(size_t)L.N + n] = r.y;
+    st_pair(rho, n, r);
     psi[n] = 1.f - expf(-r.x);
     psi[(size_t)L.N + n] = 1.f - expf(-r.y);
 }
@@ -190,8 +188,7 @@ __global__ void __launch_bounds__(256) k_rho_batch(BatchIndex B, int total)
         const int b = find_box(B.node0, B.nbox, g);
         const typename S::P *f = (const typename S::P *)bx.f[B.par[2 * b]];
         const float2 r = node_rho2<S>(f, bx.L, s.n);
-        bx.rho[s.n] = r.x;
-        bx.rho[(size_t)bx.L.N + s.n] = r.y;
+        st_pair(bx.rho, s.n, r);
         bx.psi[s.n] = 1.f - expf(-r.x);
         bx.psi[(size_t)bx.L.N + s.n] = 1.f - expf(-r.y);
     }

@@ -476,7 +476,8 @@ __global__ void __launch_bounds__(PT) k_links(Lat L, Parts P, typename S::P *__r
 #pragma unroll
             for (int c = 0; c < 2; c++) {
                 float fr = c ? fr2.y : fr2.x;
-                float C = 6.f * wgt(i) * rho[(size_t)c * L.N + m] * uc;
+                const float2 rm = ld_pair(rho, m);
+                float C = 6.f * wgt(i) * (c ? rm.y : rm.x) * uc;
                 (c ? out2.y : out2.x) = fr + C;
                 float a = -(2.f * fr + C);  // F = (2 f* + C) c_ī, c_ī = -c_i
                 float F[3] = {a * cx(i), a * cy(i), a * cz(i)};
@@ -608,8 +609,9 @@ __device__ __forceinline__ void link_entry(const Lat &L, uint2 e, bool valid, co
         // both components of slot j of the fluid node: one pair access
         typename S::P *q = fout + pidx(L, j, yf);
         const float2 fs = ld2f<S>(fout, L, j, yf);
-        const float C0 = __fmul_rn(__fmul_rn(w6, __ldg(rho + yf)), uci);
-        const float C1 = __fmul_rn(__fmul_rn(w6, __ldg(rho + (size_t)L.N + yf)), uci);
+        const float2 ry2 = __ldg(reinterpret_cast<const float2 *>(rho) + yf);
+        const float C0 = __fmul_rn(__fmul_rn(w6, ry2.x), uci);
+        const float C1 = __fmul_rn(__fmul_rn(w6, ry2.y), uci);
         *q = S::enc2(make_float2(__fadd_rn(fs.x, C0) - L.base[0][j], __fadd_rn(fs.y, C1) - L.base[1][j]));
         float a = 0.f;
         a = __fadd_rn(a, __fmaf_rn(2.f, fs.x, C0));
@@ -1242,16 +1244,27 @@ __global__ void __launch_bounds__(PT) k_reset(Lat L, Parts P, int use_old, uint3
 // list.  With the wall planes these are all the solid nodes a fluid node
 // can see.
 // The densities of the fluid neighbours come from the density kernel.
+// A particle's link entries go into the list as one contiguous segment
+// (collected in shared memory, then one reservation and a coalesced copy),
+// so that the link kernel, which walks the list in order, handles the
+// links of one particle together: their slots share cache lines.  Entries
+// beyond the buffer (very large particles) are appended directly.
+constexpr int SHELL_BUF = 1024;
+
 __global__ void __launch_bounds__(PT) k_shell_particles(Lat L, Parts P, const float *__restrict__ rho,
                                                         float *__restrict__ psi, const uint8_t *__restrict__ type,
                                                         const uint32_t *__restrict__ owner, LinkList ll)
 {
+    __shared__ uint2 buf[SHELL_BUF];
+    __shared__ int nbuf, base;
     const int p = blockIdx.x;
     const PGeom &G = reinterpret_cast<const PGeom2 *>(P.geo)[p].now;
     const Box &box = G.box;
     const Geo &geo = G.g;
     const double *sX = G.X;
     const float dr = (float)P.drho[p];
+    if (threadIdx.x == 0) nbuf = 0;
+    __syncthreads();
     for_candidates(box, geo, sX, [&](int ux, int u1, int u2, bool valid) {
         int n = 0;
         uint32_t fm = 0;
@@ -1261,8 +1274,25 @@ __global__ void __launch_bounds__(PT) k_shell_particles(Lat L, Parts P, const fl
             if (owner[n] == (uint32_t)p)
                 fm = shell_fill(L, rho, psi, type, n, dr, [&](int i) { return nbr_node(L, x, y, z, i); });
         }
-        if (ll.ent) append_links(ll, n, fm);
+        if (!ll.ent) return;
+        const unsigned want = __ballot_sync(0xffffffffu, fm != 0);
+        if (!want) return;
+        const int lane = threadIdx.x & 31, leader = __ffs(want) - 1;
+        int k0 = 0;
+        if (lane == leader) k0 = atomicAdd(&nbuf, __popc(want));
+        k0 = __shfl_sync(0xffffffffu, k0, leader);
+        const int k = k0 + __popc(want & ((1u << lane) - 1u));
+        const bool spill = fm != 0 && k >= SHELL_BUF;
+        if (fm && !spill) buf[k] = make_uint2((unsigned)n, fm);
+        append_links(ll, n, spill ? fm : 0u);
     });
+    if (!ll.ent) return;
+    __syncthreads();
+    const int cnt = min(nbuf, SHELL_BUF);
+    if (threadIdx.x == 0) base = cnt ? atomicAdd(ll.count, cnt) : 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x)
+        if (base + k < ll.cap) ll.ent[base + k] = buf[k];
 }
 
 // Shell fill of the wall planes z = 0 and nz - 1 (Δρ = 0), with the
