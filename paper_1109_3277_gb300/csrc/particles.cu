@@ -547,98 +547,139 @@ __device__ __forceinline__ void warp_add_fix(int p, const unsigned long long v[6
     for (int k = 0; k < 6; k++) atomicAdd(&fix[6 * p + k], tot[k]);
 }
 
-// One particle node (e = (node, mask of fluid neighbours)); valid = false
-// for a lane without an entry (it still takes part in the warp reduction).
-template <class S>
-__device__ __forceinline__ void link_entry(const Lat &L, uint2 e, bool valid, const float *__restrict__ rho,
-                                           const uint32_t *__restrict__ owner, const float4 *__restrict__ X32,
-                                           const float4 *__restrict__ K32, unsigned long long *fix,
-                                           typename S::P *fout)
+// c_j for a direction j known only at run time (a lane's link): 2-bit
+// fields c + 1 of the components, j = 0..18.
+constexpr unsigned long long pack_dir(int axis)
 {
-    unsigned long long acc[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+    unsigned long long v = 0;
+    for (int j = 0; j < Q; j++)
+        v |= (unsigned long long)((axis == 0 ? cx(j) : (axis == 1 ? cy(j) : cz(j))) + 1) << (2 * j);
+    return v;
+}
+constexpr unsigned long long CXP = pack_dir(0), CYP = pack_dir(1), CZP = pack_dir(2);
+__device__ __forceinline__ int cdir(unsigned long long pack, int j) { return (int)((pack >> (2 * j)) & 3ull) - 1; }
+
+// Per warp of the link kernels: the links of its 32 list entries in
+// direction-major order, (entry lane, direction) per link.
+struct LinkWarp {
+    uint16_t desc[32 * (Q - 1)];
+    unsigned bal[Q];
+    int pre[Q];
+};
+
+// The links of 32 list entries (e = (node, mask of fluid neighbours) per
+// lane; valid = false for a lane without an entry).  The entries' links
+// are laid out direction by direction, so that lanes taking neighbouring
+// links touch the same slot array at neighbouring nodes, and handed out 32
+// at a time: every lane carries one link per round, and the loads of a
+// round are all in flight together.  Called by all 32 lanes.
+template <class S>
+__device__ __forceinline__ void link_entries(const Lat &L, uint2 e, bool valid, const float *__restrict__ rho,
+                                             const uint32_t *__restrict__ owner, const float4 *__restrict__ X32,
+                                             const float4 *__restrict__ K32, unsigned long long *fix,
+                                             typename S::P *fout, LinkWarp &w)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     uint32_t fm = valid ? e.y : 0u;
     const int s = valid ? (int)e.x : 0;
     int p = -1;
-    float4 X = make_float4(0.f, 0.f, 0.f, 0.f), V = X, W = X;
     if (fm) {
         p = (int)owner[s];
         if ((unsigned)p >= (unsigned)L.np) {  // a particle node is always owned
             idx_ok(L, p, L.np, 20);
             p = -1;
             fm = 0;
-        } else {
-            X = X32[p];
-            V = K32[2 * p];
-            W = K32[2 * p + 1];
         }
     }
-    const int x = s % L.nx, t = s / L.nx, y = t % L.ny, z = t / L.ny;
-    // s - X, nearest image
-    float dx = (float)x - X.x, dy = (float)y - X.y, dz = (float)z - X.z;
-    if (dx > 0.5f * L.nx) dx -= L.nx;
-    if (dx < -0.5f * L.nx) dx += L.nx;
-    if (dy > 0.5f * L.ny) dy -= L.ny;
-    if (dy < -0.5f * L.ny) dy += L.ny;
-    if (!L.walls) {
-        if (dz > 0.5f * L.nz) dz -= L.nz;
-        if (dz < -0.5f * L.nz) dz += L.nz;
-    }
-    // Directions in lockstep over the warp: neighbouring entries (particle
-    // nodes along x) then touch neighbouring elements of the same slot
-    // array.  Each direction's offsets are compile-time constants.
-    const bool edge = x == 0 || x == L.nx - 1 || y == 0 || y == L.ny - 1 || z == 0 || z == L.nz - 1;
+    // direction j's links: the lanes of ballot j, after those of 1 .. j-1
+    int total = 0;
 #pragma unroll
     for (int j = 1; j < Q; j++) {
-        if (!((fm >> j) & 1u)) continue;
-        int yf = s + cx(j) + L.nx * (cy(j) + L.ny * cz(j));  // the fluid node
-        if (edge) {
-            int xn = x + cx(j), yn = y + cy(j), zn = z + cz(j);
+        const unsigned b = __ballot_sync(full, (fm >> j) & 1u);
+        if (lane == j) {
+            w.bal[j] = b;
+            w.pre[j] = total;
+        }
+        total += __popc(b);
+    }
+    __syncwarp();
+    for (uint32_t m = fm; m; m &= m - 1) {
+        const int j = __ffs(m) - 1;
+        const int k = w.pre[j] + __popc(w.bal[j] & ((1u << lane) - 1u));
+        w.desc[k] = (uint16_t)(lane | (j << 5));
+    }
+    __syncwarp();
+    for (int k0 = 0; k0 < total; k0 += 32) {
+        const int k = k0 + lane;
+        const bool act = k < total;
+        const int d = act ? w.desc[k] : 0;
+        const int src = d & 31, j = act ? d >> 5 : 1;
+        const int sn = __shfl_sync(full, s, src), pn = __shfl_sync(full, p, src);
+        unsigned long long acc[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+        if (act) {
+            const float4 X = X32[pn], V = K32[2 * pn], W = K32[2 * pn + 1];
+            const int x = sn % L.nx, t = sn / L.nx, y = t % L.ny, z = t / L.ny;
+            // sn - X, nearest image
+            float dx = (float)x - X.x, dy = (float)y - X.y, dz = (float)z - X.z;
+            if (dx > 0.5f * L.nx) dx -= L.nx;
+            if (dx < -0.5f * L.nx) dx += L.nx;
+            if (dy > 0.5f * L.ny) dy -= L.ny;
+            if (dy < -0.5f * L.ny) dy += L.ny;
+            if (!L.walls) {
+                if (dz > 0.5f * L.nz) dz -= L.nz;
+                if (dz < -0.5f * L.nz) dz += L.nz;
+            }
+            const int cxj = cdir(CXP, j), cyj = cdir(CYP, j), czj = cdir(CZP, j);
+            int xn = x + cxj, yn = y + cyj, zn = z + czj;  // the fluid node
             xn = xn < 0 ? xn + L.nx : (xn >= L.nx ? xn - L.nx : xn);
             yn = yn < 0 ? yn + L.ny : (yn >= L.ny ? yn - L.ny : yn);
             zn = zn < 0 ? zn + L.nz : (zn >= L.nz ? zn - L.nz : zn);
-            yf = xn + L.nx * (yn + L.ny * zn);
+            const int yf = xn + L.nx * (yn + L.ny * zn);
+            const float fcx = (float)cxj, fcy = (float)cyj, fcz = (float)czj;
+            const float rx = dx + 0.5f * fcx, ry = dy + 0.5f * fcy, rz = dz + 0.5f * fcz;
+            // surface velocity V + ω × r_b at the link midpoint
+            const float usx = __fsub_rn(__fmaf_rn(W.y, rz, V.x), __fmul_rn(W.z, ry));
+            const float usy = __fsub_rn(__fmaf_rn(W.z, rx, V.y), __fmul_rn(W.x, rz));
+            const float usz = __fsub_rn(__fmaf_rn(W.x, ry, V.z), __fmul_rn(W.y, rx));
+            // u_surf·c_i with c_i = -c_j
+            const float uci = -__fadd_rn(__fadd_rn(usx * fcx, usy * fcy), usz * fcz);
+            const float w6 = j < 7 ? -6.f / 18.f : -6.f / 36.f;
+            // both components of slot j of the fluid node: one pair access
+            typename S::P *q = fout + pidx(L, j, yf);
+            const float2 fs = ld2f<S>(fout, L, j, yf);
+            const float2 ry2 = __ldg(reinterpret_cast<const float2 *>(rho) + yf);
+            const float C0 = __fmul_rn(__fmul_rn(w6, ry2.x), uci);
+            const float C1 = __fmul_rn(__fmul_rn(w6, ry2.y), uci);
+            *q = S::enc2(make_float2(__fadd_rn(fs.x, C0) - L.base[0][j], __fadd_rn(fs.y, C1) - L.base[1][j]));
+            float a = 0.f;
+            a = __fadd_rn(a, __fmaf_rn(2.f, fs.x, C0));
+            a = __fadd_rn(a, __fmaf_rn(2.f, fs.y, C1));
+            // F = a c_i = -a c_j
+            const float Fx = -a * fcx, Fy = -a * fcy, Fz = -a * fcz;
+            acc[0] = to_fixed(Fx);
+            acc[1] = to_fixed(Fy);
+            acc[2] = to_fixed(Fz);
+            acc[3] = to_fixed(__fsub_rn(__fmul_rn(ry, Fz), __fmul_rn(rz, Fy)));
+            acc[4] = to_fixed(__fsub_rn(__fmul_rn(rz, Fx), __fmul_rn(rx, Fz)));
+            acc[5] = to_fixed(__fsub_rn(__fmul_rn(rx, Fy), __fmul_rn(ry, Fx)));
         }
-        const float rx = dx + 0.5f * cx(j), ry = dy + 0.5f * cy(j), rz = dz + 0.5f * cz(j);
-        // surface velocity V + ω × r_b at the link midpoint
-        const float usx = __fsub_rn(__fmaf_rn(W.y, rz, V.x), __fmul_rn(W.z, ry));
-        const float usy = __fsub_rn(__fmaf_rn(W.z, rx, V.y), __fmul_rn(W.x, rz));
-        const float usz = __fsub_rn(__fmaf_rn(W.x, ry, V.z), __fmul_rn(W.y, rx));
-        // u_surf·c_i with c_i = -c_j
-        const float uci = -__fadd_rn(__fadd_rn(usx * cx(j), usy * cy(j)), usz * cz(j));
-        const float w6 = j < 7 ? -6.f / 18.f : -6.f / 36.f;
-        // both components of slot j of the fluid node: one pair access
-        typename S::P *q = fout + pidx(L, j, yf);
-        const float2 fs = ld2f<S>(fout, L, j, yf);
-        const float2 ry2 = __ldg(reinterpret_cast<const float2 *>(rho) + yf);
-        const float C0 = __fmul_rn(__fmul_rn(w6, ry2.x), uci);
-        const float C1 = __fmul_rn(__fmul_rn(w6, ry2.y), uci);
-        *q = S::enc2(make_float2(__fadd_rn(fs.x, C0) - L.base[0][j], __fadd_rn(fs.y, C1) - L.base[1][j]));
-        float a = 0.f;
-        a = __fadd_rn(a, __fmaf_rn(2.f, fs.x, C0));
-        a = __fadd_rn(a, __fmaf_rn(2.f, fs.y, C1));
-        // F = a c_i = -a c_j
-        const float Fx = -a * cx(j), Fy = -a * cy(j), Fz = -a * cz(j);
-        acc[0] += to_fixed(Fx);
-        acc[1] += to_fixed(Fy);
-        acc[2] += to_fixed(Fz);
-        acc[3] += to_fixed(__fsub_rn(__fmul_rn(ry, Fz), __fmul_rn(rz, Fy)));
-        acc[4] += to_fixed(__fsub_rn(__fmul_rn(rz, Fx), __fmul_rn(rx, Fz)));
-        acc[5] += to_fixed(__fsub_rn(__fmul_rn(rx, Fy), __fmul_rn(ry, Fx)));
+        warp_add_fix(act ? pn : -1, acc, fix);
     }
-    warp_add_fix(p, acc, fix);
+    __syncwarp();
 }
 
 // Warp-uniform trip count over the entries (every lane takes part in the
 // reductions).
 template <class S>
 __device__ __forceinline__ void link_list(const Lat &L, const LinkList &ll, const float *rho, const uint32_t *owner,
-                                          const Parts &P, typename S::P *fout, int first, int stride)
+                                          const Parts &P, typename S::P *fout, int first, int stride, LinkWarp &w)
 {
     const int count = min(*ll.count, ll.cap);
     for (int w0 = first + (int)(threadIdx.x & ~31u); w0 < count; w0 += stride) {
         const int e = w0 + (threadIdx.x & 31);
         const bool valid = e < count;
-        link_entry<S>(L, valid ? ll.ent[e] : make_uint2(0u, 0u), valid, rho, owner, P.X32, P.K32, P.fix, fout);
+        link_entries<S>(L, valid ? ll.ent[e] : make_uint2(0u, 0u), valid, rho, owner, P.X32, P.K32, P.fix, fout, w);
     }
 }
 
@@ -646,7 +687,8 @@ template <class S>
 __global__ void __launch_bounds__(256) k_link(Lat L, LinkList ll, const float *rho, const uint32_t *owner, Parts P,
                                               typename S::P *fout)
 {
-    link_list<S>(L, ll, rho, owner, P, fout, blockIdx.x * blockDim.x, gridDim.x * blockDim.x);
+    __shared__ LinkWarp w[256 / 32];
+    link_list<S>(L, ll, rho, owner, P, fout, blockIdx.x * blockDim.x, gridDim.x * blockDim.x, w[threadIdx.x >> 5]);
 }
 
 // Batched: blockIdx.y is the box; LINK_BATCH_CTAS CTAs per box.
@@ -659,8 +701,9 @@ __global__ void __launch_bounds__(256) k_link_batch(BatchIndex B)
     const BoxDev &bx = B.box[b];
     if (!bx.links.ent || bx.P.n == 0) return;
     const int cur = B.par[2 * b], ocur = B.par[2 * b + 1];
+    __shared__ LinkWarp w[256 / 32];
     link_list<S>(bx.L, bx.links, bx.rho, bx.owner[ocur], bx.P, (typename S::P *)bx.f[1 - cur],
-                 blockIdx.x * blockDim.x, gridDim.x * blockDim.x);
+                 blockIdx.x * blockDim.x, gridDim.x * blockDim.x, w[threadIdx.x >> 5]);
 }
 
 // --------------------------------------------------------- pair forces
