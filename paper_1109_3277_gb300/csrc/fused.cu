@@ -4,21 +4,29 @@
 // halfway bounce-back, in one pass over the populations.
 //
 // A CTA owns a 32 x TY column of nodes and walks a chunk of z planes.  For
-// every plane from one below the chunk to one above it, one TMA tensor copy
-// brings the populations of the tile and a one-node halo into shared memory
-// (a box of the (x, y, z, direction) array of (red, blue) pairs, x widened
-// to 16-byte boundaries), completing on an mbarrier.  Each thread sums the
-// densities of its node and of at most one halo node, so the ψ of the tile
-// and its halo is formed on chip; halo nodes beyond the lattice edge wrap
-// around and are read from global memory instead.  Solid nodes (walls,
-// particles) take their ψ from the shell fill, which ran before.  The ψ,
-// node type and a per-row bitmask of solid nodes go into a four-slot ring
-// of planes; the collision of plane z reads planes z-1, z and z+1 of it.
+// every plane of the chunk one TMA tensor copy brings the populations of
+// the tile into shared memory (a box of the (x, y, z, direction) array of
+// (red, blue) pairs), completing on an mbarrier.  The ψ, node type and a
+// per-row bitmask of solid nodes of the tile and a one-node halo go into a
+// four-slot ring of planes; the collision of plane z reads planes z-1, z
+// and z+1 of it.  Two configurations fill the ring:
+//  - ψ formed on chip (lattices without particles): the box also holds a
+//    one-node halo (x widened to 16-byte boundaries), and each thread sums
+//    the densities of its node and of at most one halo node, so ψ of the
+//    tile and its halo comes from the stage; halo nodes beyond the lattice
+//    edge wrap around and are read from global memory.  Solid nodes (walls)
+//    take their ψ from the shell fill.
+//  - ψ from memory (lattices with particles): the density pass and the
+//    shell fill have written ψ of every node a fluid node sees.  The ring
+//    entries of plane z + 2 arrive by asynchronous copies issued before the
+//    collision of plane z and waited for after it.
 //
 // With τ = 1 for both components the post-collision populations are the
-// equilibria, so a node's populations are needed only for its moments,
-// which are taken when its plane arrives: two stages suffice.  Other τ keep
-// three stages and re-read the node's populations at the collision.
+// equilibria, so a node's populations are needed only for its moments:
+// with ψ formed on chip two stages suffice, while other τ keep three and
+// re-read the node's populations at the collision.  With ψ from memory a
+// third stage (copies two planes ahead) is kept where it costs no CTA per
+// SM.
 //
 // Populations streaming into a wall or particle node are reflected into the
 // opposite slot of their own node (halfway bounce-back).  For particle
