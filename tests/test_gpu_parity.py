@@ -98,6 +98,32 @@ def test_static_particle_one_step():
     assert np.max(np.abs(pg["torque"] - pr["torque"])) < 1e-5 * max(1.0, np.abs(pr["torque"]).max())
 
 
+def test_large_particle_links_beyond_the_shell_buffer():
+    """A sphere of radius 14 has about 3,000 shell nodes, more than the
+    shell kernel collects per particle in shared memory (1,024): the rest
+    enter the link list directly.  One step of a moving static sphere
+    against the oracle: populations, and the momentum exchange."""
+    shape = (40, 40, 40)
+    f0 = W.random_populations(shape, seed=29)
+    g, r = _pair(shape, np.full((2, 40, 40, 40), 0.5), g_br=0.1, particle_mode="static")
+    _add(g, r, pos=[[19.6, 20.3, 19.8]], quat=[W.axis_tilt_quaternion(0.4, 0.7)], r_par=14.2,
+         r_perp=13.8, delta_rho=0.05, vel=[[0.01, -0.015, 0.02]], omega=[[0.001, -0.002, 0.0015]])
+    _, _, tg = g.read_fields()
+    _, _, tr = r.read_fields()
+    assert np.array_equal(tg, tr)
+    g.set_populations(f0)
+    r.set_populations(f0)
+    g.step(1)
+    r.step(1)
+    fl = tr == 0
+    fg, fr = g.get_populations(), r.get_populations()
+    assert np.max(np.abs(fg[:, :, fl] - fr[:, :, fl])) < TOL_F_ONE_STEP
+    pg, pr = g.read_particles(), r.read_particles()
+    scale = max(1.0, np.abs(pr["force"]).max())
+    assert np.max(np.abs(pg["force"] - pr["force"])) < 1e-5 * scale
+    assert np.max(np.abs(pg["torque"] - pr["torque"])) < 1e-5 * max(1.0, np.abs(pr["torque"]).max())
+
+
 def test_prescribed_motion_fill_empty():
     """A particle driven through the lattice: coverage changes every few
     steps, exercising fill and empty."""
